@@ -1,0 +1,190 @@
+/*
+ * reg.h - C ABI of the GB300 (sm_103a) implementation of the reduced-space
+ * Gauss-Newton-Krylov solver for constrained H1/H2-regularized stationary-
+ * velocity image registration of Mang & Biros, "Constrained H1-regularization
+ * schemes for diffeomorphic image registration" (arXiv 1503.00757).
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * Grid.  n1 x n2 nodes on the periodic domain [0, 2 pi)^2 (the paper's
+ *   (-pi, pi)^2 shifted by a period, Sec. 2); node (i, j) is at
+ *   x = (2 pi i / n1, 2 pi j / n2).  n1 and n2 are powers of two in [16, 1024].
+ * Layout.  A scalar field is n1*n2 floats, row-major, index i*n2 + j (x^2
+ *   fastest).  A vector field is two scalar planes back to back (component 1
+ *   then component 2, 2*n1*n2 floats).  Buffers must be 16-byte aligned.
+ * Memory.  Unless an entry point says "host", every float/double pointer is a
+ *   DEVICE pointer owned by the caller.  The library never frees or retains a
+ *   caller pointer beyond the call.  Scalar outputs (double*) are HOST pointers.
+ *   The context owns its own device workspace (state history etc.).
+ * Streams.  Work is issued on the context stream (reg_set_stream; default:
+ *   the legacy default stream).  Entry points that return host scalars
+ *   synchronize that stream; the others are asynchronous.
+ * Errors.  Every entry point returns a reg_status.  Invalid arguments are
+ *   rejected with REG_ERR_ARG before any launch.  A CUDA error is returned as
+ *   REG_ERR_CUDA (the message is available from reg_last_error).  Non-finite
+ *   objective or gradient values are reported as REG_ERR_NAN.
+ * Threading.  A context is not thread-safe; distinct contexts are independent.
+ * Precision.  Fields, FFTs and transport run in FP32; objective values,
+ *   norms, inner products and the det(F) statistics are accumulated in FP64.
+ */
+#ifndef REG_H
+#define REG_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct reg_ctx reg_ctx;
+
+typedef struct {
+    int n1; /* nodes along x^1 (rows) */
+    int n2; /* nodes along x^2 (columns, contiguous) */
+} reg_grid;
+
+enum reg_norm { REG_H1 = 1, REG_H2 = 2 };
+
+enum reg_status {
+    REG_OK = 0,
+    REG_ERR_ARG = 1,
+    REG_ERR_CUDA = 2,
+    REG_ERR_NOMEM = 3,
+    REG_ERR_NAN = 4,
+    REG_ERR_LINESEARCH = 5,
+    REG_ERR_PCG_MAXIT = 6, /* reported in stats, not returned */
+    REG_ERR_TIMEOUT = 7,
+    REG_WARN_CFL = 8,      /* reported in stats, not returned */
+    REG_ERR_STATE = 9,     /* call order violated (e.g. matvec before gradient) */
+    REG_ERR_MAXIT = 10     /* Newton iteration cap reached before the tolerance */
+};
+
+enum reg_nt_policy { REG_NT_FIXED = 0, REG_NT_CFL = 1 };
+
+/* Options of the Newton-Krylov solve (Algorithm 1, Algorithm 2, Sec. 5).
+ * reg_default_opts fills the defaults given in brackets. */
+typedef struct {
+    double tol;          /* [1e-2] stop when ||g_k|| / ||g_ref|| <= tol */
+    int maxit_newton;    /* [50]  outer iteration cap */
+    int maxit_pcg;       /* [100] Hessian matvecs per PCG solve */
+    double armijo_c1;    /* [1e-4] sufficient decrease constant */
+    double armijo_rho;   /* [0.5] backtracking factor */
+    int max_ls;          /* [20]  backtracking steps before REG_ERR_LINESEARCH */
+    int nt_policy;       /* [REG_NT_FIXED] or REG_NT_CFL */
+    double cfl_max;      /* [0.25] CFL number targeted by REG_NT_CFL */
+    int warm_start;      /* [0] 1: v_inout holds the initial guess; g_ref is g(0) */
+} reg_solve_opts;
+
+/* Statistics of one solve (the measures of the paper's Tab. 1 / Appendix F). */
+typedef struct {
+    int n_newton;        /* outer iterations */
+    int n_mv;            /* Gauss-Newton Hessian matvecs */
+    int n_pde;           /* hyperbolic PDE solves (state, adjoint, 2 per matvec) */
+    int n_ls;            /* line-search objective evaluations */
+    int n_pcg_maxit;     /* PCG solves that hit maxit_pcg */
+    int status;          /* final reg_status */
+    int nt_used;         /* time steps at the end of the solve */
+    int cfl_warn;        /* 1 if the CFL number exceeded cfl_max (fixed policy) */
+    double J0, J;        /* objective at the start / end */
+    double gnorm_rel;    /* ||g_k*|| / ||g_ref|| */
+    double rnorm_rel_sq; /* ||m_R - m_1||^2 / ||m_R - m_T||^2 (Appendix F) */
+    double cfl;          /* CFL number max|v| nt^-1 / h_x at the end */
+} reg_solve_stats;
+
+/* Error string of the last failing call on this thread (never NULL). */
+const char* reg_last_error(void);
+
+void reg_default_opts(reg_solve_opts* opts);
+
+/* Create a context.  Problem (Eq. (e:objective)-(e:constraint-divv)):
+ *   nt       time steps of the RK2 transport solves (Sec. 5), >= 1;
+ *   regnorm  REG_H1 or REG_H2 seminorm on v (Eq. (e:reg-v));
+ *   beta     beta_v > 0;
+ *   gamma    beta_w of the mass-source H1 norm (Eq. (e:reg-w)); 0 disables the
+ *            divergence constraint (the paper's gamma = 0); +INFINITY enforces
+ *            div v = 0 (w = 0); a finite positive value is the mass-source
+ *            weight beta_w;
+ *   shear    s in (-1, 1); s != 0 selects the nonlinear Stokes model
+ *            (Eq. (e:shear-control-reg-v)) with nu = (1 + s) / (1 - s); it
+ *            requires REG_H1 and gamma = +INFINITY.
+ * Allocates the device workspace on the current device. */
+int reg_create(reg_grid grid, int nt, int regnorm, double beta, double gamma, double shear, reg_ctx** out);
+void reg_destroy(reg_ctx* ctx);
+
+/* Issue all work on `stream` (a cudaStream_t; NULL = legacy default stream). */
+int reg_set_stream(reg_ctx* ctx, void* stream);
+
+/* Copy the template m_T and reference m_R (device, n1*n2 floats) into the
+ * context (Eq. (e:objective), (e:init-transport-eq)). */
+int reg_set_images(reg_ctx* ctx, const float* mT, const float* mR);
+
+/* ---- rows a1-a4: spectral operators (Sec. 5, pseudospectral discretization) ---- */
+
+/* grad f (2*n1*n2 out) of a scalar field f; odd symbol i k with the Nyquist
+ * wavenumber set to 0. */
+int reg_spectral_grad(reg_ctx* ctx, const float* f, float* grad_f);
+/* div u (n1*n2 out) of a vector field u; same odd symbol. */
+int reg_spectral_div(reg_ctx* ctx, const float* u, float* div_u);
+/* beta_v A[v] (Eq. (e:var-reg-v)); for the shear model beta_v A[v] of
+ * Eq. (e:1st-var-reg-v-nls). */
+int reg_apply_reg(reg_ctx* ctx, const float* v, float* out);
+/* K[b] (Eq. (e:project-body-force)); Leray projection for gamma = inf,
+ * identity for gamma = 0. */
+int reg_apply_proj(reg_ctx* ctx, const float* b, float* out);
+/* (beta_v A)^-1 r with the k = 0 symbol replaced by 1 (Appendix E); the
+ * inverse vector Laplacian for the shear model. */
+int reg_apply_precond(reg_ctx* ctx, const float* r, float* out);
+
+/* ---- rows a5-a7: state solve, objective, adjoint, reduced gradient ---- */
+
+/* Forward state solve (Eq. (e:state-eq-elim)) and objective J[v]
+ * (Eq. (e:objective)).  m1 (nullable) receives m(t = 1); J (nullable, host). */
+int reg_objective(reg_ctx* ctx, const float* v, float* m1, double* J);
+/* Reduced gradient g = beta_v A[v] + K[b] (Eq. (e:control-eq-elim)), state
+ * and adjoint solves of Algorithm 1.  g: 2*n1*n2 out; J (nullable, host).
+ * Fixes the linearization point for reg_hessian_matvec. */
+int reg_gradient(reg_ctx* ctx, const float* v, float* g, double* J);
+
+/* ---- rows a8-a10: Gauss-Newton Hessian matvec ---- */
+
+/* H v~ = beta_v B[v~] + L[b~] (Eq. (e:inc-control-eq-elim)) with the
+ * Gauss-Newton approximation (lambda terms dropped, Sec. 5), at the v of the
+ * last reg_gradient call (REG_ERR_STATE otherwise). */
+int reg_hessian_matvec(reg_ctx* ctx, const float* vt, float* Hvt);
+
+/* ---- rows a12-a13: Newton-Krylov solve (Algorithms 1 and 2) ---- */
+
+/* v_inout (device, 2*n1*n2): initial guess if opts->warm_start, else ignored
+ * (v_0 = 0); receives the final velocity.  opts NULL = defaults.  stats
+ * (nullable, host).  Returns REG_OK, REG_ERR_LINESEARCH, REG_ERR_MAXIT,
+ * REG_ERR_NAN or an argument/CUDA error. */
+int reg_solve(reg_ctx* ctx, float* v_inout, const reg_solve_opts* opts, reg_solve_stats* stats);
+
+/* Same solve with HOST buffers: copies m_T, m_R (host, n1*n2 floats) to the
+ * device, solves, and copies v (host, 2*n1*n2 floats; the initial guess when
+ * opts->warm_start) back.  Synchronous. */
+int reg_register_host(reg_ctx* ctx, const float* mT_host, const float* mR_host, float* v_host,
+                      const reg_solve_opts* opts, reg_solve_stats* stats);
+
+/* ---- row a14: deformation gradient (Eq. (e:def-grad)) ---- */
+
+/* Transports F (F(0) = I) with v; detF (nullable, device n1*n2) receives
+ * det F1; stats (host, 5 doubles) receives min, mean, max of det F1 and max,
+ * mean of D = ||F1 - I||_F (Appendix F). */
+int reg_detgrad(reg_ctx* ctx, const float* v, float* detF, double* stats);
+
+/* ---- instrumentation ---- */
+
+/* Per-kernel-class CUDA-event timing (off by default).  While enabled, every
+ * launch of a kernel of class `kclass` is bracketed by events on the context
+ * stream.  reg_kernel_time returns the launch count and summed milliseconds
+ * since the last enable.  Classes: 0 column FFT kernels, 1 row stage kernels
+ * (advection/adjoint), 2 other row kernels, 3 pointwise/reduction kernels. */
+int reg_kernel_timing(reg_ctx* ctx, int enable);
+int reg_kernel_time(reg_ctx* ctx, int kclass, long long* launches, double* ms);
+/* Number of kernels this context has launched since creation. */
+long long reg_launch_count(reg_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* REG_H */

@@ -1,0 +1,232 @@
+"""Thin Python binding of libreg.so (include/reg.h).
+
+Argument marshalling only: every step of the computation runs in the CUDA
+kernels behind the C ABI.  Field arguments are torch CUDA float32 tensors
+(contiguous, 16-byte aligned); the binding passes their device pointers.
+If the library has not been built this module raises on first use; there is
+no CPU fallback.
+"""
+import ctypes
+import math
+import os
+
+from .build import LIB_PATH
+
+REG_H1, REG_H2 = 1, 2
+REG_NT_FIXED, REG_NT_CFL = 0, 1
+STATUS = {0: "REG_OK", 1: "REG_ERR_ARG", 2: "REG_ERR_CUDA", 3: "REG_ERR_NOMEM", 4: "REG_ERR_NAN",
+          5: "REG_ERR_LINESEARCH", 6: "REG_ERR_PCG_MAXIT", 7: "REG_ERR_TIMEOUT", 8: "REG_WARN_CFL",
+          9: "REG_ERR_STATE", 10: "REG_ERR_MAXIT"}
+
+
+class reg_grid(ctypes.Structure):
+    _fields_ = [("n1", ctypes.c_int), ("n2", ctypes.c_int)]
+
+
+class reg_solve_opts(ctypes.Structure):
+    _fields_ = [("tol", ctypes.c_double), ("maxit_newton", ctypes.c_int), ("maxit_pcg", ctypes.c_int),
+                ("armijo_c1", ctypes.c_double), ("armijo_rho", ctypes.c_double), ("max_ls", ctypes.c_int),
+                ("nt_policy", ctypes.c_int), ("cfl_max", ctypes.c_double), ("warm_start", ctypes.c_int)]
+
+
+class reg_solve_stats(ctypes.Structure):
+    _fields_ = [("n_newton", ctypes.c_int), ("n_mv", ctypes.c_int), ("n_pde", ctypes.c_int),
+                ("n_ls", ctypes.c_int), ("n_pcg_maxit", ctypes.c_int), ("status", ctypes.c_int),
+                ("nt_used", ctypes.c_int), ("cfl_warn", ctypes.c_int), ("J0", ctypes.c_double),
+                ("J", ctypes.c_double), ("gnorm_rel", ctypes.c_double), ("rnorm_rel_sq", ctypes.c_double),
+                ("cfl", ctypes.c_double)]
+
+    def as_dict(self):
+        return {name: getattr(self, name) for name, _ in self._fields_}
+
+
+_P = ctypes.c_void_p
+_I = ctypes.c_int
+_D = ctypes.c_double
+_SIGS = {
+    "reg_last_error": ([], ctypes.c_char_p),
+    "reg_default_opts": ([ctypes.POINTER(reg_solve_opts)], None),
+    "reg_create": ([reg_grid, _I, _I, _D, _D, _D, ctypes.POINTER(_P)], _I),
+    "reg_destroy": ([_P], None),
+    "reg_set_stream": ([_P, _P], _I),
+    "reg_set_images": ([_P, _P, _P], _I),
+    "reg_spectral_grad": ([_P, _P, _P], _I),
+    "reg_spectral_div": ([_P, _P, _P], _I),
+    "reg_apply_reg": ([_P, _P, _P], _I),
+    "reg_apply_proj": ([_P, _P, _P], _I),
+    "reg_apply_precond": ([_P, _P, _P], _I),
+    "reg_objective": ([_P, _P, _P, ctypes.POINTER(_D)], _I),
+    "reg_gradient": ([_P, _P, _P, ctypes.POINTER(_D)], _I),
+    "reg_hessian_matvec": ([_P, _P, _P], _I),
+    "reg_solve": ([_P, _P, ctypes.POINTER(reg_solve_opts), ctypes.POINTER(reg_solve_stats)], _I),
+    "reg_register_host": ([_P, _P, _P, _P, ctypes.POINTER(reg_solve_opts), ctypes.POINTER(reg_solve_stats)], _I),
+    "reg_detgrad": ([_P, _P, _P, ctypes.POINTER(_D)], _I),
+    "reg_kernel_timing": ([_P, _I], _I),
+    "reg_kernel_time": ([_P, _I, ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(_D)], _I),
+    "reg_launch_count": ([_P], ctypes.c_longlong),
+}
+
+_lib = None
+
+
+def lib():
+    """Load libreg.so (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is missing: build it with __graft_entry__.build()")
+        L = ctypes.CDLL(LIB_PATH)
+        for name, (args, res) in _SIGS.items():
+            fn = getattr(L, name)
+            fn.argtypes = args
+            fn.restype = res
+        _lib = L
+    return _lib
+
+
+class RegError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+def _check(st):
+    if st != 0:
+        raise RegError(st, lib().reg_last_error().decode())
+    return st
+
+
+def _ptr(t, numel=None, name="tensor"):
+    if t is None:
+        return None
+    import torch
+    if not isinstance(t, torch.Tensor) or t.device.type != "cuda" or t.dtype != torch.float32:
+        raise TypeError(f"{name} must be a CUDA float32 tensor")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    if numel is not None and t.numel() != numel:
+        raise ValueError(f"{name} has {t.numel()} elements, expected {numel}")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def default_opts(**kw):
+    o = reg_solve_opts()
+    lib().reg_default_opts(ctypes.byref(o))
+    for k, v in kw.items():
+        setattr(o, k, v)
+    return o
+
+
+class Context:
+    """Owns one reg_ctx (one registration problem on one grid)."""
+
+    def __init__(self, n1, n2, nt, regnorm=REG_H1, beta=1e-2, gamma=math.inf, shear=0.0, stream=None):
+        self.n1, self.n2, self.N = n1, n2, n1 * n2
+        h = ctypes.c_void_p()
+        _check(lib().reg_create(reg_grid(n1, n2), nt, regnorm, beta, gamma, shear, ctypes.byref(h)))
+        self.h = h
+        if stream is not None:
+            self.set_stream(stream)
+
+    def close(self):
+        if self.h:
+            lib().reg_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_stream(self, stream):
+        """stream: a torch.cuda.Stream (or None for the legacy default stream)."""
+        handle = None if stream is None else ctypes.c_void_p(stream.cuda_stream)
+        _check(lib().reg_set_stream(self.h, handle))
+
+    def set_images(self, mT, mR):
+        _check(lib().reg_set_images(self.h, _ptr(mT, self.N, "mT"), _ptr(mR, self.N, "mR")))
+
+    def spectral_grad(self, f, out):
+        _check(lib().reg_spectral_grad(self.h, _ptr(f, self.N), _ptr(out, 2 * self.N)))
+
+    def spectral_div(self, u, out):
+        _check(lib().reg_spectral_div(self.h, _ptr(u, 2 * self.N), _ptr(out, self.N)))
+
+    def apply_reg(self, v, out):
+        _check(lib().reg_apply_reg(self.h, _ptr(v, 2 * self.N), _ptr(out, 2 * self.N)))
+
+    def apply_proj(self, b, out):
+        _check(lib().reg_apply_proj(self.h, _ptr(b, 2 * self.N), _ptr(out, 2 * self.N)))
+
+    def apply_precond(self, r, out):
+        _check(lib().reg_apply_precond(self.h, _ptr(r, 2 * self.N), _ptr(out, 2 * self.N)))
+
+    def objective(self, v, m1=None):
+        J = ctypes.c_double()
+        _check(lib().reg_objective(self.h, _ptr(v, 2 * self.N), _ptr(m1, self.N), ctypes.byref(J)))
+        return J.value
+
+    def gradient(self, v, g):
+        J = ctypes.c_double()
+        _check(lib().reg_gradient(self.h, _ptr(v, 2 * self.N), _ptr(g, 2 * self.N), ctypes.byref(J)))
+        return J.value
+
+    def hessian_matvec(self, vt, Hvt):
+        _check(lib().reg_hessian_matvec(self.h, _ptr(vt, 2 * self.N), _ptr(Hvt, 2 * self.N)))
+
+    def solve(self, v, opts=None, check=True):
+        """Newton-Krylov solve; v (2, n1, n2) is overwritten.  Returns the stats dict."""
+        st = reg_solve_stats()
+        o = opts if opts is not None else default_opts()
+        rc = lib().reg_solve(self.h, _ptr(v, 2 * self.N, "v"), ctypes.byref(o), ctypes.byref(st))
+        if check:
+            _check(rc)
+        d = st.as_dict()
+        d["rc"] = rc
+        return d
+
+    def register_host(self, mT_host, mR_host, v_host, opts=None, check=True):
+        """Solve from host float32 buffers (numpy arrays or pinned CPU tensors)."""
+        import numpy as np
+
+        def hptr(a, n, writable=False):
+            if hasattr(a, "data_ptr"):
+                if a.device.type != "cpu" or a.dtype.__str__() != "torch.float32" or not a.is_contiguous():
+                    raise TypeError("host buffers must be contiguous CPU float32")
+                if a.numel() != n:
+                    raise ValueError("bad host buffer size")
+                return ctypes.c_void_p(a.data_ptr())
+            if not (isinstance(a, np.ndarray) and a.dtype == np.float32 and a.flags["C_CONTIGUOUS"]):
+                raise TypeError("host buffers must be contiguous float32")
+            if a.size != n:
+                raise ValueError("bad host buffer size")
+            return ctypes.c_void_p(a.ctypes.data)
+
+        st = reg_solve_stats()
+        o = opts if opts is not None else default_opts()
+        rc = lib().reg_register_host(self.h, hptr(mT_host, self.N), hptr(mR_host, self.N),
+                                     hptr(v_host, 2 * self.N, True), ctypes.byref(o), ctypes.byref(st))
+        if check:
+            _check(rc)
+        d = st.as_dict()
+        d["rc"] = rc
+        return d
+
+    def detgrad(self, v, detF=None):
+        """Returns (min det F1, mean det F1, max det F1, max D, mean D)."""
+        stats = (ctypes.c_double * 5)()
+        _check(lib().reg_detgrad(self.h, _ptr(v, 2 * self.N), _ptr(detF, self.N), stats))
+        return tuple(stats)
+
+    def kernel_timing(self, enable):
+        _check(lib().reg_kernel_timing(self.h, int(enable)))
+
+    def kernel_time(self, kclass):
+        n = ctypes.c_longlong()
+        ms = ctypes.c_double()
+        _check(lib().reg_kernel_time(self.h, kclass, ctypes.byref(n), ctypes.byref(ms)))
+        return n.value, ms.value
+
+    def launch_count(self):
+        return lib().reg_launch_count(self.h)

@@ -1,0 +1,786 @@
+// C ABI (include/reg.h) and host orchestration of the reduced-space
+// Gauss-Newton-Krylov registration solver (Algorithms 1 and 2 of Mang & Biros,
+// arXiv 1503.00757).  Every arithmetic step runs in the kernels of kernels.cu;
+// the host only sequences launches and reads back FP64 scalars for the
+// decisions of the PCG stop test, the Armijo test and the Newton stop test.
+#include <cmath>
+#include <cstdio>
+#include <cstdint>
+#include <cstring>
+#include <string>
+
+#include "fft.cuh"
+#include "internal.h"
+
+static thread_local std::string g_err = "no error";
+
+int reg_fail(int status, const std::string& msg) {
+    g_err = msg;
+    return status;
+}
+
+extern "C" const char* reg_last_error(void) { return g_err.c_str(); }
+
+#define CK(call)                                                                        \
+    do {                                                                                \
+        cudaError_t e_ = (call);                                                        \
+        if (e_ != cudaSuccess)                                                          \
+            return reg_fail(REG_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+    } while (0)
+
+#define CKL()                                                                                       \
+    do {                                                                                            \
+        cudaError_t e_ = cudaGetLastError();                                                        \
+        if (e_ != cudaSuccess) return reg_fail(REG_ERR_CUDA, std::string("launch: ") + cudaGetErrorString(e_)); \
+    } while (0)
+
+#define RET(x)                  \
+    do {                        \
+        int s_ = (x);           \
+        if (s_ != REG_OK) return s_; \
+    } while (0)
+
+int col_blocks(reg_ctx* ctx);
+
+static bool is_pow2(int n) { return n > 0 && (n & (n - 1)) == 0; }
+static int ilog2(int n) { int l = 0; while ((1 << l) < n) ++l; return l; }
+
+extern "C" void reg_default_opts(reg_solve_opts* o) {
+    if (!o) return;
+    o->tol = 1e-2;
+    o->maxit_newton = 50;
+    o->maxit_pcg = 100;
+    o->armijo_c1 = 1e-4;
+    o->armijo_rho = 0.5;
+    o->max_ls = 20;
+    o->nt_policy = REG_NT_FIXED;
+    o->cfl_max = 0.25;
+    o->warm_start = 0;
+}
+
+// ---------------------------------------------------------------------------
+// allocation
+// ---------------------------------------------------------------------------
+static void free_hist(reg_ctx* c) {
+    cudaFree(c->m_hist);
+    cudaFree(c->gm_hist);
+    c->m_hist = c->gm_hist = nullptr;
+}
+
+static int alloc_hist(reg_ctx* c, int nt) {
+    if (nt <= c->nt_cap && c->m_hist) return REG_OK;
+    free_hist(c);
+    const size_t N = c->N;
+    if (cudaMalloc(&c->m_hist, sizeof(float) * N * (nt + 1)) != cudaSuccess ||
+        cudaMalloc(&c->gm_hist, sizeof(float) * 2 * N * (nt + 1)) != cudaSuccess) {
+        cudaGetLastError();
+        free_hist(c);
+        c->nt_cap = 0;
+        return reg_fail(REG_ERR_NOMEM, "cudaMalloc of the state history failed");
+    }
+    c->nt_cap = nt;
+    c->have_lin = false;
+    return REG_OK;
+}
+
+extern "C" void reg_destroy(reg_ctx* c) {
+    if (!c) return;
+    float** fl[] = {&c->mT, &c->mR, &c->v_lin, &c->E_lin, &c->eta_lin, &c->w0, &c->w1, &c->w2, &c->w3,
+                    &c->bvec, &c->vtmp, &c->vtmp2, &c->gtmp, &c->T3, &c->g, &c->r, &c->z, &c->s, &c->Hs,
+                    &c->vt, &c->vtrial, &c->F, &c->Fs, &c->gF, &c->gv};
+    for (auto p : fl) cudaFree(*p);
+    for (int i = 0; i < 6; ++i) cudaFree(c->S[i]);
+    free_hist(c);
+    cudaFree(c->d_scal);
+    cudaFree(c->d_part);
+    cudaFree(c->tw);
+    cudaFreeHost(c->h_scal);
+    for (auto e : c->event_pool) cudaEventDestroy(e);
+    delete c;
+}
+
+extern "C" int reg_create(reg_grid grid, int nt, int regnorm, double beta, double gamma, double shear, reg_ctx** out) {
+    if (!out) return reg_fail(REG_ERR_ARG, "out is NULL");
+    *out = nullptr;
+    if (!is_pow2(grid.n1) || !is_pow2(grid.n2) || grid.n1 < 16 || grid.n2 < 16 || grid.n1 > 1024 || grid.n2 > 1024)
+        return reg_fail(REG_ERR_ARG, "n1 and n2 must be powers of two in [16, 1024]");
+    if (nt < 1 || nt > 100000) return reg_fail(REG_ERR_ARG, "nt must be in [1, 100000]");
+    if (regnorm != REG_H1 && regnorm != REG_H2) return reg_fail(REG_ERR_ARG, "regnorm must be REG_H1 or REG_H2");
+    if (!(beta > 0.0) || !std::isfinite(beta)) return reg_fail(REG_ERR_ARG, "beta must be finite and > 0");
+    if (!(gamma >= 0.0)) return reg_fail(REG_ERR_ARG, "gamma must be >= 0 or +INFINITY");
+    if (!(shear > -1.0 && shear < 1.0)) return reg_fail(REG_ERR_ARG, "shear must be in (-1, 1)");
+    if (shear != 0.0 && (regnorm != REG_H1 || !std::isinf(gamma)))
+        return reg_fail(REG_ERR_ARG, "shear control requires REG_H1 and gamma = +INFINITY");
+
+    reg_ctx* c = new reg_ctx();
+    memset(c->S, 0, sizeof(c->S));
+    c->n1 = grid.n1;
+    c->n2 = grid.n2;
+    c->N = grid.n1 * grid.n2;
+    c->log1 = ilog2(grid.n1);
+    c->log2 = ilog2(grid.n2);
+    c->nt = nt;
+    c->nt_cap = 0;
+    c->regnorm = regnorm;
+    c->beta_v = beta;
+    c->beta_w = gamma;
+    c->shear = shear;
+    c->shear_model = shear != 0.0;
+    c->nu = (1.0 + shear) / (1.0 - shear);
+    c->pmode = (gamma == 0.0) ? PROJ_IDENTITY : (std::isinf(gamma) ? PROJ_LERAY : PROJ_MASS);
+    c->stream = 0;
+    c->have_lin = false;
+    c->launches = 0;
+    c->timing = false;
+    for (int k = 0; k < KC_COUNT; ++k) { c->tcount[k] = 0; c->tms[k] = 0.0; }
+
+    const size_t N = c->N;
+    bool ok = true;
+    auto A = [&](float** p, size_t n) { if (ok && cudaMalloc(p, sizeof(float) * n) != cudaSuccess) ok = false; };
+    A(&c->mT, N); A(&c->mR, N); A(&c->v_lin, 2 * N); A(&c->E_lin, 3 * N); A(&c->eta_lin, N);
+    A(&c->w0, N); A(&c->w1, N); A(&c->w2, N); A(&c->w3, N);
+    A(&c->bvec, 2 * N); A(&c->vtmp, 2 * N); A(&c->vtmp2, 2 * N); A(&c->gtmp, 4 * N); A(&c->T3, 3 * N);
+    A(&c->g, 2 * N); A(&c->r, 2 * N); A(&c->z, 2 * N); A(&c->s, 2 * N); A(&c->Hs, 2 * N);
+    A(&c->vt, 2 * N); A(&c->vtrial, 2 * N);
+    A(&c->F, 4 * N); A(&c->Fs, 4 * N); A(&c->gF, 8 * N); A(&c->gv, 4 * N);
+    for (int i = 0; i < 6 && ok; ++i)
+        if (cudaMalloc(&c->S[i], sizeof(float2) * N / 2) != cudaSuccess) ok = false;
+    c->npart = 5 * 304 + 4096;
+    if (ok && cudaMalloc(&c->d_scal, sizeof(double) * SL_COUNT) != cudaSuccess) ok = false;
+    if (ok && cudaMalloc(&c->d_part, sizeof(double) * c->npart) != cudaSuccess) ok = false;
+    if (ok && cudaMalloc(&c->tw, sizeof(float2) * REG_TW_N) != cudaSuccess) ok = false;
+    if (ok && cudaMallocHost(&c->h_scal, sizeof(double) * SL_COUNT) != cudaSuccess) ok = false;
+    if (!ok) {
+        cudaGetLastError();
+        reg_destroy(c);
+        return reg_fail(REG_ERR_NOMEM, "device allocation failed");
+    }
+    if (k_init_twiddles(c) != cudaSuccess) {
+        reg_destroy(c);
+        return reg_fail(REG_ERR_CUDA, "twiddle upload failed");
+    }
+    int st = alloc_hist(c, nt);
+    if (st != REG_OK) {
+        reg_destroy(c);
+        return st;
+    }
+    cudaMemset(c->mT, 0, sizeof(float) * N);
+    cudaMemset(c->mR, 0, sizeof(float) * N);
+    *out = c;
+    return REG_OK;
+}
+
+extern "C" int reg_set_stream(reg_ctx* c, void* stream) {
+    if (!c) return reg_fail(REG_ERR_ARG, "ctx is NULL");
+    c->stream = (cudaStream_t)stream;
+    return REG_OK;
+}
+
+static int check_ptr(const void* p, const char* what) {
+    if (!p) return reg_fail(REG_ERR_ARG, std::string(what) + " is NULL");
+    if (((uintptr_t)p) & 15) return reg_fail(REG_ERR_ARG, std::string(what) + " is not 16-byte aligned");
+    return REG_OK;
+}
+
+extern "C" int reg_set_images(reg_ctx* c, const float* mT, const float* mR) {
+    if (!c) return reg_fail(REG_ERR_ARG, "ctx is NULL");
+    RET(check_ptr(mT, "mT"));
+    RET(check_ptr(mR, "mR"));
+    CK(cudaMemcpyAsync(c->mT, mT, sizeof(float) * c->N, cudaMemcpyDeviceToDevice, c->stream));
+    CK(cudaMemcpyAsync(c->mR, mR, sizeof(float) * c->N, cudaMemcpyDeviceToDevice, c->stream));
+    c->have_lin = false;
+    return REG_OK;
+}
+
+// ---------------------------------------------------------------------------
+// spectral building blocks
+// ---------------------------------------------------------------------------
+static SpecParams spec_params(reg_ctx* c, float coefA) {
+    SpecParams P;
+    P.scale = 1.0f / (float)c->N;
+    P.coefA = coefA;
+    P.beta_v = (float)c->beta_v;
+    P.beta_w = (c->pmode == PROJ_MASS) ? (float)c->beta_w : 0.f;
+    P.regnorm = c->shear_model ? REG_H1 : c->regnorm;
+    P.pmode = c->pmode;
+    const double h1 = 2.0 * M_PI / c->n1, h2 = 2.0 * M_PI / c->n2;
+    P.escale = h1 * h2 / (double)c->N;
+    P.ebv = 0.5 * c->beta_v;
+    P.ebw = (c->pmode == PROJ_MASS) ? 0.5 * c->beta_w : 0.0;
+    return P;
+}
+
+static double hh(reg_ctx* c) { return (2.0 * M_PI / c->n1) * (2.0 * M_PI / c->n2); }
+
+// grad of a scalar field into out (2N)
+static void sp_grad(reg_ctx* c, const float* f, float* out) {
+    launch_r2c_scalar(c, f, c->S[0]);
+    const float2* in[1] = {c->S[0]};
+    float2* o[2] = {c->S[1], c->S[2]};
+    launch_col(c, OP_GRAD, in, o, spec_params(c, 0.f), nullptr);
+    launch_c2r_vec(c, c->S[1], c->S[2], out, out + c->N);
+}
+
+static void sp_div(reg_ctx* c, const float* u, float* out) {
+    launch_r2c_vec(c, u, u + c->N, c->S[0], c->S[1]);
+    const float2* in[2] = {c->S[0], c->S[1]};
+    float2* o[1] = {c->S[2]};
+    launch_col(c, OP_DIV, in, o, spec_params(c, 0.f), nullptr);
+    launch_c2r_scalar(c, c->S[2], out);
+}
+
+static void sp_vec(reg_ctx* c, int op, float coefA, const float* u, float* out) {
+    launch_r2c_vec(c, u, u + c->N, c->S[0], c->S[1]);
+    const float2* in[2] = {c->S[0], c->S[1]};
+    float2* o[2] = {c->S[2], c->S[3]};
+    launch_col(c, op, in, o, spec_params(c, coefA), nullptr);
+    launch_c2r_vec(c, c->S[2], c->S[3], out, out + c->N);
+}
+
+// out = coefA A u + K b  (reduced gradient / Hessian assembly, Eq. (e:control-eq-elim), (e:inc-control-eq-elim))
+static void sp_assemble(reg_ctx* c, float coefA, const float* u, const float* b, float* out) {
+    launch_r2c_vec(c, u, u + c->N, c->S[0], c->S[1]);
+    launch_r2c_vec(c, b, b + c->N, c->S[2], c->S[3]);
+    const float2* in[4] = {c->S[0], c->S[1], c->S[2], c->S[3]};
+    float2* o[2] = {c->S[4], c->S[5]};
+    launch_col(c, OP_ASSEMBLE, in, o, spec_params(c, coefA), nullptr);
+    launch_c2r_vec(c, c->S[4], c->S[5], out, out + c->N);
+}
+
+// grad of a vector field: gv planes (d1 u1, d2 u1, d1 u2, d2 u2)
+static void sp_grad_vec(reg_ctx* c, const float* u, float* gv) {
+    sp_grad(c, u, gv);
+    sp_grad(c, u + c->N, gv + 2 * (size_t)c->N);
+}
+
+// out = P_L(coefA div T + b), T = 3 planes (shear model)
+static void sp_divt_proj(reg_ctx* c, float coefA, const float* T, const float* b, float* out) {
+    const size_t N = c->N;
+    launch_r2c_vec(c, T, T + N, c->S[0], c->S[1]);
+    launch_r2c_vec(c, T + 2 * N, b, c->S[2], c->S[3]);
+    launch_r2c_scalar(c, b + N, c->S[4]);
+    const float2* in[5] = {c->S[0], c->S[1], c->S[2], c->S[3], c->S[4]};
+    float2* o[2] = {c->S[5], c->S[0]};
+    launch_col(c, OP_DIVT_PROJ, in, o, spec_params(c, coefA), nullptr);
+    launch_c2r_vec(c, c->S[5], c->S[0], out, out + N);
+}
+
+// regularization energy into d_scal[SL_JREG]
+static void reg_energy(reg_ctx* c, const float* v) {
+    if (c->shear_model) {
+        sp_grad_vec(c, v, c->gtmp);
+        int np = launch_shear_strain(c, c->gtmp, (float)c->nu, nullptr, nullptr, nullptr, c->d_part);
+        const double coef = c->beta_v * (2.0 * c->nu / (c->nu + 1.0)) * hh(c);
+        launch_finalize(c, c->d_part, np, c->d_scal + SL_JREG, coef, 0, 0);
+        return;
+    }
+    launch_r2c_vec(c, v, v + c->N, c->S[0], c->S[1]);
+    const float2* in[2] = {c->S[0], c->S[1]};
+    launch_col(c, OP_ENERGY, in, nullptr, spec_params(c, 0.f), c->d_part);
+    launch_finalize(c, c->d_part, col_blocks(c), c->d_scal + SL_JREG, 1.0, 0, 0);
+}
+
+static float* mh(reg_ctx* c, int j) { return c->m_hist + (size_t)j * c->N; }
+static float* gmh(reg_ctx* c, int j) { return c->gm_hist + (size_t)j * 2 * c->N; }
+
+// State equation (Eq. (e:state-eq-elim)), Heun in time: fills m_hist[0..nt], gm_hist[0..nt].
+static void state_solve(reg_ctx* c, const float* v, int nt) {
+    const float h = 1.0f / (float)nt;
+    cudaMemcpyAsync(mh(c, 0), c->mT, sizeof(float) * c->N, cudaMemcpyDeviceToDevice, c->stream);
+    launch_r2c_scalar(c, mh(c, 0), c->S[0]);
+    const float2* in[1] = {c->S[0]};
+    float2* G[2] = {c->S[1], c->S[2]};
+    const SpecParams P = spec_params(c, 0.f);
+    for (int j = 0; j < nt; ++j) {
+        launch_col(c, OP_GRAD, in, G, P, nullptr);
+        AdvArgs a = {};
+        a.G1 = c->S[1]; a.G2 = c->S[2];
+        a.uj = mh(c, j); a.us = nullptr; a.v = v;
+        a.gm = nullptr; a.vt = nullptr;
+        a.u_out = c->w0; a.grad_out = gmh(c, j); a.S_out = c->S[0];
+        a.h = h; a.stage = 1;
+        launch_row_adv(c, a);
+        launch_col(c, OP_GRAD, in, G, P, nullptr);
+        a.us = c->w0; a.u_out = mh(c, j + 1); a.grad_out = nullptr; a.stage = 2;
+        launch_row_adv(c, a);
+    }
+    launch_col(c, OP_GRAD, in, G, P, nullptr);
+    launch_c2r_vec(c, c->S[1], c->S[2], gmh(c, nt), gmh(c, nt) + c->N);
+}
+
+// Adjoint (Eq. (e:adj-eq-elim)) or Gauss-Newton incremental adjoint
+// (Eq. (e:inc-adj-eq-elim)) backward in time from lam_nt = ca*a + cb*cf, with
+// the body force b = int lam grad m dt (trapezoid) accumulated into bout.
+static void adjoint_solve(reg_ctx* c, const float* v, int nt, const float* a, float ca, const float* cf, float cb,
+                          float* bout, double* part_jdata) {
+    const float h = 1.0f / (float)nt;
+    float* lam = c->w1;
+    float* lst = c->w2;
+    launch_adj_init(c, a, ca, cf, cb, v, lam, bout, gmh(c, nt), 0.5f * h, c->S[1], c->S[2], part_jdata);
+    const float2* Fin[2] = {c->S[1], c->S[2]};
+    float2* D[1] = {c->S[0]};
+    const SpecParams P = spec_params(c, 0.f);
+    for (int j = nt; j >= 1; --j) {
+        launch_col(c, OP_DIV, Fin, D, P, nullptr);
+        AdjArgs s1 = {};
+        s1.D = c->S[0]; s1.lj = lam; s1.ls = nullptr; s1.v = v; s1.l_out = lst;
+        s1.b = nullptr; s1.gm = nullptr; s1.w = 0.f; s1.F1 = c->S[1]; s1.F2 = c->S[2]; s1.h = h; s1.stage = 1;
+        launch_row_adj(c, s1);
+        launch_col(c, OP_DIV, Fin, D, P, nullptr);
+        AdjArgs s2 = s1;
+        s2.ls = lst; s2.l_out = lam; s2.stage = 2;
+        s2.b = bout; s2.gm = gmh(c, j - 1); s2.w = (j - 1 == 0) ? 0.5f * h : h;
+        if (j == 1) { s2.F1 = nullptr; s2.F2 = nullptr; }
+        launch_row_adj(c, s2);
+    }
+}
+
+// Incremental state (Eq. (e:inc-state-eq-elim)); leaves m~(1) in c->w3.
+static void inc_state_solve(reg_ctx* c, const float* v, const float* vt, int nt) {
+    const float h = 1.0f / (float)nt;
+    float* mj = c->w3;
+    float* ms = c->w0;
+    launch_fill(c, c->N, mj, 0.f);
+    const float2* in[1] = {c->S[0]};
+    float2* G[2] = {c->S[1], c->S[2]};
+    const SpecParams P = spec_params(c, 0.f);
+    for (int j = 0; j < nt; ++j) {
+        AdvArgs a = {};
+        if (j > 0) {
+            launch_col(c, OP_GRAD, in, G, P, nullptr);
+            a.G1 = c->S[1]; a.G2 = c->S[2];
+        }
+        a.uj = mj; a.us = nullptr; a.v = v; a.gm = gmh(c, j); a.vt = vt;
+        a.u_out = ms; a.grad_out = nullptr; a.S_out = c->S[0]; a.h = h; a.stage = 1;
+        launch_row_adv(c, a);
+        launch_col(c, OP_GRAD, in, G, P, nullptr);
+        a.G1 = c->S[1]; a.G2 = c->S[2];
+        a.us = ms; a.gm = gmh(c, j + 1); a.u_out = mj; a.stage = 2;
+        a.S_out = (j + 1 < nt) ? c->S[0] : nullptr;
+        launch_row_adv(c, a);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// objective / gradient / matvec
+// ---------------------------------------------------------------------------
+static int read_scalars(reg_ctx* c) {
+    CK(cudaMemcpyAsync(c->h_scal, c->d_scal, sizeof(double) * SL_COUNT, cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    return REG_OK;
+}
+
+static int ensure_nt(reg_ctx* c, int nt) { return alloc_hist(c, nt); }
+
+// forward solve + J (device slots SL_JDATA, SL_JREG); lam_nt left in w1 if want_adj
+static int objective_dev(reg_ctx* c, const float* v, int nt) {
+    RET(ensure_nt(c, nt));
+    state_solve(c, v, nt);
+    // J_data = 0.5 ||m_R - m_1||^2
+    launch_axpby(c, c->N, 1.f, c->mR, -1.f, mh(c, nt), -1, -1, c->w1);
+    int np = launch_dot_partial(c, c->w1, c->w1, c->N, c->d_part);
+    launch_finalize(c, c->d_part, np, c->d_scal + SL_JDATA, 0.5 * hh(c), 0, 0);
+    reg_energy(c, v);
+    CKL();
+    return REG_OK;
+}
+
+static int gradient_dev(reg_ctx* c, const float* v, float* g, int nt) {
+    RET(objective_dev(c, v, nt));
+    adjoint_solve(c, v, nt, c->mR, 1.f, mh(c, nt), -1.f, c->bvec, nullptr);
+    if (c->shear_model) {
+        sp_grad_vec(c, v, c->gtmp);
+        launch_shear_strain(c, c->gtmp, (float)c->nu, c->E_lin, c->eta_lin, c->T3, nullptr);
+        sp_divt_proj(c, -(float)c->beta_v, c->T3, c->bvec, g);
+    } else {
+        sp_assemble(c, (float)c->beta_v, v, c->bvec, g);
+    }
+    if (v != c->v_lin)
+        cudaMemcpyAsync(c->v_lin, v, sizeof(float) * 2 * c->N, cudaMemcpyDeviceToDevice, c->stream);
+    c->nt_lin = nt;
+    c->have_lin = true;
+    CKL();
+    return REG_OK;
+}
+
+static int matvec_dev(reg_ctx* c, const float* vt, float* Hvt) {
+    if (!c->have_lin) return reg_fail(REG_ERR_STATE, "reg_hessian_matvec called before reg_gradient");
+    const int nt = c->nt_lin;
+    inc_state_solve(c, c->v_lin, vt, nt);
+    adjoint_solve(c, c->v_lin, nt, nullptr, 0.f, c->w3, -1.f, c->bvec, nullptr);
+    if (c->shear_model) {
+        sp_grad_vec(c, vt, c->gtmp);
+        launch_shear_second(c, c->gtmp, c->E_lin, c->eta_lin, (float)c->nu, c->T3);
+        sp_divt_proj(c, -(float)c->beta_v, c->T3, c->bvec, Hvt);
+    } else {
+        sp_assemble(c, (float)c->beta_v, vt, c->bvec, Hvt);
+    }
+    CKL();
+    return REG_OK;
+}
+
+static void precond_dev(reg_ctx* c, const float* r, float* z) {
+    sp_vec(c, OP_PRECOND, 0.f, r, z);
+}
+
+// ---------------------------------------------------------------------------
+// C ABI: unit operators
+// ---------------------------------------------------------------------------
+#define CTX_CHECK(c) if (!(c)) return reg_fail(REG_ERR_ARG, "ctx is NULL")
+
+extern "C" int reg_spectral_grad(reg_ctx* c, const float* f, float* out) {
+    CTX_CHECK(c);
+    RET(check_ptr(f, "f")); RET(check_ptr(out, "grad_f"));
+    sp_grad(c, f, out);
+    CKL();
+    return REG_OK;
+}
+
+extern "C" int reg_spectral_div(reg_ctx* c, const float* u, float* out) {
+    CTX_CHECK(c);
+    RET(check_ptr(u, "u")); RET(check_ptr(out, "div_u"));
+    sp_div(c, u, out);
+    CKL();
+    return REG_OK;
+}
+
+extern "C" int reg_apply_reg(reg_ctx* c, const float* v, float* out) {
+    CTX_CHECK(c);
+    RET(check_ptr(v, "v")); RET(check_ptr(out, "out"));
+    if (c->shear_model) {
+        sp_grad_vec(c, v, c->gtmp);
+        launch_shear_strain(c, c->gtmp, (float)c->nu, nullptr, nullptr, c->T3, nullptr);
+        // beta_v A[v] = -beta_v div(2 eta E), without projection: use the divergence of each row of T
+        const size_t N = c->N;
+        launch_r2c_vec(c, c->T3, c->T3 + N, c->S[0], c->S[1]);
+        const float2* in0[2] = {c->S[0], c->S[1]};
+        float2* o0[1] = {c->S[2]};
+        launch_col(c, OP_DIV, in0, o0, spec_params(c, 0.f), nullptr);
+        launch_r2c_vec(c, c->T3 + N, c->T3 + 2 * N, c->S[0], c->S[1]);
+        float2* o1[1] = {c->S[3]};
+        launch_col(c, OP_DIV, in0, o1, spec_params(c, 0.f), nullptr);
+        launch_c2r_vec(c, c->S[2], c->S[3], out, out + N);
+        launch_axpby(c, 2 * (long long)N, -(float)c->beta_v, out, 0.f, out, -1, -1, out);
+    } else {
+        sp_vec(c, OP_REG, (float)c->beta_v, v, out);
+    }
+    CKL();
+    return REG_OK;
+}
+
+extern "C" int reg_apply_proj(reg_ctx* c, const float* b, float* out) {
+    CTX_CHECK(c);
+    RET(check_ptr(b, "b")); RET(check_ptr(out, "out"));
+    sp_vec(c, OP_PROJ, 0.f, b, out);
+    CKL();
+    return REG_OK;
+}
+
+extern "C" int reg_apply_precond(reg_ctx* c, const float* r, float* out) {
+    CTX_CHECK(c);
+    RET(check_ptr(r, "r")); RET(check_ptr(out, "out"));
+    precond_dev(c, r, out);
+    CKL();
+    return REG_OK;
+}
+
+extern "C" int reg_objective(reg_ctx* c, const float* v, float* m1, double* J) {
+    CTX_CHECK(c);
+    RET(check_ptr(v, "v"));
+    if (m1) RET(check_ptr(m1, "m1"));
+    RET(objective_dev(c, v, c->nt));
+    c->have_lin = false;  // history now belongs to this v, but grad/adjoint data do not
+    if (m1) CK(cudaMemcpyAsync(m1, mh(c, c->nt), sizeof(float) * c->N, cudaMemcpyDeviceToDevice, c->stream));
+    if (J) {
+        RET(read_scalars(c));
+        *J = c->h_scal[SL_JDATA] + c->h_scal[SL_JREG];
+        if (!std::isfinite(*J)) return reg_fail(REG_ERR_NAN, "objective is not finite");
+    }
+    return REG_OK;
+}
+
+extern "C" int reg_gradient(reg_ctx* c, const float* v, float* g, double* J) {
+    CTX_CHECK(c);
+    RET(check_ptr(v, "v")); RET(check_ptr(g, "g"));
+    RET(gradient_dev(c, v, g, c->nt));
+    if (J) {
+        RET(read_scalars(c));
+        *J = c->h_scal[SL_JDATA] + c->h_scal[SL_JREG];
+        if (!std::isfinite(*J)) return reg_fail(REG_ERR_NAN, "objective is not finite");
+    }
+    return REG_OK;
+}
+
+extern "C" int reg_hessian_matvec(reg_ctx* c, const float* vt, float* Hvt) {
+    CTX_CHECK(c);
+    RET(check_ptr(vt, "vt")); RET(check_ptr(Hvt, "Hvt"));
+    return matvec_dev(c, vt, Hvt);
+}
+
+// ---------------------------------------------------------------------------
+// Newton-Krylov solve (Algorithm 1) with PCG (Algorithm 2)
+// ---------------------------------------------------------------------------
+static int dot_dev(reg_ctx* c, const float* x, const float* y, int slot) {
+    int np = launch_dot_partial(c, x, y, 2 * (long long)c->N, c->d_part);
+    launch_finalize(c, c->d_part, np, c->d_scal + slot, hh(c), 0, 0);
+    return REG_OK;
+}
+
+static int nt_for(reg_ctx* c, const float* v, const reg_solve_opts& o, double* cfl_out) {
+    int np = launch_maxnorm_partial(c, v, c->N, c->d_part);
+    launch_finalize(c, c->d_part, np, c->d_scal + SL_VMAX, 1.0, 0, 1);
+    if (read_scalars(c) != REG_OK) return -1;
+    const double vmax = c->h_scal[SL_VMAX];
+    const int n = c->n1 > c->n2 ? c->n1 : c->n2;
+    int nt = c->nt;
+    if (o.nt_policy == REG_NT_CFL) {
+        const int need = (int)std::ceil(vmax * n / (2.0 * M_PI * o.cfl_max));
+        if (need > nt) nt = need;
+    }
+    if (cfl_out) *cfl_out = vmax * n / (2.0 * M_PI * nt);
+    return nt;
+}
+
+// PCG (Algorithm 2) on H vt = -g; returns #matvecs
+static int pcg_dev(reg_ctx* c, double gnorm, double eta, int maxit, int* hit_max, int* status) {
+    const long long n2N = 2 * (long long)c->N;
+    const double scale = hh(c);
+    *status = REG_OK;
+    launch_fill(c, n2N, c->vt, 0.f);
+    launch_axpby(c, n2N, -1.f, c->g, 0.f, c->r, -1, -1, c->r);  // r = -g
+    precond_dev(c, c->r, c->z);
+    CK(cudaMemcpyAsync(c->s, c->z, sizeof(float) * n2N, cudaMemcpyDeviceToDevice, c->stream));
+    dot_dev(c, c->r, c->z, SL_RZ);
+    int it = 0;
+    *hit_max = 1;
+    for (int l = 0; l < maxit; ++l) {
+        int st = matvec_dev(c, c->s, c->Hs);
+        if (st != REG_OK) { *status = st; return it; }
+        ++it;
+        dot_dev(c, c->s, c->Hs, SL_SHS);
+        if (read_scalars(c) != REG_OK) { *status = REG_ERR_CUDA; return it; }
+        const double sHs = c->h_scal[SL_SHS];
+        if (!std::isfinite(sHs)) { *status = REG_ERR_NAN; return it; }
+        if (sHs <= 0.0) {
+            *hit_max = 0;
+            if (it == 1) CK(cudaMemcpyAsync(c->vt, c->s, sizeof(float) * n2N, cudaMemcpyDeviceToDevice, c->stream));
+            break;
+        }
+        int np = launch_pcg_update(c, n2N, c->vt, c->s, c->r, c->Hs, c->d_part);
+        launch_finalize(c, c->d_part, np, c->d_scal + SL_RNORM2, scale, 0, 0);
+        if (read_scalars(c) != REG_OK) { *status = REG_ERR_CUDA; return it; }
+        const double rn = std::sqrt(c->h_scal[SL_RNORM2]);
+        if (!std::isfinite(rn)) { *status = REG_ERR_NAN; return it; }
+        if (rn < eta * gnorm) { *hit_max = 0; break; }
+        precond_dev(c, c->r, c->z);
+        dot_dev(c, c->z, c->r, SL_RZNEW);
+        launch_pcg_dir(c, n2N, c->z, c->s);
+        CK(cudaMemcpyAsync(c->d_scal + SL_RZ, c->d_scal + SL_RZNEW, sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
+    }
+    CKL();
+    return it;
+}
+
+extern "C" int reg_solve(reg_ctx* c, float* v, const reg_solve_opts* opts, reg_solve_stats* stats) {
+    CTX_CHECK(c);
+    RET(check_ptr(v, "v_inout"));
+    reg_solve_opts o;
+    reg_default_opts(&o);
+    if (opts) o = *opts;
+    if (!(o.tol > 0) || o.maxit_newton < 0 || o.maxit_pcg < 1 || o.max_ls < 1 || !(o.armijo_rho > 0 && o.armijo_rho < 1) ||
+        !(o.cfl_max > 0))
+        return reg_fail(REG_ERR_ARG, "invalid solve options");
+    reg_solve_stats st;
+    memset(&st, 0, sizeof(st));
+    const long long n2N = 2 * (long long)c->N;
+    const size_t vb = sizeof(float) * n2N;
+    int n_pde = 0;
+    double gref;
+    if (!o.warm_start) launch_fill(c, n2N, v, 0.f);
+    double cfl = 0.0;
+    int nt = nt_for(c, v, o, &cfl);
+    if (nt < 0) return reg_fail(REG_ERR_CUDA, "scalar readback failed");
+    if (o.warm_start) {
+        launch_fill(c, n2N, c->vtrial, 0.f);
+        RET(gradient_dev(c, c->vtrial, c->g, c->nt));
+        n_pde += 2;
+        dot_dev(c, c->g, c->g, SL_GNORM2);
+        RET(read_scalars(c));
+        gref = std::sqrt(c->h_scal[SL_GNORM2]);
+    }
+    RET(gradient_dev(c, v, c->g, nt));
+    n_pde += 2;
+    dot_dev(c, c->g, c->g, SL_GNORM2);
+    RET(read_scalars(c));
+    double J = c->h_scal[SL_JDATA] + c->h_scal[SL_JREG];
+    double gnorm = std::sqrt(c->h_scal[SL_GNORM2]);
+    if (!o.warm_start) gref = gnorm;
+    st.J0 = J;
+    int status = REG_OK;
+    int k = 0;
+    if (!std::isfinite(J) || !std::isfinite(gnorm)) status = REG_ERR_NAN;
+    while (status == REG_OK) {
+        if (gref == 0.0 || gnorm / gref <= o.tol) break;
+        if (k >= o.maxit_newton) { status = REG_ERR_MAXIT; break; }
+        const double eta = std::fmin(0.5, std::sqrt(gnorm / gref));
+        int hit = 0, pst = REG_OK;
+        const int it = pcg_dev(c, gnorm, eta, o.maxit_pcg, &hit, &pst);
+        st.n_mv += it;
+        n_pde += 2 * it;
+        st.n_pcg_maxit += hit;
+        if (pst != REG_OK) { status = pst; break; }
+        dot_dev(c, c->g, c->vt, SL_GV);
+        RET(read_scalars(c));
+        double gv = c->h_scal[SL_GV];
+        if (!(gv < 0.0)) {
+            precond_dev(c, c->g, c->vt);
+            launch_axpby(c, n2N, 0.f, c->vt, -1.f, c->vt, -1, -1, c->vt);
+            dot_dev(c, c->g, c->vt, SL_GV);
+            RET(read_scalars(c));
+            gv = c->h_scal[SL_GV];
+        }
+        double alpha = 1.0;
+        bool accepted = false;
+        double Jt = J;
+        for (int ls = 0; ls < o.max_ls; ++ls) {
+            launch_axpby(c, n2N, (float)alpha, c->vt, 1.f, v, -1, -1, c->vtrial);
+            RET(objective_dev(c, c->vtrial, nt));
+            n_pde += 1;
+            st.n_ls += 1;
+            RET(read_scalars(c));
+            Jt = c->h_scal[SL_JDATA] + c->h_scal[SL_JREG];
+            if (std::isfinite(Jt) && Jt <= J + o.armijo_c1 * alpha * gv) { accepted = true; break; }
+            alpha *= o.armijo_rho;
+        }
+        if (!accepted) {
+            status = REG_ERR_LINESEARCH;
+            // restore the linearization data of the current iterate for a consistent return
+            RET(gradient_dev(c, v, c->g, nt));
+            n_pde += 2;
+            break;
+        }
+        CK(cudaMemcpyAsync(v, c->vtrial, vb, cudaMemcpyDeviceToDevice, c->stream));
+        ++k;
+        nt = nt_for(c, v, o, &cfl);
+        if (nt < 0) return reg_fail(REG_ERR_CUDA, "scalar readback failed");
+        RET(gradient_dev(c, v, c->g, nt));
+        n_pde += 2;
+        dot_dev(c, c->g, c->g, SL_GNORM2);
+        RET(read_scalars(c));
+        J = c->h_scal[SL_JDATA] + c->h_scal[SL_JREG];
+        gnorm = std::sqrt(c->h_scal[SL_GNORM2]);
+        if (!std::isfinite(J) || !std::isfinite(gnorm)) status = REG_ERR_NAN;
+    }
+    // mismatch measure (Appendix F): ||m_R - m_1||^2 / ||m_R - m_T||^2
+    launch_axpby(c, c->N, 1.f, c->mR, -1.f, c->mT, -1, -1, c->w0);
+    {
+        int np = launch_dot_partial(c, c->w0, c->w0, c->N, c->d_part);
+        launch_finalize(c, c->d_part, np, c->d_scal + SL_DOT0, hh(c), 0, 0);
+    }
+    RET(read_scalars(c));
+    const double r0 = c->h_scal[SL_DOT0];
+    const double r1 = 2.0 * c->h_scal[SL_JDATA];
+    st.n_newton = k;
+    st.n_pde = n_pde;
+    st.status = status;
+    st.nt_used = nt;
+    st.J = J;
+    st.gnorm_rel = gref > 0 ? gnorm / gref : 0.0;
+    st.rnorm_rel_sq = r0 > 0 ? r1 / r0 : 0.0;
+    st.cfl = cfl;
+    st.cfl_warn = cfl > o.cfl_max ? 1 : 0;
+    if (stats) *stats = st;
+    CKL();
+    if (status == REG_ERR_NAN) return reg_fail(REG_ERR_NAN, "objective or gradient became non-finite");
+    if (status == REG_ERR_LINESEARCH) return reg_fail(REG_ERR_LINESEARCH, "Armijo line search failed");
+    if (status == REG_ERR_MAXIT) return reg_fail(REG_ERR_MAXIT, "Newton iteration cap reached");
+    return status;
+}
+
+extern "C" int reg_register_host(reg_ctx* c, const float* mT_host, const float* mR_host, float* v_host,
+                                 const reg_solve_opts* opts, reg_solve_stats* stats) {
+    CTX_CHECK(c);
+    if (!mT_host || !mR_host || !v_host) return reg_fail(REG_ERR_ARG, "host buffer is NULL");
+    const size_t N = c->N;
+    CK(cudaMemcpyAsync(c->mT, mT_host, sizeof(float) * N, cudaMemcpyHostToDevice, c->stream));
+    CK(cudaMemcpyAsync(c->mR, mR_host, sizeof(float) * N, cudaMemcpyHostToDevice, c->stream));
+    c->have_lin = false;
+    float* v = c->vtmp2;
+    if (opts && opts->warm_start)
+        CK(cudaMemcpyAsync(v, v_host, sizeof(float) * 2 * N, cudaMemcpyHostToDevice, c->stream));
+    const int st = reg_solve(c, v, opts, stats);
+    if (st == REG_ERR_ARG || st == REG_ERR_CUDA || st == REG_ERR_NOMEM) return st;
+    CK(cudaMemcpyAsync(v_host, v, sizeof(float) * 2 * N, cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    return st;
+}
+
+// ---------------------------------------------------------------------------
+// deformation gradient (Eq. (e:def-grad)) and its measures (Appendix F)
+// ---------------------------------------------------------------------------
+extern "C" int reg_detgrad(reg_ctx* c, const float* v, float* detF, double* stats) {
+    CTX_CHECK(c);
+    RET(check_ptr(v, "v"));
+    if (detF) RET(check_ptr(detF, "detF"));
+    const size_t N = c->N;
+    const int nt = c->nt;
+    const float h = 1.0f / (float)nt;
+    sp_grad_vec(c, v, c->gv);
+    // F = I
+    launch_fill(c, 4 * (long long)N, c->F, 0.f);
+    launch_fill(c, N, c->F, 1.f);
+    launch_fill(c, N, c->F + 3 * N, 1.f);
+    for (int j = 0; j < nt; ++j) {
+        for (int comp = 0; comp < 4; ++comp) sp_grad(c, c->F + comp * N, c->gF + 2 * comp * N);
+        launch_defgrad_stage(c, 1, c->F, nullptr, c->gF, c->gv, v, h, c->Fs);
+        for (int comp = 0; comp < 4; ++comp) sp_grad(c, c->Fs + comp * N, c->gF + 2 * comp * N);
+        launch_defgrad_stage(c, 2, c->F, c->Fs, c->gF, c->gv, v, h, c->gtmp);
+        CK(cudaMemcpyAsync(c->F, c->gtmp, sizeof(float) * 4 * N, cudaMemcpyDeviceToDevice, c->stream));
+    }
+    const int np = launch_det_stats(c, c->F, detF, c->d_part);
+    launch_finalize(c, c->d_part + 0 * np, np, c->d_scal + SL_DET0 + 0, 1.0, 0, 2);
+    launch_finalize(c, c->d_part + 1 * np, np, c->d_scal + SL_DET0 + 1, 1.0 / (double)N, 0, 0);
+    launch_finalize(c, c->d_part + 2 * np, np, c->d_scal + SL_DET0 + 2, 1.0, 0, 1);
+    launch_finalize(c, c->d_part + 3 * np, np, c->d_scal + SL_DET0 + 3, 1.0, 0, 1);
+    launch_finalize(c, c->d_part + 4 * np, np, c->d_scal + SL_DET0 + 4, 1.0 / (double)N, 0, 0);
+    CKL();
+    if (stats) {
+        RET(read_scalars(c));
+        for (int q = 0; q < 5; ++q) stats[q] = c->h_scal[SL_DET0 + q];
+    }
+    return REG_OK;
+}
+
+// ---------------------------------------------------------------------------
+// instrumentation
+// ---------------------------------------------------------------------------
+static void drain_events(reg_ctx* c) {
+    if (c->events.empty()) return;
+    cudaStreamSynchronize(c->stream);
+    for (auto& e : c->events) {
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e.a, e.b);
+        c->tcount[e.kclass]++;
+        c->tms[e.kclass] += ms;
+    }
+    c->events.clear();
+}
+
+extern "C" int reg_kernel_timing(reg_ctx* c, int enable) {
+    CTX_CHECK(c);
+    drain_events(c);
+    for (int k = 0; k < KC_COUNT; ++k) { c->tcount[k] = 0; c->tms[k] = 0.0; }
+    c->timing = enable != 0;
+    return REG_OK;
+}
+
+extern "C" int reg_kernel_time(reg_ctx* c, int kclass, long long* launches, double* ms) {
+    CTX_CHECK(c);
+    if (kclass < 0 || kclass >= KC_COUNT) return reg_fail(REG_ERR_ARG, "bad kernel class");
+    drain_events(c);
+    if (launches) *launches = c->tcount[kclass];
+    if (ms) *ms = c->tms[kclass];
+    return REG_OK;
+}
+
+extern "C" long long reg_launch_count(reg_ctx* c) { return c ? c->launches : 0; }

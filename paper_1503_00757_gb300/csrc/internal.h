@@ -1,0 +1,170 @@
+// Internal declarations shared by kernels.cu (device code and launchers) and
+// api.cu (C ABI and Newton-Krylov orchestration).
+#pragma once
+#include <cuda_runtime.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/reg.h"
+
+// Spectral operations applied by the column-pass kernel (per wavenumber k):
+enum SpecOp {
+    OP_GRAD = 0,     // 1 in -> 2 out: (i k1~ x, i k2~ x)
+    OP_DIV = 1,      // 2 in -> 1 out: i k1~ x0 + i k2~ x1
+    OP_REG = 2,      // 2 in -> 2 out: coefA A^(k) x
+    OP_PROJ = 3,     // 2 in -> 2 out: K^(k) x
+    OP_PRECOND = 4,  // 2 in -> 2 out: x / (beta_v A'^(k)), A'(0) = 1
+    OP_ASSEMBLE = 5, // 4 in -> 2 out: coefA A^(k) x01 + K^(k) x23
+    OP_ENERGY = 6,   // 2 in -> 0 out: FP64 sum of the quadratic regularization energy
+    OP_DIVT_PROJ = 7 // 5 in -> 2 out: P_L(coefA * div(T) + b), T = (T11, T12, T22)
+};
+
+// Projection modes (Eq. (e:project-body-force)):
+enum ProjMode { PROJ_IDENTITY = 0, PROJ_LERAY = 1, PROJ_MASS = 2 };
+
+struct SpecParams {
+    float scale;    // 1 / (n1 n2)
+    float coefA;    // coefficient of A^ (beta_v for the gradient/Hessian)
+    float beta_v;   // regularization weight
+    float beta_w;   // mass-source weight (PROJ_MASS)
+    int regnorm;    // 1 = H1, 2 = H2
+    int pmode;      // ProjMode
+    double escale;  // OP_ENERGY: h1 h2 / (n1 n2)
+    double ebv;     // OP_ENERGY: beta_v / 2
+    double ebw;     // OP_ENERGY: beta_w / 2 (0 unless PROJ_MASS)
+};
+
+enum KClass { KC_COL = 0, KC_ROWSTAGE = 1, KC_ROW = 2, KC_POINT = 3, KC_COUNT = 4 };
+
+// Device-scalar slots (doubles) in reg_ctx::d_scal.
+enum Slot {
+    SL_JDATA = 0, SL_JREG = 1, SL_DOT0 = 2, SL_DOT1 = 3, SL_DOT2 = 4, SL_RZ = 5, SL_SHS = 6,
+    SL_RZNEW = 7, SL_RNORM2 = 8, SL_VMAX = 9, SL_GNORM2 = 10, SL_GV = 11,
+    SL_DET0 = 12, /* 5 slots */ SL_COUNT = 20
+};
+
+struct EventPair { cudaEvent_t a, b; int kclass; };
+
+struct reg_ctx {
+    int n1, n2, N, log1, log2;
+    int nt;          // requested nt
+    int nt_cap;      // history capacity
+    int regnorm;
+    double beta_v, beta_w, shear, nu;
+    int pmode;
+    bool shear_model;
+    cudaStream_t stream;
+
+    // images and history
+    float *mT, *mR;
+    float *m_hist;   // (nt_cap + 1) * N
+    float *gm_hist;  // (nt_cap + 1) * 2N
+    // linearization point
+    float* v_lin;    // 2N
+    int nt_lin;
+    bool have_lin;
+    // shear-model linearization data: E(v) (3 planes) and eta (1 plane)
+    float *E_lin, *eta_lin;
+
+    // spectra (transposed packed layout, N/2 float2 each)
+    float2 *S[6];
+    // scalar work fields
+    float *w0, *w1, *w2, *w3;
+    // vector work fields (2N each)
+    float *bvec, *vtmp, *vtmp2, *gtmp, *T3;  // T3: 3 planes
+    // PCG / solve workspace (2N each)
+    float *g, *r, *z, *s, *Hs, *vt, *vtrial;
+    // det F workspace
+    float *F, *Fs, *gF, *gv;  // 4N, 4N, 8N, 4N
+
+    double* d_scal;  // SL_COUNT
+    double* d_part;  // partial sums
+    int npart;
+    double* h_scal;  // pinned host mirror
+
+    float2* tw;      // twiddle table (REG_TW_N entries)
+
+    long long launches;
+    bool timing;
+    std::vector<EventPair> events;
+    std::vector<cudaEvent_t> event_pool;
+    long long tcount[KC_COUNT];
+    double tms[KC_COUNT];
+};
+
+// ---- launchers (kernels.cu); all asynchronous on ctx->stream ----
+cudaError_t k_init_twiddles(reg_ctx* ctx);
+
+void launch_r2c_scalar(reg_ctx* ctx, const float* f, float2* S);
+void launch_r2c_vec(reg_ctx* ctx, const float* u1, const float* u2, float2* S1, float2* S2);
+void launch_c2r_scalar(reg_ctx* ctx, const float2* S, float* f);
+void launch_c2r_vec(reg_ctx* ctx, const float2* S1, const float2* S2, float* u1, float* u2);
+void launch_col(reg_ctx* ctx, int op, const float2* const* in, float2* const* out, const SpecParams& P,
+                double* part_out);
+
+struct AdvArgs {
+    const float2 *G1, *G2;  // spectra of d1 u_s, d2 u_s; G1 == nullptr -> zero gradient
+    const float *uj, *us;   // u_j and the stage-2 input u* (stage 1: us unused)
+    const float* v;         // velocity (2N)
+    const float* gm;        // grad m at the source time (2N); nullptr -> no source
+    const float* vt;        // incremental velocity (2N)
+    float* u_out;           // stage result
+    float* grad_out;        // nullable: receives grad u_s (2N)
+    float2* S_out;          // nullable: packed spectrum of u_out
+    float h;
+    int stage;
+};
+void launch_row_adv(reg_ctx* ctx, const AdvArgs& a);
+
+struct AdjArgs {
+    const float2* D;        // spectrum of div(lam_s v)
+    const float *lj, *ls;   // lam_j, stage-2 input lam*
+    const float* v;
+    float* l_out;
+    float* b;               // nullable: body force accumulator (2N), stage 2 only
+    const float* gm;        // grad m at the output time
+    float w;                // trapezoid weight
+    float2 *F1, *F2;        // nullable: flux spectra of l_out
+    float h;
+    int stage;
+};
+void launch_row_adj(reg_ctx* ctx, const AdjArgs& a);
+
+// lam = ca * a + cb * c (a nullable); b = w lam gm; flux spectra of lam v;
+// optional FP64 partials of 0.5 * sum(lam^2) * h1 h2.
+void launch_adj_init(reg_ctx* ctx, const float* a, float ca, const float* c, float cb, const float* v,
+                     float* lam, float* b, const float* gm, float w, float2* F1, float2* F2, double* part);
+
+// ---- pointwise / reductions ----
+// part[...] <- partial sums of sum_i x_i y_i over n elements; returns #partials
+int launch_dot_partial(reg_ctx* ctx, const float* x, const float* y, long long n, double* part);
+int launch_maxnorm_partial(reg_ctx* ctx, const float* v, int N, double* part);
+// out[slot] = scale * sum(part[0..np)) (+ out[slot] if accumulate); op 0 = sum, 1 = max, 2 = min
+void launch_finalize(reg_ctx* ctx, const double* part, int np, double* out, double scale, int accumulate, int op);
+// y = a * x + b * y, with optional device-scalar factor: if (num >= 0) a *= d_scal[num] / d_scal[den]
+void launch_axpby(reg_ctx* ctx, long long n, float a, const float* x, float b, float* y, int num, int den,
+                  float* out);
+// PCG step: vt += kappa s; r -= kappa Hs; partial sum r^2; kappa = d_scal[SL_RZ] / d_scal[SL_SHS]
+int launch_pcg_update(reg_ctx* ctx, long long n, float* vt, const float* s, float* r, const float* Hs, double* part);
+// s = z + (d_scal[SL_RZNEW] / d_scal[SL_RZ]) s
+void launch_pcg_dir(reg_ctx* ctx, long long n, const float* z, float* s);
+void launch_fill(reg_ctx* ctx, long long n, float* y, float val);
+
+// deformation gradient
+void launch_defgrad_stage(reg_ctx* ctx, int stage, const float* F, const float* Fs, const float* gF,
+                          const float* gv, const float* v, float h, float* out);
+int launch_det_stats(reg_ctx* ctx, const float* F, float* detF, double* part);
+
+// shear model
+// from grad v (gv: d1v1, d2v1, d1v2, d2v2) compute E (3 planes) and eta; and
+// optionally T = 2 eta E (3 planes) and energy partials
+int launch_shear_strain(reg_ctx* ctx, const float* gv, float nu, float* E, float* eta, float* T, double* part);
+// T' = 2 eta (E~ + q E), q = ((1-nu)/nu) (E : E~) / (E:E + eps^2), E~ from grad v~
+void launch_shear_second(reg_ctx* ctx, const float* gvt, const float* E, const float* eta, float nu, float* T);
+
+// timing hooks
+void ktimer_begin(reg_ctx* ctx, int kclass);
+void ktimer_end(reg_ctx* ctx);
+
+int reg_fail(int status, const std::string& msg);

@@ -1,0 +1,216 @@
+"""GPU (CUDA, via the C ABI) vs FP64 oracle parity, element by element.
+
+Tolerances: operator applications (spectral operators, objective, reduced
+gradient, Gauss-Newton matvec) <= 1e-5 relative L2 in FP32; the end-to-end
+solve <= 1e-3 relative in v and in the mismatch."""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import spectral as S
+from oracle import transport as T
+from oracle.registration import Registration
+from paper_1503_00757_gb300 import synth
+
+from .gpu_util import make_ctx, rel_l2, to_gpu, to_np
+
+pytestmark = pytest.mark.gpu
+
+OP_TOL = 1e-5
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1503_00757_gb300.binding import lib
+    lib()
+
+
+def _field(n1, n2, seed, kmax=None):
+    rng = np.random.default_rng(seed)
+    kmax = kmax or min(n1, n2) // 4
+    return synth.smooth_field(n1, n2, kmax, rng, decay=0.5) + 0.01 * rng.standard_normal((n1, n2))
+
+
+GRIDS = [(16, 16), (64, 128), (128, 32), (256, 256)]
+
+
+@pytest.mark.parametrize("n1,n2", GRIDS + [(1024, 1024)])
+def test_spectral_grad_div(n1, n2):
+    import torch
+    ctx = make_ctx(n1, n2, 2)
+    f = _field(n1, n2, 1)
+    u = np.stack([_field(n1, n2, 2), _field(n1, n2, 3)])
+    g = torch.empty(2, n1, n2, device="cuda")
+    ctx.spectral_grad(to_gpu(f), g)
+    d = torch.empty(n1, n2, device="cuda")
+    ctx.spectral_div(to_gpu(u), d)
+    assert rel_l2(to_np(g), S.grad(f)) < OP_TOL
+    assert rel_l2(to_np(d), S.div(u)) < OP_TOL
+
+
+@pytest.mark.parametrize("n1,n2", GRIDS)
+@pytest.mark.parametrize("regnorm,gamma", [(1, math.inf), (2, 0.0), (1, 1e-3), (2, 1e-3)])
+def test_spectral_reg_proj_precond(n1, n2, regnorm, gamma):
+    import torch
+    beta = 1e-3
+    ctx = make_ctx(n1, n2, 2, regnorm=regnorm, beta=beta, gamma=gamma)
+    u = np.stack([_field(n1, n2, 4), _field(n1, n2, 5)])
+    out = torch.empty(2, n1, n2, device="cuda")
+    ctx.apply_reg(to_gpu(u), out)
+    assert rel_l2(to_np(out), beta * S.apply_A(u, regnorm)) < OP_TOL
+    ctx.apply_proj(to_gpu(u), out)
+    assert rel_l2(to_np(out), S.apply_K(u, regnorm, beta, gamma)) < OP_TOL
+    ctx.apply_precond(to_gpu(u), out)
+    assert rel_l2(to_np(out), S.apply_precond(u, regnorm, beta)) < OP_TOL
+
+
+CASES = [
+    # n1, n2, nt, regnorm, beta_v, beta_w, pair
+    (64, 64, 4, 1, 1e-2, math.inf, "blobs"),
+    (64, 64, 4, 2, 1e-2, 0.0, "blobs"),
+    (64, 128, 8, 1, 1e-3, 1e-3, "blobs"),
+    (128, 64, 8, 2, 1e-3, 1e-3, "labels"),
+    (128, 128, 16, 1, 1e-3, math.inf, "ellipses"),
+]
+
+
+def _pair(kind, n1, n2, seed):
+    if kind == "blobs":
+        mT, mR, vs = synth.blobs_pair(max(n1, n2), seed)
+    elif kind == "labels":
+        mT, mR, vs = synth.labels_pair(max(n1, n2), seed, vmax=0.3)
+    else:
+        mT, mR, vs = synth.ellipses_pair(max(n1, n2), seed, vmax=0.2)
+    # non-square grids subsample the square periodic images (they stay periodic and smooth)
+    return _resample(mT, n1, n2), _resample(mR, n1, n2), _resample_v(vs, n1, n2)
+
+
+def _resample(f, n1, n2):
+    n = f.shape[0]
+    return f[:: n // n1, :: n // n2] if (n1, n2) != f.shape else f
+
+
+def _resample_v(v, n1, n2):
+    return np.stack([_resample(v[0], n1, n2), _resample(v[1], n1, n2)])
+
+
+@pytest.mark.parametrize("case", CASES)
+def test_objective_gradient_matvec(case):
+    import torch
+    n1, n2, nt, regnorm, bv, bw, kind = case
+    mT, mR, vs = _pair(kind, n1, n2, 2000)
+    v = 0.5 * vs
+    vt = synth.velocity(n1, n2, min(n1, n2) // 8, 0.3, np.random.default_rng(7), grad_fraction=0.5)
+    P = Registration(mT, mR, nt, regnorm=regnorm, beta_v=bv, beta_w=bw)
+    ctx = make_ctx(n1, n2, nt, regnorm=regnorm, beta=bv, gamma=bw)
+    ctx.set_images(to_gpu(mT), to_gpu(mR))
+    m1 = torch.empty(n1, n2, device="cuda")
+    J = ctx.objective(to_gpu(v), m1)
+    J_ref, m_ref = P.objective(v)
+    assert rel_l2(to_np(m1), m_ref[-1]) < OP_TOL
+    assert abs(J - J_ref) < OP_TOL * abs(J_ref)
+    g = torch.empty(2, n1, n2, device="cuda")
+    Jg = ctx.gradient(to_gpu(v), g)
+    g_ref, _ = P.gradient(v)
+    assert abs(Jg - J_ref) < OP_TOL * abs(J_ref)
+    assert rel_l2(to_np(g), g_ref) < OP_TOL
+    Hv = torch.empty(2, n1, n2, device="cuda")
+    ctx.hessian_matvec(to_gpu(vt), Hv)
+    Hv_ref = P.matvec(vt)
+    assert rel_l2(to_np(Hv), Hv_ref) < OP_TOL
+    ctx.close()
+
+
+def test_degenerate_cases():
+    import torch
+    n = 16
+    # constant images: no image force, g = beta_v A v exactly; zero velocity keeps m_T
+    c = np.full((n, n), 0.25)
+    ctx = make_ctx(n, n, 1, regnorm=1, beta=0.05, gamma=0.0)
+    ctx.set_images(to_gpu(c), to_gpu(c))
+    v = synth.velocity(n, n, 3, 0.4, np.random.default_rng(1), grad_fraction=1.0)
+    g = torch.empty(2, n, n, device="cuda")
+    J = ctx.gradient(to_gpu(v), g)
+    assert rel_l2(to_np(g), 0.05 * S.apply_A(v, 1)) < OP_TOL
+    m1 = torch.empty(n, n, device="cuda")
+    ctx.objective(torch.zeros(2, n, n, device="cuda"), m1)
+    assert np.abs(to_np(m1) - 0.25).max() < 1e-7
+    assert J > 0
+    ctx.close()
+
+
+def test_matvec_before_gradient_is_state_error():
+    import torch
+    from paper_1503_00757_gb300.binding import RegError
+    ctx = make_ctx(16, 16, 2)
+    with pytest.raises(RegError) as e:
+        ctx.hessian_matvec(torch.zeros(2, 16, 16, device="cuda"), torch.zeros(2, 16, 16, device="cuda"))
+    assert e.value.status == 9
+    ctx.close()
+
+
+@pytest.mark.parametrize("n,nt", [(32, 4), (64, 8)])
+def test_detgrad(n, nt):
+    import torch
+    vv = synth.velocity(n, n, 4, 0.5, np.random.default_rng(3), grad_fraction=0.5)
+    ctx = make_ctx(n, n, nt)
+    det = torch.empty(n, n, device="cuda")
+    st = ctx.detgrad(to_gpu(vv), det)
+    F1 = T.defgrad_solve(vv, nt)
+    det_ref, D_ref = T.defgrad_measures(F1)
+    assert rel_l2(to_np(det), det_ref) < OP_TOL
+    ref = (det_ref.min(), det_ref.mean(), det_ref.max(), D_ref.max(), D_ref.mean())
+    for a, b in zip(st, ref):
+        assert abs(a - b) < 1e-5 * max(1.0, abs(b))
+    # shear flow: det F1 = 1 exactly (Heun exact), D = |cos x2|
+    X1, X2 = S.grid_coords(n, n)
+    vsh = np.stack([np.sin(X2), np.zeros((n, n))])
+    st = ctx.detgrad(to_gpu(vsh), det)
+    assert np.abs(to_np(det) - 1).max() < 1e-5
+    assert abs(st[3] - 1.0) < 1e-5
+    ctx.close()
+
+
+@pytest.mark.parametrize("s", [-0.5, 0.5])
+def test_shear_gradient_matvec(s):
+    import torch
+    n1 = n2 = 64
+    nt = 8
+    mT, mR, vs = synth.blobs_pair(n1, 2001, vmax=0.4, kmax=3)
+    v = 0.5 * vs
+    vt = synth.velocity(n1, n2, 6, 0.3, np.random.default_rng(8))
+    P = Registration(mT, mR, nt, regnorm=1, beta_v=1e-3, beta_w=math.inf, shear=s)
+    ctx = make_ctx(n1, n2, nt, regnorm=1, beta=1e-3, gamma=math.inf, shear=s)
+    ctx.set_images(to_gpu(mT), to_gpu(mR))
+    g = torch.empty(2, n1, n2, device="cuda")
+    J = ctx.gradient(to_gpu(v), g)
+    g_ref, J_ref = P.gradient(v)
+    assert abs(J - J_ref) < OP_TOL * abs(J_ref)
+    assert rel_l2(to_np(g), g_ref) < OP_TOL
+    Hv = torch.empty(2, n1, n2, device="cuda")
+    ctx.hessian_matvec(to_gpu(vt), Hv)
+    assert rel_l2(to_np(Hv), P.matvec(vt)) < OP_TOL
+    ctx.close()
+
+
+@pytest.mark.parametrize("regnorm,gamma,shear", [(1, math.inf, 0.0), (2, 0.0, 0.0), (1, 1e-3, 0.0),
+                                                 (1, math.inf, 0.5)])
+def test_solve_end_to_end(regnorm, gamma, shear):
+    import torch
+    n, nt = 64, 4
+    mT, mR, vs = synth.blobs_pair(n, 1000)
+    P = Registration(mT, mR, nt, regnorm=regnorm, beta_v=1e-2, beta_w=gamma, shear=shear)
+    v_ref, st_ref = P.solve(tol=1e-2)
+    ctx = make_ctx(n, n, nt, regnorm=regnorm, beta=1e-2, gamma=gamma, shear=shear)
+    ctx.set_images(to_gpu(mT), to_gpu(mR))
+    v = torch.zeros(2, n, n, device="cuda")
+    st = ctx.solve(v)
+    assert st["status"] == 0 and st["gnorm_rel"] <= 1e-2
+    assert st["n_newton"] == st_ref["n_newton"]
+    assert rel_l2(to_np(v), v_ref) < 1e-3
+    assert abs(st["rnorm_rel_sq"] - st_ref["rnorm_rel_sq"]) < 1e-3 * st_ref["rnorm_rel_sq"]
+    ctx.close()
