@@ -1,0 +1,324 @@
+"""Benchmark: registrations/s and Gauss-Newton Hessian matvecs/s at 512^2, nt=32.
+
+Workload: synthetic "brain-like" nested smoothed ellipses (5 labels, random
+contrasts), reference = template displaced by a divergence-free velocity with
+modes |k| <= 16 (max |v| = 0.098, CFL 0.25 at nt = 32); H1 seminorm,
+incompressible (div v = 0), beta_v = 1e-3, zero start, relative gradient 1e-2.
+One step = one full Newton-Krylov registration (reg_solve: state, adjoint,
+gradient, PCG with GN matvecs, Armijo, Newton) plus det F1 (reg_detgrad).
+
+Arms:
+  default            the CUDA library through the C ABI (device-resident inputs);
+                     also e2e through reg_register_host with host buffers,
+                     a matvec throughput loop, per-kernel-class timing for the
+                     roofline and the FP64 oracle CPU baseline.
+  --impl reference   the FP64 oracle on the host cores (bounded sample).
+Multi-GPU (torchrun): independent replicas, one registration per rank
+(pairs are independent), value = all ranks' registrations / max time.
+"""
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "registrations/sec and Hessian matvecs/sec at 512² nt=32; warm-start vs plain"
+N_GRID, NT, BETA, SEED, VMAX = 512, 32, 1e-3, 3000, 0.098
+WORKLOAD = ("C3 synthetic brain-like ellipses 512x512, nt=32, H1, beta_v=1e-3, incompressible, "
+            "shear s=0, zero start, tol 1e-2")
+# PDE solves of one registration of this workload as counted by reg_solve
+# (stats n_pde); used to scale the oracle's per-PDE-solve time to a registration.
+PDE_PER_REG_FALLBACK = 200
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def images(seed=SEED):
+    from paper_1503_00757_gb300 import synth
+    mT, mR, _ = synth.ellipses_pair(N_GRID, seed, vmax=VMAX)
+    return mT.astype(np.float32), mR.astype(np.float32)
+
+
+class Clocks:
+    """Samples nvidia-smi clocks and throttle reasons during the timed region."""
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{index}.csv")
+
+    def start(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.f = open(self.path, "w")
+            q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+                 "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+                 "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.close()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[5:9]):
+                if val.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def cpu_oracle_pde_time(mT, mR):
+    """Time one FP64 oracle state solve (one PDE solve) of this workload."""
+    from oracle.transport import state_solve
+    from paper_1503_00757_gb300 import synth
+    v = 0.5 * synth.velocity(N_GRID, N_GRID, 16, VMAX, np.random.default_rng(SEED + 7))
+    t0 = time.perf_counter()
+    state_solve(mT.astype(np.float64), v, NT)
+    return time.perf_counter() - t0
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    mT, mR = images()
+    pde_per_reg = PDE_PER_REG_FALLBACK
+    for _ in range(args.warmup):
+        pass  # the oracle has no warm-up effects worth paying 15 s for
+    times = [cpu_oracle_pde_time(mT, mR) for _ in range(args.steps)]
+    t = float(np.mean(times))
+    value = 1.0 / (t * pde_per_reg)
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "registrations/s",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": t * 1e3, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64", "data": "synthetic", "config": {"workload": WORKLOAD},
+        "cpu_baseline": {"value": value, "unit": "registrations/s", "cores": 1, "kind": "oracle",
+                         "sample": f"one FP64 oracle state solve (512^2, nt=32) per step, scaled by "
+                                   f"{pde_per_reg} PDE solves per registration"},
+        "e2e": {"value": value, "unit": "registrations/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--matvecs", type=int, default=200)
+    ap.add_argument("--profile", action="store_true",
+                    help="run --warmup registrations then one registration and exit (for ncu launch lists)")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+        return
+
+    import torch
+    import torch.distributed as dist
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl", init_method="env://")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+
+    from paper_1503_00757_gb300 import build as libbuild
+    if not os.path.exists(libbuild.LIB_PATH):
+        libbuild.build()
+    from paper_1503_00757_gb300.binding import Context, default_opts
+
+    mT_np, mR_np = images(SEED + rank)
+    mT = torch.from_numpy(mT_np).to(dev)
+    mR = torch.from_numpy(mR_np).to(dev)
+    stream = torch.cuda.Stream(device=dev)
+    ctx = Context(N_GRID, N_GRID, NT, regnorm=1, beta=BETA, gamma=math.inf, shear=0.0, stream=stream)
+    v = torch.zeros(2, N_GRID, N_GRID, device=dev)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)  # > 129 MB L2
+    opts = default_opts(tol=1e-2)
+    stats = {}
+
+    def step():
+        ctx.set_images(mT, mR)
+        st = ctx.solve(v, opts)
+        det = ctx.detgrad(v)
+        return st, det
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    if args.profile:
+        with torch.cuda.stream(stream):
+            for _ in range(args.warmup):
+                step()
+            torch.cuda.synchronize()
+            l0 = ctx.launch_count()
+            st, _ = step()
+            torch.cuda.synchronize()
+        print(json.dumps({"profile": True, "launches_warmup": l0, "launches_step": ctx.launch_count() - l0,
+                          "solve": {k: st[k] for k in ("n_newton", "n_mv", "n_pde", "n_ls")}}))
+        ctx.close()
+        return
+
+    with torch.cuda.stream(stream):
+        for _ in range(args.warmup):
+            stats, det = step()
+        torch.cuda.synchronize()
+        barrier()
+        torch.cuda.synchronize()
+        clocks = Clocks(local)
+        clocks.start()
+        l0 = ctx.launch_count()
+        total_ms = 0.0
+        for _ in range(args.steps):
+            flush.fill_(1.0)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            stats, det = step()
+            e1.record(stream)
+            e1.synchronize()
+            total_ms += e0.elapsed_time(e1)
+        torch.cuda.synchronize()
+        barrier()
+        torch.cuda.synchronize()
+        clk = clocks.stop()
+        launches = ctx.launch_count() - l0
+        ms_step = total_ms / args.steps
+        t = torch.tensor([ms_step], device=dev, dtype=torch.float64)
+        if world > 1:
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_step = float(t.item())
+        value = world * 1e3 / ms_step
+
+        # e2e: same registration from pinned host buffers through reg_register_host
+        hT = torch.from_numpy(mT_np).pin_memory()
+        hR = torch.from_numpy(mR_np).pin_memory()
+        hv = torch.zeros(2 * N_GRID * N_GRID, dtype=torch.float32).pin_memory()
+        torch.cuda.synchronize()
+        e2e_ms = 0.0
+        for _ in range(args.steps):
+            flush.fill_(1.0)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            ctx.register_host(hT, hR, hv, opts)
+            ctx.detgrad(v)
+            torch.cuda.synchronize()
+            e2e_ms += (time.perf_counter() - t0) * 1e3
+        e2e_ms /= args.steps
+        et = torch.tensor([e2e_ms], device=dev, dtype=torch.float64)
+        if world > 1:
+            dist.all_reduce(et, op=dist.ReduceOp.MAX)
+        e2e_value = world * 1e3 / float(et.item())
+
+        # Hessian matvec throughput at a fixed linearization point (the converged v)
+        g = torch.empty_like(v)
+        ctx.gradient(v, g)
+        vt = torch.randn_like(v)
+        Hv = torch.empty_like(v)
+        for _ in range(5):
+            ctx.hessian_matvec(vt, Hv)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.matvecs):
+            ctx.hessian_matvec(vt, Hv)
+        e1.record(stream)
+        e1.synchronize()
+        mv_ms = e0.elapsed_time(e1) / args.matvecs
+
+        # roofline: per-kernel-class CUDA-event timing over one more registration
+        ctx.kernel_timing(True)
+        ctx.set_images(mT, mR)
+        ctx.solve(v, opts)
+        torch.cuda.synchronize()
+        classes = {}
+        names = ["column FFT + multiplier", "row FFT + RK2 stage", "row FFT (other)", "pointwise/reduction"]
+        for kc in range(4):
+            n, ms, byt = ctx.kernel_time(kc)
+            classes[kc] = (n, ms, byt)
+        ctx.kernel_timing(False)
+    dom = max(classes, key=lambda k: classes[k][1])
+    n_dom, ms_dom, bytes_dom = classes[dom]
+    peak, peak_kind = peaks()
+    achieved = (bytes_dom / (ms_dom * 1e-3)) / 1e9 if ms_dom > 0 else 0.0
+
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        t_pde = cpu_oracle_pde_time(mT_np, mR_np)
+        n_pde = stats.get("n_pde", PDE_PER_REG_FALLBACK)
+        cpu = {"value": 1.0 / (t_pde * n_pde), "unit": "registrations/s", "cores": 1, "kind": "oracle",
+               "sample": f"one FP64 oracle state solve (512^2, nt=32) = {t_pde:.1f} s, scaled by the "
+                         f"{n_pde} PDE solves of the GPU registration"}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": "registrations/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "grid": [N_GRID, N_GRID], "nt": NT, "l2": "flushed between steps",
+                       "parallelism": f"replicas x{world}", "start": "zero (plain); warm start not built"},
+            "matvec_per_s": 1e3 / mv_ms, "ms_per_matvec": mv_ms,
+            "solve": {k: stats[k] for k in ("n_newton", "n_mv", "n_pde", "n_ls", "gnorm_rel", "rnorm_rel_sq", "status")},
+            "detF": {"min": det[0], "mean": det[1], "max": det[2], "maxD": det[3]},
+            "e2e": {"value": e2e_value, "unit": "registrations/s", "h2d_bytes_per_step": 2 * 4 * N_GRID * N_GRID,
+                    "d2h_bytes_per_step": 2 * 4 * N_GRID * N_GRID + 5 * 8},
+            "gpu_launches": launches,
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "traffic": None, "kernel": names[dom],
+                         "launches": n_dom, "ms": ms_dom, "peak_kind": peak_kind},
+            "kernel_classes": {names[k]: {"launches": classes[k][0], "ms": classes[k][1],
+                                          "GB": classes[k][2] / 1e9} for k in classes},
+            "clocks": clk,
+            "cpu_baseline": cpu,
+        }
+        print(json.dumps(line))
+    ctx.close()
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

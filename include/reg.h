@@ -174,12 +174,15 @@ int reg_detgrad(reg_ctx* ctx, const float* v, float* detF, double* stats);
 /* ---- instrumentation ---- */
 
 /* Per-kernel-class CUDA-event timing (off by default).  While enabled, every
- * launch of a kernel of class `kclass` is bracketed by events on the context
- * stream.  reg_kernel_time returns the launch count and summed milliseconds
- * since the last enable.  Classes: 0 column FFT kernels, 1 row stage kernels
- * (advection/adjoint), 2 other row kernels, 3 pointwise/reduction kernels. */
+ * kernel launch is bracketed by events on the context stream.
+ * reg_kernel_time returns, for class `kclass`, the launch count, the summed
+ * milliseconds and the summed algorithmic bytes (every input read once and
+ * every output written once) since the last enable (host pointers, each
+ * nullable).  Classes: 0 column FFT + multiplier kernels, 1 row FFT + RK2
+ * stage kernels (advection / adjoint), 2 other row FFT kernels,
+ * 3 pointwise / reduction kernels. */
 int reg_kernel_timing(reg_ctx* ctx, int enable);
-int reg_kernel_time(reg_ctx* ctx, int kclass, long long* launches, double* ms);
+int reg_kernel_time(reg_ctx* ctx, int kclass, long long* launches, double* ms, double* bytes);
 /* Number of kernels this context has launched since creation. */
 long long reg_launch_count(reg_ctx* ctx);
 

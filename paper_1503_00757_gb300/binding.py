@@ -62,7 +62,7 @@ _SIGS = {
     "reg_register_host": ([_P, _P, _P, _P, ctypes.POINTER(reg_solve_opts), ctypes.POINTER(reg_solve_stats)], _I),
     "reg_detgrad": ([_P, _P, _P, ctypes.POINTER(_D)], _I),
     "reg_kernel_timing": ([_P, _I], _I),
-    "reg_kernel_time": ([_P, _I, ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(_D)], _I),
+    "reg_kernel_time": ([_P, _I, ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(_D), ctypes.POINTER(_D)], _I),
     "reg_launch_count": ([_P], ctypes.c_longlong),
 }
 
@@ -223,10 +223,12 @@ class Context:
         _check(lib().reg_kernel_timing(self.h, int(enable)))
 
     def kernel_time(self, kclass):
+        """(launches, milliseconds, algorithmic bytes) of kernel class kclass since timing was enabled."""
         n = ctypes.c_longlong()
         ms = ctypes.c_double()
-        _check(lib().reg_kernel_time(self.h, kclass, ctypes.byref(n), ctypes.byref(ms)))
-        return n.value, ms.value
+        by = ctypes.c_double()
+        _check(lib().reg_kernel_time(self.h, kclass, ctypes.byref(n), ctypes.byref(ms), ctypes.byref(by)))
+        return n.value, ms.value, by.value
 
     def launch_count(self):
         return lib().reg_launch_count(self.h)

@@ -132,7 +132,7 @@ extern "C" int reg_create(reg_grid grid, int nt, int regnorm, double beta, doubl
     c->have_lin = false;
     c->launches = 0;
     c->timing = false;
-    for (int k = 0; k < KC_COUNT; ++k) { c->tcount[k] = 0; c->tms[k] = 0.0; }
+    for (int k = 0; k < KC_COUNT; ++k) { c->tcount[k] = 0; c->tms[k] = 0.0; c->tbytes[k] = 0.0; }
 
     const size_t N = c->N;
     bool ok = true;
@@ -762,6 +762,7 @@ static void drain_events(reg_ctx* c) {
         cudaEventElapsedTime(&ms, e.a, e.b);
         c->tcount[e.kclass]++;
         c->tms[e.kclass] += ms;
+        c->tbytes[e.kclass] += e.bytes;
     }
     c->events.clear();
 }
@@ -769,17 +770,18 @@ static void drain_events(reg_ctx* c) {
 extern "C" int reg_kernel_timing(reg_ctx* c, int enable) {
     CTX_CHECK(c);
     drain_events(c);
-    for (int k = 0; k < KC_COUNT; ++k) { c->tcount[k] = 0; c->tms[k] = 0.0; }
+    for (int k = 0; k < KC_COUNT; ++k) { c->tcount[k] = 0; c->tms[k] = 0.0; c->tbytes[k] = 0.0; }
     c->timing = enable != 0;
     return REG_OK;
 }
 
-extern "C" int reg_kernel_time(reg_ctx* c, int kclass, long long* launches, double* ms) {
+extern "C" int reg_kernel_time(reg_ctx* c, int kclass, long long* launches, double* ms, double* bytes) {
     CTX_CHECK(c);
     if (kclass < 0 || kclass >= KC_COUNT) return reg_fail(REG_ERR_ARG, "bad kernel class");
     drain_events(c);
     if (launches) *launches = c->tcount[kclass];
     if (ms) *ms = c->tms[kclass];
+    if (bytes) *bytes = c->tbytes[kclass];
     return REG_OK;
 }
 

@@ -44,7 +44,7 @@ enum Slot {
     SL_DET0 = 12, /* 5 slots */ SL_COUNT = 20
 };
 
-struct EventPair { cudaEvent_t a, b; int kclass; };
+struct EventPair { cudaEvent_t a, b; int kclass; double bytes; };
 
 struct reg_ctx {
     int n1, n2, N, log1, log2;
@@ -91,6 +91,7 @@ struct reg_ctx {
     std::vector<cudaEvent_t> event_pool;
     long long tcount[KC_COUNT];
     double tms[KC_COUNT];
+    double tbytes[KC_COUNT];
 };
 
 // ---- launchers (kernels.cu); all asynchronous on ctx->stream ----
@@ -164,7 +165,8 @@ int launch_shear_strain(reg_ctx* ctx, const float* gv, float nu, float* E, float
 void launch_shear_second(reg_ctx* ctx, const float* gvt, const float* E, const float* eta, float nu, float* T);
 
 // timing hooks
-void ktimer_begin(reg_ctx* ctx, int kclass);
+// bytes: algorithmic bytes of the launch (each input read once, each output written once)
+void ktimer_begin(reg_ctx* ctx, int kclass, double bytes);
 void ktimer_end(reg_ctx* ctx);
 
 int reg_fail(int status, const std::string& msg);

@@ -25,7 +25,7 @@
 // ---------------------------------------------------------------------------
 // timing hooks
 // ---------------------------------------------------------------------------
-void ktimer_begin(reg_ctx* ctx, int kclass) {
+void ktimer_begin(reg_ctx* ctx, int kclass, double bytes) {
     ctx->launches++;
     if (!ctx->timing) return;
     EventPair ep;
@@ -38,6 +38,7 @@ void ktimer_begin(reg_ctx* ctx, int kclass) {
     ep.a = ctx->event_pool[need - 2];
     ep.b = ctx->event_pool[need - 1];
     ep.kclass = kclass;
+    ep.bytes = bytes;
     cudaEventRecord(ep.a, ctx->stream);
     ctx->events.push_back(ep);
 }
@@ -514,7 +515,7 @@ static void set_smem(K kern, size_t bytes) {
 void launch_r2c_scalar(reg_ctx* ctx, const float* f, float2* S) {
     const int L = ctx->n2, R = rows_per_cta(ctx->n1, L);
     const size_t smem = 2 * (size_t)R * L * sizeof(float2);
-    ktimer_begin(ctx, KC_ROW);
+    ktimer_begin(ctx, KC_ROW, 8.0 * ctx->N);
     DISPATCH_LOG(ctx->log2, {
         auto kern = k_r2c<LG, false>;
         set_smem(kern, smem);
@@ -526,7 +527,7 @@ void launch_r2c_scalar(reg_ctx* ctx, const float* f, float2* S) {
 void launch_r2c_vec(reg_ctx* ctx, const float* u1, const float* u2, float2* S1, float2* S2) {
     const int L = ctx->n2, R = rows_per_cta(ctx->n1, L);
     const size_t smem = 2 * (size_t)R * L * sizeof(float2);
-    ktimer_begin(ctx, KC_ROW);
+    ktimer_begin(ctx, KC_ROW, 16.0 * ctx->N);
     DISPATCH_LOG(ctx->log2, {
         auto kern = k_r2c<LG, true>;
         set_smem(kern, smem);
@@ -538,7 +539,7 @@ void launch_r2c_vec(reg_ctx* ctx, const float* u1, const float* u2, float2* S1, 
 void launch_c2r_scalar(reg_ctx* ctx, const float2* S, float* f) {
     const int L = ctx->n2, R = rows_per_cta(ctx->n1, L);
     const size_t smem = 2 * (size_t)R * L * sizeof(float2);
-    ktimer_begin(ctx, KC_ROW);
+    ktimer_begin(ctx, KC_ROW, 8.0 * ctx->N);
     DISPATCH_LOG(ctx->log2, {
         auto kern = k_c2r<LG, false>;
         set_smem(kern, smem);
@@ -550,7 +551,7 @@ void launch_c2r_scalar(reg_ctx* ctx, const float2* S, float* f) {
 void launch_c2r_vec(reg_ctx* ctx, const float2* S1, const float2* S2, float* u1, float* u2) {
     const int L = ctx->n2, R = rows_per_cta(ctx->n1, L);
     const size_t smem = 2 * (size_t)R * L * sizeof(float2);
-    ktimer_begin(ctx, KC_ROW);
+    ktimer_begin(ctx, KC_ROW, 16.0 * ctx->N);
     DISPATCH_LOG(ctx->log2, {
         auto kern = k_c2r<LG, true>;
         set_smem(kern, smem);
@@ -562,7 +563,11 @@ void launch_c2r_vec(reg_ctx* ctx, const float2* S1, const float2* S2, float* u1,
 void launch_row_adv(reg_ctx* ctx, const AdvArgs& a) {
     const int L = ctx->n2, R = rows_per_cta(ctx->n1, L);
     const size_t smem = 2 * (size_t)R * L * sizeof(float2);
-    ktimer_begin(ctx, KC_ROWSTAGE);
+    // floats per node read/written: G 2 (complex half spectra = 1 float per node each), u_j 1,
+    // u* 1 (stage 2), v 2, source gm + v~ 4, u_out 1, grad_out 2, S_out 1
+    double fl = 1 + 2 + 1 + (a.G1 ? 2 : 0) + (a.stage == 2 ? 1 : 0) + (a.gm ? 4 : 0) + (a.grad_out ? 2 : 0) +
+                (a.S_out ? 1 : 0);
+    ktimer_begin(ctx, KC_ROWSTAGE, 4.0 * fl * ctx->N);
     DISPATCH_LOG(ctx->log2, {
         auto kern = k_row_adv<LG>;
         set_smem(kern, smem);
@@ -574,7 +579,9 @@ void launch_row_adv(reg_ctx* ctx, const AdvArgs& a) {
 void launch_row_adj(reg_ctx* ctx, const AdjArgs& a) {
     const int L = ctx->n2, R = rows_per_cta(ctx->n1, L);
     const size_t smem = 2 * (size_t)R * L * sizeof(float2);
-    ktimer_begin(ctx, KC_ROWSTAGE);
+    // D 1, lam_j 1, lam* 1 (stage 2), v 2, l_out 1, body force b read+write 4 and gm 2, flux spectra 2
+    double fl = 1 + 1 + 2 + 1 + (a.stage == 2 ? 1 : 0) + (a.b ? 6 : 0) + (a.F1 ? 2 : 0);
+    ktimer_begin(ctx, KC_ROWSTAGE, 4.0 * fl * ctx->N);
     DISPATCH_LOG(ctx->log2, {
         auto kern = k_row_adj<LG>;
         set_smem(kern, smem);
@@ -587,7 +594,8 @@ void launch_adj_init(reg_ctx* ctx, const float* a, float ca, const float* c, flo
                      float* b, const float* gm, float w, float2* F1, float2* F2, double* part) {
     const int L = ctx->n2, R = rows_per_cta(ctx->n1, L);
     const size_t smem = 2 * (size_t)R * L * sizeof(float2);
-    ktimer_begin(ctx, KC_ROW);
+    // a 1 (optional), c 1, v 2, lam 1, b 2 + gm 2, flux spectra 2
+    ktimer_begin(ctx, KC_ROW, 4.0 * ((a ? 1 : 0) + 1 + 2 + 1 + 4 + 2) * ctx->N);
     DISPATCH_LOG(ctx->log2, {
         auto kern = k_adj_init<LG>;
         set_smem(kern, smem);
@@ -611,7 +619,7 @@ static void launch_col_t(reg_ctx* ctx, const float2* const* in, float2* const* o
     a.part = part;
     a.cpb = cpb;
     a.n2 = ctx->n2;
-    ktimer_begin(ctx, KC_COL);
+    ktimer_begin(ctx, KC_COL, 4.0 * (NIN + NOUT) * ctx->N);
     DISPATCH_LOG(ctx->log1, {
         auto kern = k_col<LG, NIN, NOUT, OP>;
         set_smem(kern, smem);
@@ -652,7 +660,7 @@ __global__ void k_dot_partial(const float* __restrict__ x, const float* __restri
 }
 
 int launch_dot_partial(reg_ctx* ctx, const float* x, const float* y, long long n, double* part) {
-    ktimer_begin(ctx, KC_POINT);
+    ktimer_begin(ctx, KC_POINT, 8.0 * n);
     k_dot_partial<<<NBLK_RED, NTHREADS, 0, ctx->stream>>>(x, y, n, part);
     ktimer_end(ctx);
     return NBLK_RED;
@@ -669,7 +677,7 @@ __global__ void k_maxnorm_partial(const float* __restrict__ v, int N, double* pa
 }
 
 int launch_maxnorm_partial(reg_ctx* ctx, const float* v, int N, double* part) {
-    ktimer_begin(ctx, KC_POINT);
+    ktimer_begin(ctx, KC_POINT, 8.0 * N);
     k_maxnorm_partial<<<NBLK_RED, NTHREADS, 0, ctx->stream>>>(v, N, part);
     ktimer_end(ctx);
     return NBLK_RED;
@@ -684,7 +692,7 @@ __global__ void k_finalize(const double* __restrict__ part, int np, double* out,
 }
 
 void launch_finalize(reg_ctx* ctx, const double* part, int np, double* out, double scale, int accumulate, int op) {
-    ktimer_begin(ctx, KC_POINT);
+    ktimer_begin(ctx, KC_POINT, 8.0 * np);
     if (op == 0) k_finalize<0><<<1, NTHREADS, 0, ctx->stream>>>(part, np, out, scale, accumulate);
     else if (op == 1) k_finalize<1><<<1, NTHREADS, 0, ctx->stream>>>(part, np, out, scale, accumulate);
     else k_finalize<2><<<1, NTHREADS, 0, ctx->stream>>>(part, np, out, scale, accumulate);
@@ -703,7 +711,7 @@ __global__ void k_axpby(long long n, float a, const float* __restrict__ x, float
 }
 
 void launch_axpby(reg_ctx* ctx, long long n, float a, const float* x, float b, float* y, int num, int den, float* out) {
-    ktimer_begin(ctx, KC_POINT);
+    ktimer_begin(ctx, KC_POINT, 4.0 * n * ((a != 0.f) + (b != 0.f) + 1));
     k_axpby<<<NBLK_RED, NTHREADS, 0, ctx->stream>>>(n, a, x, b, y, out ? out : y, ctx->d_scal, num, den);
     ktimer_end(ctx);
 }
@@ -723,7 +731,7 @@ __global__ void k_pcg_update(long long n, float* vt, const float* __restrict__ s
 }
 
 int launch_pcg_update(reg_ctx* ctx, long long n, float* vt, const float* s, float* r, const float* Hs, double* part) {
-    ktimer_begin(ctx, KC_POINT);
+    ktimer_begin(ctx, KC_POINT, 4.0 * n * 6);
     k_pcg_update<<<NBLK_RED, NTHREADS, 0, ctx->stream>>>(n, vt, s, r, Hs, ctx->d_scal, part);
     ktimer_end(ctx);
     return NBLK_RED;
@@ -736,7 +744,7 @@ __global__ void k_pcg_dir(long long n, const float* __restrict__ z, float* s, co
 }
 
 void launch_pcg_dir(reg_ctx* ctx, long long n, const float* z, float* s) {
-    ktimer_begin(ctx, KC_POINT);
+    ktimer_begin(ctx, KC_POINT, 4.0 * n * 3);
     k_pcg_dir<<<NBLK_RED, NTHREADS, 0, ctx->stream>>>(n, z, s, ctx->d_scal);
     ktimer_end(ctx);
 }
@@ -747,7 +755,7 @@ __global__ void k_fill(long long n, float* y, float val) {
 }
 
 void launch_fill(reg_ctx* ctx, long long n, float* y, float val) {
-    ktimer_begin(ctx, KC_POINT);
+    ktimer_begin(ctx, KC_POINT, 4.0 * n);
     k_fill<<<NBLK_RED, NTHREADS, 0, ctx->stream>>>(n, y, val);
     ktimer_end(ctx);
 }
@@ -780,7 +788,7 @@ __global__ void k_defgrad_stage(int N, int stage, const float* __restrict__ F, c
 
 void launch_defgrad_stage(reg_ctx* ctx, int stage, const float* F, const float* Fs, const float* gF, const float* gv,
                           const float* v, float h, float* out) {
-    ktimer_begin(ctx, KC_POINT);
+    ktimer_begin(ctx, KC_POINT, 4.0 * (4 + (stage == 2 ? 4 : 0) + 8 + 4 + 2 + 4) * ctx->N);
     k_defgrad_stage<<<NBLK_RED, NTHREADS, 0, ctx->stream>>>(ctx->N, stage, F, Fs, gF, gv, v, h, out);
     ktimer_end(ctx);
 }
@@ -812,7 +820,7 @@ __global__ void k_det_stats(int N, const float* __restrict__ F, float* detF, dou
 }
 
 int launch_det_stats(reg_ctx* ctx, const float* F, float* detF, double* part) {
-    ktimer_begin(ctx, KC_POINT);
+    ktimer_begin(ctx, KC_POINT, 4.0 * (4 + (detF ? 1 : 0)) * ctx->N);
     k_det_stats<<<NBLK_RED, NTHREADS, 0, ctx->stream>>>(ctx->N, F, detF, part);
     ktimer_end(ctx);
     return NBLK_RED;
@@ -851,7 +859,7 @@ __global__ void k_shear_strain(int N, const float* __restrict__ gv, float nu, fl
 }
 
 int launch_shear_strain(reg_ctx* ctx, const float* gv, float nu, float* E, float* eta, float* T, double* part) {
-    ktimer_begin(ctx, KC_POINT);
+    ktimer_begin(ctx, KC_POINT, 4.0 * (4 + (E ? 3 : 0) + (eta ? 1 : 0) + (T ? 3 : 0)) * ctx->N);
     k_shear_strain<<<NBLK_RED, NTHREADS, 0, ctx->stream>>>(ctx->N, gv, nu, E, eta, T, part);
     ktimer_end(ctx);
     return NBLK_RED;
@@ -875,7 +883,7 @@ __global__ void k_shear_second(int N, const float* __restrict__ gvt, const float
 }
 
 void launch_shear_second(reg_ctx* ctx, const float* gvt, const float* E, const float* eta, float nu, float* T) {
-    ktimer_begin(ctx, KC_POINT);
+    ktimer_begin(ctx, KC_POINT, 4.0 * (4 + 3 + 1 + 3) * ctx->N);
     k_shear_second<<<NBLK_RED, NTHREADS, 0, ctx->stream>>>(ctx->N, gvt, E, eta, nu, T);
     ktimer_end(ctx);
 }

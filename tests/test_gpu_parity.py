@@ -18,6 +18,16 @@ from .gpu_util import make_ctx, rel_l2, to_gpu, to_np
 pytestmark = pytest.mark.gpu
 
 OP_TOL = 1e-5
+U32 = 2.0 ** -24
+
+
+def op_tol(beta_v, regnorm, n1, n2, x, y):
+    """1e-5 plus the FP32 rounding bound of the regularization term: u * beta_v
+    * max A^ * ||x|| / ||y|| (x the operand, y the reference output).  For the
+    H2 seminorm on smooth fields this term dominates: rounding the FP32 inputs
+    alone moves the FP64 result by up to that amount."""
+    Amax = S.reg_symbol(n1, n2, regnorm).max()
+    return OP_TOL + U32 * beta_v * Amax * np.linalg.norm(x) / np.linalg.norm(y)
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -117,11 +127,11 @@ def test_objective_gradient_matvec(case):
     Jg = ctx.gradient(to_gpu(v), g)
     g_ref, _ = P.gradient(v)
     assert abs(Jg - J_ref) < OP_TOL * abs(J_ref)
-    assert rel_l2(to_np(g), g_ref) < OP_TOL
+    assert rel_l2(to_np(g), g_ref) < op_tol(bv, regnorm, n1, n2, v, g_ref)
     Hv = torch.empty(2, n1, n2, device="cuda")
     ctx.hessian_matvec(to_gpu(vt), Hv)
     Hv_ref = P.matvec(vt)
-    assert rel_l2(to_np(Hv), Hv_ref) < OP_TOL
+    assert rel_l2(to_np(Hv), Hv_ref) < op_tol(bv, regnorm, n1, n2, vt, Hv_ref)
     ctx.close()
 
 
@@ -190,10 +200,11 @@ def test_shear_gradient_matvec(s):
     J = ctx.gradient(to_gpu(v), g)
     g_ref, J_ref = P.gradient(v)
     assert abs(J - J_ref) < OP_TOL * abs(J_ref)
-    assert rel_l2(to_np(g), g_ref) < OP_TOL
+    assert rel_l2(to_np(g), g_ref) < op_tol(1e-3, 1, n1, n2, v, g_ref)
     Hv = torch.empty(2, n1, n2, device="cuda")
     ctx.hessian_matvec(to_gpu(vt), Hv)
-    assert rel_l2(to_np(Hv), P.matvec(vt)) < OP_TOL
+    Hv_ref = P.matvec(vt)
+    assert rel_l2(to_np(Hv), Hv_ref) < op_tol(1e-3, 1, n1, n2, vt, Hv_ref)
     ctx.close()
 
 
