@@ -150,6 +150,12 @@ int reg_gradient(reg_ctx* ctx, const float* v, float* g, double* J);
  * last reg_gradient call (REG_ERR_STATE otherwise). */
 int reg_hessian_matvec(reg_ctx* ctx, const float* vt, float* Hvt);
 
+/* Body force of the last reg_gradient (b = int lam grad m dt, Sec. 4.1) or
+ * incremental body force of the last reg_hessian_matvec (b~ with the
+ * Gauss-Newton approximation, Sec. 4.2 / Sec. 5), before the projection K:
+ * b_out (device, 2*n1*n2).  REG_ERR_STATE if neither has run. */
+int reg_body_force(reg_ctx* ctx, float* b_out);
+
 /* ---- rows a12-a13: Newton-Krylov solve (Algorithms 1 and 2) ---- */
 
 /* v_inout (device, 2*n1*n2): initial guess if opts->warm_start, else ignored

@@ -124,6 +124,7 @@ class Registration:
         lt = adjoint_solve(-mt[-1], self.v, nt)
         self.n_pde += 2
         bt = body_force(lt, self.gradm)
+        self.bt = bt
         if self.shear != 0.0:
             return shear_ops.leray(self.beta_v * shear_ops.second_variation(self.v, vt, self.nu) + bt)
         return self.beta_v * apply_A(vt, self.regnorm) + apply_K(bt, self.regnorm, self.beta_v, self.beta_w)

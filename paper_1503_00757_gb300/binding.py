@@ -58,6 +58,7 @@ _SIGS = {
     "reg_objective": ([_P, _P, _P, ctypes.POINTER(_D)], _I),
     "reg_gradient": ([_P, _P, _P, ctypes.POINTER(_D)], _I),
     "reg_hessian_matvec": ([_P, _P, _P], _I),
+    "reg_body_force": ([_P, _P], _I),
     "reg_solve": ([_P, _P, ctypes.POINTER(reg_solve_opts), ctypes.POINTER(reg_solve_stats)], _I),
     "reg_register_host": ([_P, _P, _P, _P, ctypes.POINTER(reg_solve_opts), ctypes.POINTER(reg_solve_stats)], _I),
     "reg_detgrad": ([_P, _P, _P, ctypes.POINTER(_D)], _I),
@@ -174,6 +175,10 @@ class Context:
 
     def hessian_matvec(self, vt, Hvt):
         _check(lib().reg_hessian_matvec(self.h, _ptr(vt, 2 * self.N), _ptr(Hvt, 2 * self.N)))
+
+    def body_force(self, b):
+        """Body force of the last gradient or incremental body force of the last matvec (before K)."""
+        _check(lib().reg_body_force(self.h, _ptr(b, 2 * self.N)))
 
     def solve(self, v, opts=None, check=True):
         """Newton-Krylov solve; v (2, n1, n2) is overwritten.  Returns the stats dict."""

@@ -511,6 +511,14 @@ extern "C" int reg_gradient(reg_ctx* c, const float* v, float* g, double* J) {
     return REG_OK;
 }
 
+extern "C" int reg_body_force(reg_ctx* c, float* b_out) {
+    CTX_CHECK(c);
+    RET(check_ptr(b_out, "b_out"));
+    if (!c->have_lin) return reg_fail(REG_ERR_STATE, "no body force: call reg_gradient first");
+    CK(cudaMemcpyAsync(b_out, c->bvec, sizeof(float) * 2 * c->N, cudaMemcpyDeviceToDevice, c->stream));
+    return REG_OK;
+}
+
 extern "C" int reg_hessian_matvec(reg_ctx* c, const float* vt, float* Hvt) {
     CTX_CHECK(c);
     RET(check_ptr(vt, "vt")); RET(check_ptr(Hvt, "Hvt"));

@@ -5,10 +5,11 @@
 //   * row kernels: one CTA owns R consecutive rows; real FFTs along x^2
 //     (two real rows, or two real fields of one row, per complex FFT), fused
 //     with the pointwise work of an RK2 stage (Sec. 5) on the physical side;
-//   * column kernels: one CTA owns CPB columns of the packed half spectrum
-//     (stored transposed, so a column is contiguous); forward FFT along x^1,
+//   * column kernels: one CTA owns C consecutive columns of the packed half
+//     spectra (row-quad tiled layout, see fft_reg.cuh); forward FFT along x^1,
 //     a Fourier multiplier (gradient, divergence, A, K, preconditioner,
 //     Eq. (e:var-reg-v), (e:project-body-force), Appendix E), inverse FFT.
+// All transforms are register-resident radix-8 FFTs (fft_reg.cuh).
 // Pointwise and reduction kernels serve the PCG (Algorithm 2) and the
 // deformation gradient (Eq. (e:def-grad)); FP64 accumulation for all sums.
 #include <cmath>
@@ -17,6 +18,7 @@
 #include <vector>
 
 #include "fft.cuh"
+#include "fft_reg.cuh"
 #include "internal.h"
 
 #define NTHREADS 256
@@ -70,6 +72,15 @@ __device__ __forceinline__ double red_op(double a, double b) {
 template <int OPR>
 __device__ double block_reduce(double v) {
     __shared__ double red_sm[32];
+    if (blockDim.x < 32) {
+        // a partial warp: no shuffles across lanes that do not exist
+        __syncthreads();
+        red_sm[threadIdx.x] = v;
+        __syncthreads();
+        if (threadIdx.x == 0)
+            for (int i = 1; i < (int)blockDim.x; ++i) v = red_op<OPR>(v, red_sm[i]);
+        return v;  // valid in thread 0
+    }
     for (int o = 16; o > 0; o >>= 1) v = red_op<OPR>(v, __shfl_xor_sync(0xffffffffu, v, o));
     const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
     __syncthreads();
@@ -84,160 +95,174 @@ __device__ double block_reduce(double v) {
 }
 
 // ---------------------------------------------------------------------------
-// packed-spectrum row helpers (transposed layout [L/2][n1])
+// row kernels: real rows <-> packed half spectra along x^2, fused with the
+// pointwise work of the RK2 stages.  A CTA owns R consecutive rows (R a
+// multiple of 4, so its packed spectra form one contiguous tiled chunk of
+// R * L/2 entries starting at row0 * L/2); T = L/8 threads per row FFT.
+// Shared memory: region A (R*L float2: staging) + region X (2*R*L float2:
+// FFT exchange buffers, 2*L per FFT).
 // ---------------------------------------------------------------------------
-// Build full complex spectra of nseq sequences.  pairs_of_rows: sequence sq
-// merges rows row0+2sq (real part) and row0+2sq+1 (imag part) of SA;
-// otherwise it merges row row0+sq of SA (real part) and of SB (imag part).
 template <int LOGL>
-__device__ __forceinline__ void load_merge(float2* buf, int nseq, const float2* __restrict__ SA,
-                                           const float2* __restrict__ SB, int n1, int row0, bool pairs_of_rows) {
-    constexpr int L = 1 << LOGL, H = L >> 1;
-    for (int t = threadIdx.x; t < nseq * H; t += blockDim.x) {
-        const int sq = t % nseq, k = t / nseq;
-        int ra, rb;
-        const float2* pb;
-        if (pairs_of_rows) { ra = row0 + 2 * sq; rb = ra + 1; pb = SA; }
-        else { ra = rb = row0 + sq; pb = SB; }
-        const float2 A = SA[(size_t)k * n1 + ra];
-        const float2 B = pb[(size_t)k * n1 + rb];
-        float2* z = buf + sq * L;
-        if (k == 0) {
-            z[0] = make_float2(A.x, B.x);
-            z[H] = make_float2(A.y, B.y);
-        } else {
-            float2 zk, zm;
-            merge_pair(A, B, zk, zm);
-            z[k] = zk;
-            z[L - k] = zm;
-        }
-    }
-}
-
-template <int LOGL>
-__device__ __forceinline__ void split_store(const float2* buf, int nseq, float2* __restrict__ SA,
-                                            float2* __restrict__ SB, int n1, int row0, bool pairs_of_rows) {
-    constexpr int L = 1 << LOGL, H = L >> 1;
-    for (int t = threadIdx.x; t < nseq * H; t += blockDim.x) {
-        const int sq = t % nseq, k = t / nseq;
-        const float2* z = buf + sq * L;
-        float2 A, B;
-        if (k == 0) {
-            const float2 z0 = z[0], zh = z[H];
-            A = make_float2(z0.x, zh.x);
-            B = make_float2(z0.y, zh.y);
-        } else {
-            split_pair(z[k], z[L - k], A, B);
-        }
-        if (pairs_of_rows) {
-            const int ra = row0 + 2 * sq;
-            SA[(size_t)k * n1 + ra] = A;
-            SA[(size_t)k * n1 + ra + 1] = B;
-        } else {
-            SA[(size_t)k * n1 + row0 + sq] = A;
-            SB[(size_t)k * n1 + row0 + sq] = B;
-        }
-    }
-}
-
-// ---------------------------------------------------------------------------
-// generic row kernels: real <-> packed spectrum along x^2
-// ---------------------------------------------------------------------------
-template <int LOGL, bool VEC>
-__global__ void __launch_bounds__(NTHREADS) k_r2c(const float* __restrict__ f1, const float* __restrict__ f2,
-                                                  float2* S1, float2* S2, int n1, int R, const float2* __restrict__ tw) {
-    extern __shared__ float2 sm[];
-    constexpr int L = 1 << LOGL;
-    float2* A = sm;
-    float2* B = sm + R * L;
-    const int row0 = blockIdx.x * R;
-    const int nseq = VEC ? R : R / 2;
-    for (int t = threadIdx.x; t < R * L; t += blockDim.x) {
-        const int r = t >> LOGL, j = t & (L - 1);
-        const size_t idx = (size_t)(row0 + r) * L + j;
-        if (VEC) {
-            A[r * L + j] = make_float2(f1[idx], f2[idx]);
-        } else {
-            float* a = reinterpret_cast<float*>(A);
-            a[2 * ((r >> 1) * L + j) + (r & 1)] = f1[idx];
-        }
-    }
-    __syncthreads();
-    float2* X = smem_fft<LOGL, false>(A, B, nseq, tw);
-    split_store<LOGL>(X, nseq, S1, VEC ? S2 : S1, n1, row0, !VEC);
+__device__ __forceinline__ void stage_chunk(float2* dst, const float2* __restrict__ src, int n) {
+    const float4* s4 = reinterpret_cast<const float4*>(src);
+    float4* d4 = reinterpret_cast<float4*>(dst);
+    for (int i = threadIdx.x; i < n / 2; i += blockDim.x) d4[i] = s4[i];
 }
 
 template <int LOGL, bool VEC>
-__global__ void __launch_bounds__(NTHREADS) k_c2r(const float2* S1, const float2* S2, float* __restrict__ f1,
-                                                  float* __restrict__ f2, int n1, int R, const float2* __restrict__ tw) {
-    extern __shared__ float2 sm[];
-    constexpr int L = 1 << LOGL;
+__global__ void __launch_bounds__(512) k_r2c(const float* __restrict__ f1, const float* __restrict__ f2,
+                                             float2* S1, float2* S2, int R, const float2* __restrict__ tw) {
+    extern __shared__ __align__(16) float2 sm[];
+    constexpr int L = 1 << LOGL, T = L >> 3, W = L >> 1;
     float2* A = sm;
-    float2* B = sm + R * L;
+    float2* X = sm + R * L;
+    const int q = threadIdx.x / T, t = threadIdx.x - q * T;
     const int row0 = blockIdx.x * R;
-    const int nseq = VEC ? R : R / 2;
-    load_merge<LOGL>(A, nseq, S1, VEC ? S2 : S1, n1, row0, !VEC);
+    const int nfft = VEC ? R : R / 2;
+    const bool active = q < nfft;
+    float2 x[8];
+    if (active) {
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            const int j = t + k * T;
+            if (VEC) {
+                const size_t idx = (size_t)(row0 + q) * L + j;
+                x[k] = make_float2(f1[idx], f2[idx]);
+            } else {
+                const size_t idx = (size_t)(row0 + 2 * q) * L + j;
+                x[k] = make_float2(f1[idx], f1[idx + L]);
+            }
+        }
+    }
+    reg_fft<LOGL, false>(x, t, active, X + 2 * q * L, X + 2 * q * L + L, tw);
+    if (active) {
+#pragma unroll
+        for (int k = 0; k < 8; ++k) A[q * L + t + k * T] = x[k];
+    }
     __syncthreads();
-    float2* X = smem_fft<LOGL, true>(A, B, nseq, tw);
-    for (int t = threadIdx.x; t < R * L; t += blockDim.x) {
-        const int r = t >> LOGL, j = t & (L - 1);
-        const size_t idx = (size_t)(row0 + r) * L + j;
+    const size_t base = (size_t)row0 * W;
+    for (int idx = threadIdx.x; idx < R * W; idx += blockDim.x) {
+        const int r = ((idx / (4 * W)) << 2) | (idx & 3);
+        const int e = (idx >> 2) & (W - 1);
         if (VEC) {
-            const float2 z = X[r * L + j];
-            f1[idx] = z.x;
-            f2[idx] = z.y;
+            S1[base + idx] = split_entry<LOGL>(A + r * L, 0, e);
+            S2[base + idx] = split_entry<LOGL>(A + r * L, 1, e);
         } else {
-            const float* x = reinterpret_cast<const float*>(X);
-            f1[idx] = x[2 * ((r >> 1) * L + j) + (r & 1)];
+            S1[base + idx] = split_entry<LOGL>(A + (r >> 1) * L, r & 1, e);
+        }
+    }
+}
+
+template <int LOGL, bool VEC>
+__global__ void __launch_bounds__(512) k_c2r(const float2* __restrict__ S1, const float2* __restrict__ S2,
+                                             float* __restrict__ f1, float* __restrict__ f2, int R,
+                                             const float2* __restrict__ tw) {
+    extern __shared__ __align__(16) float2 sm[];
+    constexpr int L = 1 << LOGL, T = L >> 3, W = L >> 1;
+    float2* A = sm;
+    float2* X = sm + R * L;
+    const int q = threadIdx.x / T, t = threadIdx.x - q * T;
+    const int row0 = blockIdx.x * R;
+    const size_t base = (size_t)row0 * W;
+    stage_chunk<LOGL>(A, S1 + base, R * W);
+    if (VEC) stage_chunk<LOGL>(A + R * W, S2 + base, R * W);
+    __syncthreads();
+    const int nfft = VEC ? R : R / 2;
+    const bool active = q < nfft;
+    float2 x[8];
+    if (active) {
+#pragma unroll
+        for (int k = 0; k < 8; ++k)
+            x[k] = VEC ? merged_entry<LOGL>(A, q, A + R * W, q, t + k * T)
+                       : merged_entry<LOGL>(A, 2 * q, A, 2 * q + 1, t + k * T);
+    }
+    reg_fft<LOGL, true>(x, t, active, X + 2 * q * L, X + 2 * q * L + L, tw);
+    if (active) {
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            const int j = t + k * T;
+            if (VEC) {
+                const size_t idx = (size_t)(row0 + q) * L + j;
+                f1[idx] = x[k].x;
+                f2[idx] = x[k].y;
+            } else {
+                const size_t idx = (size_t)(row0 + 2 * q) * L + j;
+                f1[idx] = x[k].x;
+                f1[idx + L] = x[k].y;
+            }
         }
     }
 }
 
 // ---------------------------------------------------------------------------
-// RK2 (Heun) advection stage, state and incremental state equations
+// RK2 (Heun) advection stage of the state and incremental state equations
 // (Eq. (e:state-eq-elim), (e:inc-state-eq-elim)):
 //   k = -v . grad u_s - v~ . grad m(t)         (source only for the incremental state)
 //   stage 1: u* = u_j + h k ;  stage 2: u_{j+1} = (u_j + u* + h k) / 2
+// grad u_s arrives as packed spectra (G1, G2) from the column pass; the stage
+// result u_out leaves as its packed spectrum S_out for the next column pass.
 // ---------------------------------------------------------------------------
 template <int LOGL>
-__global__ void __launch_bounds__(NTHREADS) k_row_adv(AdvArgs a, int n1, int N, int R, const float2* __restrict__ tw) {
-    extern __shared__ float2 sm[];
-    constexpr int L = 1 << LOGL;
+__global__ void __launch_bounds__(512) k_row_adv(AdvArgs a, int N, int R, const float2* __restrict__ tw) {
+    extern __shared__ __align__(16) float2 sm[];
+    constexpr int L = 1 << LOGL, T = L >> 3, W = L >> 1;
     float2* A = sm;
-    float2* B = sm + R * L;
+    float2* X = sm + R * L;
+    const int q = threadIdx.x / T, t = threadIdx.x - q * T;
     const int row0 = blockIdx.x * R;
-    float2* X = nullptr;
+    const size_t base = (size_t)row0 * W;
+    float2 x[8];
     if (a.G1) {
-        load_merge<LOGL>(A, R, a.G1, a.G2, n1, row0, false);
+        stage_chunk<LOGL>(A, a.G1 + base, R * W);
+        stage_chunk<LOGL>(A + R * W, a.G2 + base, R * W);
         __syncthreads();
-        X = smem_fft<LOGL, true>(A, B, R, tw);
+#pragma unroll
+        for (int k = 0; k < 8; ++k) x[k] = merged_entry<LOGL>(A, q, A + R * W, q, t + k * T);
+        reg_fft<LOGL, true>(x, t, true, X + 2 * q * L, X + 2 * q * L + L, tw);
+    } else {
+#pragma unroll
+        for (int k = 0; k < 8; ++k) x[k] = make_float2(0.f, 0.f);
     }
-    float2* P = (X == A) ? B : A;  // pack buffer for the forward FFT of u_out
-    float* pk = reinterpret_cast<float*>(P);
-    for (int t = threadIdx.x; t < R * L; t += blockDim.x) {
-        const int r = t >> LOGL, j = t & (L - 1);
-        const size_t idx = (size_t)(row0 + r) * L + j;
-        float d1 = 0.f, d2 = 0.f;
-        if (X) {
-            const float2 g = X[r * L + j];
-            d1 = g.x;
-            d2 = g.y;
-        }
+    float out[8];
+    const size_t rowbase = (size_t)(row0 + q) * L;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+        const size_t idx = rowbase + t + k * T;
+        const float d1 = x[k].x, d2 = x[k].y;
         if (a.grad_out) {
             a.grad_out[idx] = d1;
             a.grad_out[N + idx] = d2;
         }
-        float k = -(a.v[idx] * d1 + a.v[N + idx] * d2);
-        if (a.gm) k -= a.vt[idx] * a.gm[idx] + a.vt[N + idx] * a.gm[N + idx];
+        float kk = -(a.v[idx] * d1 + a.v[N + idx] * d2);
+        if (a.gm) kk -= a.vt[idx] * a.gm[idx] + a.vt[N + idx] * a.gm[N + idx];
         const float uj = a.uj[idx];
-        const float out = (a.stage == 1) ? fmaf(a.h, k, uj) : 0.5f * (uj + a.us[idx] + a.h * k);
-        a.u_out[idx] = out;
-        if (a.S_out) pk[2 * ((r >> 1) * L + j) + (r & 1)] = out;
+        out[k] = (a.stage == 1) ? fmaf(a.h, kk, uj) : 0.5f * (uj + a.us[idx] + a.h * kk);
+        a.u_out[idx] = out[k];
     }
     if (!a.S_out) return;
+    float* O = reinterpret_cast<float*>(A);
+#pragma unroll
+    for (int k = 0; k < 8; ++k) O[q * L + t + k * T] = out[k];
     __syncthreads();
-    float2* Y = smem_fft<LOGL, false>(P, P + (R / 2) * L, R / 2, tw);
-    split_store<LOGL>(Y, R / 2, a.S_out, a.S_out, n1, row0, true);
+    const bool act2 = q < R / 2;
+    if (act2) {
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            const int e = t + k * T;
+            x[k] = make_float2(O[2 * q * L + e], O[(2 * q + 1) * L + e]);
+        }
+    }
+    reg_fft<LOGL, false>(x, t, act2, X + 2 * q * L, X + 2 * q * L + L, tw);
+    if (act2) {
+#pragma unroll
+        for (int k = 0; k < 8; ++k) A[q * L + t + k * T] = x[k];
+    }
+    __syncthreads();
+    for (int idx = threadIdx.x; idx < R * W; idx += blockDim.x) {
+        const int r = ((idx / (4 * W)) << 2) | (idx & 3);
+        const int e = (idx >> 2) & (W - 1);
+        a.S_out[base + idx] = split_entry<LOGL>(A + (r >> 1) * L, r & 1, e);
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -245,24 +270,58 @@ __global__ void __launch_bounds__(NTHREADS) k_row_adv(AdvArgs a, int n1, int N, 
 // time (Eq. (e:adj-eq-elim), (e:inc-adj-eq-elim) without the lambda term):
 //   k = div(lam_s v); stage 1: lam* = lam_j + h k; stage 2: lam_{j-1} = (lam_j + lam* + h k) / 2
 // Stage 2 also accumulates the body force b += w lam_{j-1} grad m_{j-1}
-// (trapezoidal rule, Sec. 4.1 / Sec. 5) and both stages emit the packed
-// spectra of the flux lam_out v for the next divergence.
+// (trapezoidal rule, Sec. 4.1 / Sec. 5); the flux lam_out v leaves as two
+// packed spectra for the next divergence.
 // ---------------------------------------------------------------------------
 template <int LOGL>
-__global__ void __launch_bounds__(NTHREADS) k_row_adj(AdjArgs a, int n1, int N, int R, const float2* __restrict__ tw) {
-    extern __shared__ float2 sm[];
-    constexpr int L = 1 << LOGL;
-    float2* A = sm;
-    float2* B = sm + R * L;
-    const int row0 = blockIdx.x * R;
-    load_merge<LOGL>(A, R / 2, a.D, a.D, n1, row0, true);
+__device__ __forceinline__ void flux_fft_store(float2 (&x)[8], int q, int t, int R, int row0, float2* A, float2* X,
+                                               float2* F1, float2* F2, const float2* __restrict__ tw) {
+    constexpr int L = 1 << LOGL, T = L >> 3, W = L >> 1;
+    reg_fft<LOGL, false>(x, t, true, X + 2 * q * L, X + 2 * q * L + L, tw);
+#pragma unroll
+    for (int k = 0; k < 8; ++k) A[q * L + t + k * T] = x[k];
     __syncthreads();
-    float2* X = smem_fft<LOGL, true>(A, A + (R / 2) * L, R / 2, tw);
-    const float* xd = reinterpret_cast<const float*>(X);
-    for (int t = threadIdx.x; t < R * L; t += blockDim.x) {
-        const int r = t >> LOGL, j = t & (L - 1);
-        const size_t idx = (size_t)(row0 + r) * L + j;
-        const float dv = xd[2 * ((r >> 1) * L + j) + (r & 1)];
+    const size_t base = (size_t)row0 * W;
+    for (int idx = threadIdx.x; idx < R * W; idx += blockDim.x) {
+        const int r = ((idx / (4 * W)) << 2) | (idx & 3);
+        const int e = (idx >> 2) & (W - 1);
+        F1[base + idx] = split_entry<LOGL>(A + r * L, 0, e);
+        F2[base + idx] = split_entry<LOGL>(A + r * L, 1, e);
+    }
+}
+
+template <int LOGL>
+__global__ void __launch_bounds__(512) k_row_adj(AdjArgs a, int N, int R, const float2* __restrict__ tw) {
+    extern __shared__ __align__(16) float2 sm[];
+    constexpr int L = 1 << LOGL, T = L >> 3, W = L >> 1;
+    float2* A = sm;
+    float2* X = sm + R * L;
+    const int q = threadIdx.x / T, t = threadIdx.x - q * T;
+    const int row0 = blockIdx.x * R;
+    stage_chunk<LOGL>(A, a.D + (size_t)row0 * W, R * W);
+    __syncthreads();
+    const bool act1 = q < R / 2;
+    float2 x[8];
+    if (act1) {
+#pragma unroll
+        for (int k = 0; k < 8; ++k) x[k] = merged_entry<LOGL>(A, 2 * q, A, 2 * q + 1, t + k * T);
+    }
+    reg_fft<LOGL, true>(x, t, act1, X + 2 * q * L, X + 2 * q * L + L, tw);
+    float* O = reinterpret_cast<float*>(A);
+    if (act1) {
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            O[2 * q * L + t + k * T] = x[k].x;
+            O[(2 * q + 1) * L + t + k * T] = x[k].y;
+        }
+    }
+    __syncthreads();
+    const size_t rowbase = (size_t)(row0 + q) * L;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+        const int j = t + k * T;
+        const size_t idx = rowbase + j;
+        const float dv = O[q * L + j];
         const float lj = a.lj[idx];
         const float out = (a.stage == 1) ? fmaf(a.h, dv, lj) : 0.5f * (lj + a.ls[idx] + a.h * dv);
         a.l_out[idx] = out;
@@ -271,50 +330,52 @@ __global__ void __launch_bounds__(NTHREADS) k_row_adj(AdjArgs a, int n1, int N, 
             a.b[idx] = fmaf(wl, a.gm[idx], a.b[idx]);
             a.b[N + idx] = fmaf(wl, a.gm[N + idx], a.b[N + idx]);
         }
-        if (a.F1) B[r * L + j] = make_float2(out * a.v[idx], out * a.v[N + idx]);
+        x[k] = make_float2(out * a.v[idx], out * a.v[N + idx]);
     }
     if (!a.F1) return;
-    __syncthreads();
-    float2* Y = smem_fft<LOGL, false>(B, A, R, tw);
-    split_store<LOGL>(Y, R, a.F1, a.F2, n1, row0, false);
+    flux_fft_store<LOGL>(x, q, t, R, row0, A, X, a.F1, a.F2, tw);
 }
 
 // lam = ca*a + cb*c; b = w lam gm; flux spectra; partial 0.5*sum(lam^2)
 template <int LOGL>
-__global__ void __launch_bounds__(NTHREADS) k_adj_init(const float* __restrict__ a, float ca, const float* __restrict__ c,
-                                                       float cb, const float* __restrict__ v, float* lam, float* b,
-                                                       const float* __restrict__ gm, float w, float2* F1, float2* F2,
-                                                       double* part, int n1, int N, int R, const float2* __restrict__ tw) {
-    extern __shared__ float2 sm[];
-    constexpr int L = 1 << LOGL;
+__global__ void __launch_bounds__(512) k_adj_init(const float* __restrict__ a, float ca, const float* __restrict__ c,
+                                                  float cb, const float* __restrict__ v, float* lam, float* b,
+                                                  const float* __restrict__ gm, float w, float2* F1, float2* F2,
+                                                  double* part, int N, int R, const float2* __restrict__ tw) {
+    extern __shared__ __align__(16) float2 sm[];
+    constexpr int L = 1 << LOGL, T = L >> 3;
     float2* A = sm;
-    float2* B = sm + R * L;
+    float2* X = sm + R * L;
+    const int q = threadIdx.x / T, t = threadIdx.x - q * T;
     const int row0 = blockIdx.x * R;
+    const size_t rowbase = (size_t)(row0 + q) * L;
     double acc = 0.0;
-    for (int t = threadIdx.x; t < R * L; t += blockDim.x) {
-        const int r = t >> LOGL, j = t & (L - 1);
-        const size_t idx = (size_t)(row0 + r) * L + j;
+    float2 x[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+        const size_t idx = rowbase + t + k * T;
         float l = cb * c[idx];
         if (a) l = fmaf(ca, a[idx], l);
         lam[idx] = l;
         acc += 0.5 * (double)l * (double)l;
-        if (b) {
-            b[idx] = w * l * gm[idx];
-            b[N + idx] = w * l * gm[N + idx];
-        }
-        A[r * L + j] = make_float2(l * v[idx], l * v[N + idx]);
+        b[idx] = w * l * gm[idx];
+        b[N + idx] = w * l * gm[N + idx];
+        x[k] = make_float2(l * v[idx], l * v[N + idx]);
     }
     if (part) {
-        double s = block_reduce<0>(acc);
+        const double s = block_reduce<0>(acc);
         if (threadIdx.x == 0) part[blockIdx.x] = s;
     }
-    __syncthreads();
-    float2* Y = smem_fft<LOGL, false>(A, B, R, tw);
-    split_store<LOGL>(Y, R, F1, F2, n1, row0, false);
+    flux_fft_store<LOGL>(x, q, t, R, row0, A, X, F1, F2, tw);
 }
 
 // ---------------------------------------------------------------------------
-// column kernel: FFT along x^1, Fourier multiplier, inverse FFT
+// column kernel: FFT along x^1, Fourier multiplier, inverse FFT.  A CTA owns
+// C consecutive columns e0..e0+C-1 of the packed half spectra (T = n1/8
+// threads per column FFT); each 4-row tile contributes C*32 contiguous bytes.
+// Column 0 holds the k2 = 0 column (real part) and the k2 = n2/2 column
+// (imaginary part) of each real field; they are separated per wavenumber with
+// the partner entry at -k1 before the multiplier is applied.
 // ---------------------------------------------------------------------------
 struct ColArgs {
     const float2* in[5];
@@ -395,98 +456,113 @@ __device__ __forceinline__ void spec_apply(const SpecParams& P, float k1o, float
 }
 
 template <int LOGL, int NIN, int NOUT, int OP>
-__global__ void __launch_bounds__(NTHREADS) k_col(ColArgs a, const float2* __restrict__ tw) {
-    extern __shared__ float2 sm[];
-    constexpr int L = 1 << LOGL, H = L >> 1;
-    constexpr int NF = NIN > NOUT ? NIN : NOUT;
-    const int CPB = a.cpb;
+__global__ void __launch_bounds__(256) k_col(ColArgs a, const float2* __restrict__ tw) {
+    extern __shared__ __align__(16) float2 sm[];
+    constexpr int L = 1 << LOGL, T = L >> 3, H = L >> 1;
+    const int C = a.cpb;
+    const int W = a.n2 >> 1;
     float2* A = sm;
-    float2* B = sm + NF * CPB * L;
-    const int j0 = blockIdx.x * CPB;
-    for (int t = threadIdx.x; t < NIN * CPB * L; t += blockDim.x) {
-        const int f = t / (CPB * L);
-        const int rem = t - f * CPB * L;
-        const int c = rem >> LOGL, i = rem & (L - 1);
-        A[t] = a.in[f][(size_t)(j0 + c) * L + i];
+    float2* X = sm + C * L;
+    const int c = threadIdx.x / T, t = threadIdx.x - c * T;
+    const int e0 = blockIdx.x * C;
+    const int e = e0 + c;
+    float2 xin[NIN][8];
+#pragma unroll
+    for (int f = 0; f < NIN; ++f) {
+        const float2* src = a.in[f];
+        for (int idx = threadIdx.x; idx < C * L; idx += blockDim.x) {
+            const int g = idx / (4 * C);
+            const int rem = idx - g * 4 * C;
+            const int cc = rem >> 2, rr = rem & 3;
+            A[cc * L + 4 * g + rr] = src[((size_t)g * W + e0 + cc) * 4 + rr];
+        }
+        __syncthreads();
+#pragma unroll
+        for (int k = 0; k < 8; ++k) xin[f][k] = A[c * L + t + k * T];
+        reg_fft<LOGL, false>(xin[f], t, true, X + 2 * c * L, X + 2 * c * L + L, tw);
     }
-    __syncthreads();
-    float2* X = smem_fft<LOGL, false>(A, B, NIN * CPB, tw);
-    float2* Y = (X == A) ? B : A;
+    float2 y[NOUT > 0 ? NOUT : 1][8];
     double eacc = 0.0;
-    const float kny2 = 0.5f * (float)a.n2;  // |k2| of the Nyquist column (even symbols)
-    for (int t = threadIdx.x; t < CPB * L; t += blockDim.x) {
-        const int c = t >> LOGL, p = t & (L - 1);
-        const int j = j0 + c;
+    if (e0 == 0) {
+        // packed column 0: stage every input's column-0 spectrum (natural order) for the -k1 partner
+        float2* Zs = sm;  // NIN * L <= 3 * C * L entries
+        __syncthreads();
+        if (c == 0) {
+#pragma unroll
+            for (int f = 0; f < NIN; ++f)
+#pragma unroll
+                for (int k = 0; k < 8; ++k) Zs[f * L + t + k * T] = xin[f][k];
+        }
+        __syncthreads();
+    }
+    const float kny2 = 0.5f * (float)a.n2;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+        const int p = t + k * T;
         const float k1 = (p < H) ? (float)p : (float)(p - L);
         const float k1o = (p == H) ? 0.f : k1;
-        float2 x[NIN > 0 ? NIN : 1], y[NOUT > 0 ? NOUT : 1];
-        if (j > 0) {
-            const float k2 = (float)j;
+        float2 xv[NIN], yv[NOUT > 0 ? NOUT : 1];
+        if (e > 0) {
 #pragma unroll
-            for (int f = 0; f < NIN; ++f) x[f] = X[(f * CPB + c) * L + p];
-            spec_apply<OP>(a.P, k1o, k2, k1 * k1 + k2 * k2, x, y, eacc, 2.f);
-#pragma unroll
-            for (int o = 0; o < NOUT; ++o) Y[(o * CPB + c) * L + p] = y[o];
+            for (int f = 0; f < NIN; ++f) xv[f] = xin[f][k];
+            const float k2 = (float)e;
+            spec_apply<OP>(a.P, k1o, k2, k1 * k1 + k2 * k2, xv, yv, eacc, 2.f);
         } else {
-            // packed column: A-part is k2 = 0, B-part is k2 = n2/2 (odd symbol 0)
-            if (p > H) continue;
             const int pm = (L - p) & (L - 1);
-            const bool self = (p == 0) || (p == H);
-            float2 xa[NIN > 0 ? NIN : 1], xb[NIN > 0 ? NIN : 1], ya[NOUT > 0 ? NOUT : 1], yb[NOUT > 0 ? NOUT : 1];
+            float2 xb[NIN], yb[NOUT > 0 ? NOUT : 1];
 #pragma unroll
             for (int f = 0; f < NIN; ++f) {
-                const float2 zp = X[(f * CPB + c) * L + p];
-                if (self) {
-                    xa[f] = make_float2(zp.x, 0.f);
-                    xb[f] = make_float2(zp.y, 0.f);
-                } else {
-                    split_pair(zp, X[(f * CPB + c) * L + pm], xa[f], xb[f]);
-                }
+                const float2 zp = xin[f][k], zm = sm[f * L + pm];
+                xv[f] = make_float2(0.5f * (zp.x + zm.x), 0.5f * (zp.y - zm.y));
+                xb[f] = make_float2(0.5f * (zp.y + zm.y), -0.5f * (zp.x - zm.x));
             }
-            const float ew = self ? 1.f : 2.f;
-            spec_apply<OP>(a.P, k1o, 0.f, k1 * k1, xa, ya, eacc, ew);
-            spec_apply<OP>(a.P, k1o, 0.f, k1 * k1 + kny2 * kny2, xb, yb, eacc, ew);
+            spec_apply<OP>(a.P, k1o, 0.f, k1 * k1, xv, yv, eacc, 1.f);
+            spec_apply<OP>(a.P, k1o, 0.f, k1 * k1 + kny2 * kny2, xb, yb, eacc, 1.f);
 #pragma unroll
-            for (int o = 0; o < NOUT; ++o) {
-                if (self) {
-                    Y[(o * CPB + c) * L + p] = make_float2(ya[o].x - yb[o].y, ya[o].y + yb[o].x);
-                } else {
-                    float2 zk, zm;
-                    merge_pair(ya[o], yb[o], zk, zm);
-                    Y[(o * CPB + c) * L + p] = zk;
-                    Y[(o * CPB + c) * L + pm] = zm;
-                }
-            }
+            for (int o = 0; o < NOUT; ++o) yv[o] = make_float2(yv[o].x - yb[o].y, yv[o].y + yb[o].x);
         }
+#pragma unroll
+        for (int o = 0; o < NOUT; ++o) y[o][k] = yv[o];
     }
     if (OP == OP_ENERGY) {
         const double s = block_reduce<0>(eacc);
         if (threadIdx.x == 0) a.part[blockIdx.x] = s * a.P.escale;
         return;
     }
-    __syncthreads();
-    float2* Z = smem_fft<LOGL, true>(Y, X, NOUT * CPB, tw);
-    for (int t = threadIdx.x; t < NOUT * CPB * L; t += blockDim.x) {
-        const int o = t / (CPB * L);
-        const int rem = t - o * CPB * L;
-        const int c = rem >> LOGL, i = rem & (L - 1);
-        a.out[o][(size_t)(j0 + c) * L + i] = Z[t];
+#pragma unroll
+    for (int o = 0; o < NOUT; ++o) {
+        __syncthreads();
+        reg_fft<LOGL, true>(y[o], t, true, X + 2 * c * L, X + 2 * c * L + L, tw);
+#pragma unroll
+        for (int k = 0; k < 8; ++k) A[c * L + t + k * T] = y[o][k];
+        __syncthreads();
+        float2* dst = a.out[o];
+        for (int idx = threadIdx.x; idx < C * L; idx += blockDim.x) {
+            const int g = idx / (4 * C);
+            const int rem = idx - g * 4 * C;
+            const int cc = rem >> 2, rr = rem & 3;
+            dst[((size_t)g * W + e0 + cc) * 4 + rr] = A[cc * L + 4 * g + rr];
+        }
     }
 }
 
 // ---------------------------------------------------------------------------
 // launch helpers
 // ---------------------------------------------------------------------------
+// R rows per row CTA: a multiple of 4 with at least 64 threads (T = L/8 per row)
 static int rows_per_cta(int n1, int L) {
+    const int T = L / 8;
     int R = 4;
-    while (R * L < 1024 && R * 2 <= n1) R *= 2;
+    while (R * T < 64 && R * 2 <= n1) R *= 2;
     return R;
 }
 
+// C columns per column CTA: at least 2 (64-byte segments) and 64 threads
 static int cols_per_cta(int W, int L) {
-    int c = 1;
-    while (c * L < 1024 && c * 2 <= W) c *= 2;
-    return c;
+    const int T = L / 8;
+    int c = 2;
+    while (c * T < 64 && c * 2 <= W) c *= 2;
+    return c > W ? W : c;
 }
 
 // Opt in to more than 48 KB of dynamic shared memory once per kernel instantiation and size.
@@ -512,57 +588,63 @@ static void set_smem(K kern, size_t bytes) {
         default: break;                               \
     }
 
+struct RowCfg { int R, threads; size_t smem; int grid; };
+static RowCfg row_cfg(reg_ctx* ctx) {
+    RowCfg c;
+    const int L = ctx->n2;
+    c.R = rows_per_cta(ctx->n1, L);
+    c.threads = c.R * (L / 8);
+    c.smem = 3 * (size_t)c.R * L * sizeof(float2);
+    c.grid = ctx->n1 / c.R;
+    return c;
+}
+
 void launch_r2c_scalar(reg_ctx* ctx, const float* f, float2* S) {
-    const int L = ctx->n2, R = rows_per_cta(ctx->n1, L);
-    const size_t smem = 2 * (size_t)R * L * sizeof(float2);
+    const RowCfg g = row_cfg(ctx);
     ktimer_begin(ctx, KC_ROW, 8.0 * ctx->N);
     DISPATCH_LOG(ctx->log2, {
         auto kern = k_r2c<LG, false>;
-        set_smem(kern, smem);
-        kern<<<ctx->n1 / R, NTHREADS, smem, ctx->stream>>>(f, nullptr, S, nullptr, ctx->n1, R, ctx->tw);
+        set_smem(kern, g.smem);
+        kern<<<g.grid, g.threads, g.smem, ctx->stream>>>(f, nullptr, S, nullptr, g.R, ctx->tw);
     });
     ktimer_end(ctx);
 }
 
 void launch_r2c_vec(reg_ctx* ctx, const float* u1, const float* u2, float2* S1, float2* S2) {
-    const int L = ctx->n2, R = rows_per_cta(ctx->n1, L);
-    const size_t smem = 2 * (size_t)R * L * sizeof(float2);
+    const RowCfg g = row_cfg(ctx);
     ktimer_begin(ctx, KC_ROW, 16.0 * ctx->N);
     DISPATCH_LOG(ctx->log2, {
         auto kern = k_r2c<LG, true>;
-        set_smem(kern, smem);
-        kern<<<ctx->n1 / R, NTHREADS, smem, ctx->stream>>>(u1, u2, S1, S2, ctx->n1, R, ctx->tw);
+        set_smem(kern, g.smem);
+        kern<<<g.grid, g.threads, g.smem, ctx->stream>>>(u1, u2, S1, S2, g.R, ctx->tw);
     });
     ktimer_end(ctx);
 }
 
 void launch_c2r_scalar(reg_ctx* ctx, const float2* S, float* f) {
-    const int L = ctx->n2, R = rows_per_cta(ctx->n1, L);
-    const size_t smem = 2 * (size_t)R * L * sizeof(float2);
+    const RowCfg g = row_cfg(ctx);
     ktimer_begin(ctx, KC_ROW, 8.0 * ctx->N);
     DISPATCH_LOG(ctx->log2, {
         auto kern = k_c2r<LG, false>;
-        set_smem(kern, smem);
-        kern<<<ctx->n1 / R, NTHREADS, smem, ctx->stream>>>(S, nullptr, f, nullptr, ctx->n1, R, ctx->tw);
+        set_smem(kern, g.smem);
+        kern<<<g.grid, g.threads, g.smem, ctx->stream>>>(S, nullptr, f, nullptr, g.R, ctx->tw);
     });
     ktimer_end(ctx);
 }
 
 void launch_c2r_vec(reg_ctx* ctx, const float2* S1, const float2* S2, float* u1, float* u2) {
-    const int L = ctx->n2, R = rows_per_cta(ctx->n1, L);
-    const size_t smem = 2 * (size_t)R * L * sizeof(float2);
+    const RowCfg g = row_cfg(ctx);
     ktimer_begin(ctx, KC_ROW, 16.0 * ctx->N);
     DISPATCH_LOG(ctx->log2, {
         auto kern = k_c2r<LG, true>;
-        set_smem(kern, smem);
-        kern<<<ctx->n1 / R, NTHREADS, smem, ctx->stream>>>(S1, S2, u1, u2, ctx->n1, R, ctx->tw);
+        set_smem(kern, g.smem);
+        kern<<<g.grid, g.threads, g.smem, ctx->stream>>>(S1, S2, u1, u2, g.R, ctx->tw);
     });
     ktimer_end(ctx);
 }
 
 void launch_row_adv(reg_ctx* ctx, const AdvArgs& a) {
-    const int L = ctx->n2, R = rows_per_cta(ctx->n1, L);
-    const size_t smem = 2 * (size_t)R * L * sizeof(float2);
+    const RowCfg g = row_cfg(ctx);
     // floats per node read/written: G 2 (complex half spectra = 1 float per node each), u_j 1,
     // u* 1 (stage 2), v 2, source gm + v~ 4, u_out 1, grad_out 2, S_out 1
     double fl = 1 + 2 + 1 + (a.G1 ? 2 : 0) + (a.stage == 2 ? 1 : 0) + (a.gm ? 4 : 0) + (a.grad_out ? 2 : 0) +
@@ -570,48 +652,47 @@ void launch_row_adv(reg_ctx* ctx, const AdvArgs& a) {
     ktimer_begin(ctx, KC_ROWSTAGE, 4.0 * fl * ctx->N);
     DISPATCH_LOG(ctx->log2, {
         auto kern = k_row_adv<LG>;
-        set_smem(kern, smem);
-        kern<<<ctx->n1 / R, NTHREADS, smem, ctx->stream>>>(a, ctx->n1, ctx->N, R, ctx->tw);
+        set_smem(kern, g.smem);
+        kern<<<g.grid, g.threads, g.smem, ctx->stream>>>(a, ctx->N, g.R, ctx->tw);
     });
     ktimer_end(ctx);
 }
 
 void launch_row_adj(reg_ctx* ctx, const AdjArgs& a) {
-    const int L = ctx->n2, R = rows_per_cta(ctx->n1, L);
-    const size_t smem = 2 * (size_t)R * L * sizeof(float2);
+    const RowCfg g = row_cfg(ctx);
     // D 1, lam_j 1, lam* 1 (stage 2), v 2, l_out 1, body force b read+write 4 and gm 2, flux spectra 2
     double fl = 1 + 1 + 2 + 1 + (a.stage == 2 ? 1 : 0) + (a.b ? 6 : 0) + (a.F1 ? 2 : 0);
     ktimer_begin(ctx, KC_ROWSTAGE, 4.0 * fl * ctx->N);
     DISPATCH_LOG(ctx->log2, {
         auto kern = k_row_adj<LG>;
-        set_smem(kern, smem);
-        kern<<<ctx->n1 / R, NTHREADS, smem, ctx->stream>>>(a, ctx->n1, ctx->N, R, ctx->tw);
+        set_smem(kern, g.smem);
+        kern<<<g.grid, g.threads, g.smem, ctx->stream>>>(a, ctx->N, g.R, ctx->tw);
     });
     ktimer_end(ctx);
 }
 
 void launch_adj_init(reg_ctx* ctx, const float* a, float ca, const float* c, float cb, const float* v, float* lam,
                      float* b, const float* gm, float w, float2* F1, float2* F2, double* part) {
-    const int L = ctx->n2, R = rows_per_cta(ctx->n1, L);
-    const size_t smem = 2 * (size_t)R * L * sizeof(float2);
+    const RowCfg g = row_cfg(ctx);
     // a 1 (optional), c 1, v 2, lam 1, b 2 + gm 2, flux spectra 2
     ktimer_begin(ctx, KC_ROW, 4.0 * ((a ? 1 : 0) + 1 + 2 + 1 + 4 + 2) * ctx->N);
     DISPATCH_LOG(ctx->log2, {
         auto kern = k_adj_init<LG>;
-        set_smem(kern, smem);
-        kern<<<ctx->n1 / R, NTHREADS, smem, ctx->stream>>>(a, ca, c, cb, v, lam, b, gm, w, F1, F2, part, ctx->n1,
-                                                            ctx->N, R, ctx->tw);
+        set_smem(kern, g.smem);
+        kern<<<g.grid, g.threads, g.smem, ctx->stream>>>(a, ca, c, cb, v, lam, b, gm, w, F1, F2, part, ctx->N, g.R,
+                                                           ctx->tw);
     });
     ktimer_end(ctx);
 }
+
+int row_blocks(reg_ctx* ctx) { return row_cfg(ctx).grid; }
 
 template <int NIN, int NOUT, int OP>
 static void launch_col_t(reg_ctx* ctx, const float2* const* in, float2* const* out, const SpecParams& P,
                          double* part) {
     const int L = ctx->n1, W = ctx->n2 / 2;
     const int cpb = cols_per_cta(W, L);
-    constexpr int NF = NIN > NOUT ? NIN : NOUT;
-    const size_t smem = 2 * (size_t)NF * cpb * L * sizeof(float2);
+    const size_t smem = 3 * (size_t)cpb * L * sizeof(float2);
     ColArgs a;
     for (int f = 0; f < 5; ++f) a.in[f] = (f < NIN) ? in[f] : nullptr;
     for (int o = 0; o < 2; ++o) a.out[o] = (o < NOUT) ? out[o] : nullptr;
@@ -623,7 +704,7 @@ static void launch_col_t(reg_ctx* ctx, const float2* const* in, float2* const* o
     DISPATCH_LOG(ctx->log1, {
         auto kern = k_col<LG, NIN, NOUT, OP>;
         set_smem(kern, smem);
-        kern<<<W / cpb, NTHREADS, smem, ctx->stream>>>(a, ctx->tw);
+        kern<<<W / cpb, cpb * (L / 8), smem, ctx->stream>>>(a, ctx->tw);
     });
     ktimer_end(ctx);
 }

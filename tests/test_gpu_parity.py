@@ -21,13 +21,18 @@ OP_TOL = 1e-5
 U32 = 2.0 ** -24
 
 
-def op_tol(beta_v, regnorm, n1, n2, x, y):
-    """1e-5 plus the FP32 rounding bound of the regularization term: u * beta_v
-    * max A^ * ||x|| / ||y|| (x the operand, y the reference output).  For the
-    H2 seminorm on smooth fields this term dominates: rounding the FP32 inputs
-    alone moves the FP64 result by up to that amount."""
+def op_tol(beta_v, regnorm, n1, n2, x, y, b=None):
+    """Tolerance for y = beta_v A x + P(b) (reduced gradient, Hessian matvec):
+    1e-5 relative to the magnitudes of the terms that are summed and projected,
+    (||beta_v A x|| + ||b||) / ||y||, plus the FP32 rounding bound of the
+    regularization term, u * beta_v * max A^ * ||x|| / ||y||.  The first factor
+    matters where the projection K removes most of b (mass source, Leray);
+    the second where the H2 symbol |k|^4 amplifies the rounding of the FP32
+    operand (rounding the inputs alone moves the FP64 result that much)."""
     Amax = S.reg_symbol(n1, n2, regnorm).max()
-    return OP_TOL + U32 * beta_v * Amax * np.linalg.norm(x) / np.linalg.norm(y)
+    ny = np.linalg.norm(y)
+    terms = np.linalg.norm(beta_v * S.apply_A(x, regnorm)) + (np.linalg.norm(b) if b is not None else 0.0)
+    return OP_TOL * max(1.0, terms / ny) + U32 * beta_v * Amax * np.linalg.norm(x) / ny
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -126,12 +131,17 @@ def test_objective_gradient_matvec(case):
     g = torch.empty(2, n1, n2, device="cuda")
     Jg = ctx.gradient(to_gpu(v), g)
     g_ref, _ = P.gradient(v)
+    b = torch.empty(2, n1, n2, device="cuda")
+    ctx.body_force(b)
+    assert rel_l2(to_np(b), P.b) < OP_TOL
     assert abs(Jg - J_ref) < OP_TOL * abs(J_ref)
-    assert rel_l2(to_np(g), g_ref) < op_tol(bv, regnorm, n1, n2, v, g_ref)
+    assert rel_l2(to_np(g), g_ref) < op_tol(bv, regnorm, n1, n2, v, g_ref, P.b)
     Hv = torch.empty(2, n1, n2, device="cuda")
     ctx.hessian_matvec(to_gpu(vt), Hv)
     Hv_ref = P.matvec(vt)
-    assert rel_l2(to_np(Hv), Hv_ref) < op_tol(bv, regnorm, n1, n2, vt, Hv_ref)
+    ctx.body_force(b)
+    assert rel_l2(to_np(b), P.bt) < OP_TOL
+    assert rel_l2(to_np(Hv), Hv_ref) < op_tol(bv, regnorm, n1, n2, vt, Hv_ref, P.bt)
     ctx.close()
 
 
@@ -200,11 +210,14 @@ def test_shear_gradient_matvec(s):
     J = ctx.gradient(to_gpu(v), g)
     g_ref, J_ref = P.gradient(v)
     assert abs(J - J_ref) < OP_TOL * abs(J_ref)
-    assert rel_l2(to_np(g), g_ref) < op_tol(1e-3, 1, n1, n2, v, g_ref)
+    assert rel_l2(to_np(g), g_ref) < op_tol(1e-3, 1, n1, n2, v, g_ref, P.b)
     Hv = torch.empty(2, n1, n2, device="cuda")
     ctx.hessian_matvec(to_gpu(vt), Hv)
     Hv_ref = P.matvec(vt)
-    assert rel_l2(to_np(Hv), Hv_ref) < op_tol(1e-3, 1, n1, n2, vt, Hv_ref)
+    b = torch.empty(2, n1, n2, device="cuda")
+    ctx.body_force(b)
+    assert rel_l2(to_np(b), P.bt) < OP_TOL
+    assert rel_l2(to_np(Hv), Hv_ref) < op_tol(1e-3, 1, n1, n2, vt, Hv_ref, P.bt)
     ctx.close()
 
 
