@@ -61,7 +61,13 @@ extern "C" void reg_default_opts(reg_solve_opts* o) {
 // ---------------------------------------------------------------------------
 // allocation
 // ---------------------------------------------------------------------------
+static void clear_graphs(reg_ctx* c) {
+    for (auto& g : c->graphs) cudaGraphExecDestroy(g.exec);
+    c->graphs.clear();
+}
+
 static void free_hist(reg_ctx* c) {
+    clear_graphs(c);  // captured sequences hold history pointers
     cudaFree(c->m_hist);
     cudaFree(c->gm_hist);
     c->m_hist = c->gm_hist = nullptr;
@@ -91,6 +97,7 @@ extern "C" void reg_destroy(reg_ctx* c) {
     for (auto p : fl) cudaFree(*p);
     for (int i = 0; i < 6; ++i) cudaFree(c->S[i]);
     free_hist(c);
+    clear_graphs(c);
     cudaFree(c->d_scal);
     cudaFree(c->d_part);
     cudaFree(c->tw);
@@ -131,6 +138,7 @@ extern "C" int reg_create(reg_grid grid, int nt, int regnorm, double beta, doubl
     c->stream = 0;
     c->have_lin = false;
     c->launches = 0;
+    c->use_graphs = true;
     c->timing = false;
     for (int k = 0; k < KC_COUNT; ++k) { c->tcount[k] = 0; c->tms[k] = 0.0; c->tbytes[k] = 0.0; }
 
@@ -172,7 +180,56 @@ extern "C" int reg_create(reg_grid grid, int nt, int regnorm, double beta, doubl
 
 extern "C" int reg_set_stream(reg_ctx* c, void* stream) {
     if (!c) return reg_fail(REG_ERR_ARG, "ctx is NULL");
+    if ((cudaStream_t)stream != c->stream) clear_graphs(c);
     c->stream = (cudaStream_t)stream;
+    return REG_OK;
+}
+
+// ---------------------------------------------------------------------------
+// CUDA graphs: each fixed launch sequence (objective, gradient tail, matvec,
+// one PCG iteration) is captured once per (kind, pointers, nt) and replayed.
+// Sequences run directly on the legacy default stream (it cannot be
+// captured) and while per-kernel timing is on.
+// ---------------------------------------------------------------------------
+enum GraphKind { GK_OBJECTIVE = 1, GK_GRADIENT = 2, GK_MATVEC = 3, GK_PCG_ITER = 4, GK_PCG_INIT = 5 };
+
+template <typename F>
+static int run_seq(reg_ctx* c, int kind, const void* p0, const void* p1, int nt, F&& body) {
+    if (!c->use_graphs || c->timing || c->stream == 0) {
+        body();
+        CKL();
+        return REG_OK;
+    }
+    for (auto& g : c->graphs) {
+        if (g.kind == kind && g.p0 == p0 && g.p1 == p1 && g.nt == nt) {
+            CK(cudaGraphLaunch(g.exec, c->stream));
+            c->launches += g.nkern;
+            return REG_OK;
+        }
+    }
+    const long long l0 = c->launches;
+    CK(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeRelaxed));
+    body();
+    cudaGraph_t graph = nullptr;
+    cudaError_t e = cudaStreamEndCapture(c->stream, &graph);
+    const long long nk = c->launches - l0;
+    c->launches = l0;
+    if (e != cudaSuccess || graph == nullptr) {
+        cudaGetLastError();
+        return reg_fail(REG_ERR_CUDA, std::string("stream capture failed: ") + cudaGetErrorString(e));
+    }
+    GraphEntry g;
+    g.kind = kind; g.p0 = p0; g.p1 = p1; g.nt = nt; g.nkern = nk;
+    e = cudaGraphInstantiate(&g.exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) return reg_fail(REG_ERR_CUDA, std::string("graph instantiate: ") + cudaGetErrorString(e));
+    if (c->graphs.size() >= 64) {  // callers that pass many distinct pointers: drop the oldest capture
+        cudaGraphExecDestroy(c->graphs.front().exec);
+        c->graphs.erase(c->graphs.begin());
+    }
+    c->graphs.push_back(g);
+    CK(cudaGraphLaunch(g.exec, c->stream));
+    c->launches += nk;
     return REG_OK;
 }
 
@@ -372,21 +429,22 @@ static int read_scalars(reg_ctx* c) {
 
 static int ensure_nt(reg_ctx* c, int nt) { return alloc_hist(c, nt); }
 
-// forward solve + J (device slots SL_JDATA, SL_JREG); lam_nt left in w1 if want_adj
-static int objective_dev(reg_ctx* c, const float* v, int nt) {
-    RET(ensure_nt(c, nt));
+// forward solve + J (device slots SL_JDATA, SL_JREG)
+static void objective_launches(reg_ctx* c, const float* v, int nt) {
     state_solve(c, v, nt);
     // J_data = 0.5 ||m_R - m_1||^2
     launch_axpby(c, c->N, 1.f, c->mR, -1.f, mh(c, nt), -1, -1, c->w1);
     int np = launch_dot_partial(c, c->w1, c->w1, c->N, c->d_part);
     launch_finalize(c, c->d_part, np, c->d_scal + SL_JDATA, 0.5 * hh(c), 0, 0);
     reg_energy(c, v);
-    CKL();
-    return REG_OK;
 }
 
-static int gradient_dev(reg_ctx* c, const float* v, float* g, int nt) {
-    RET(objective_dev(c, v, nt));
+static int objective_dev(reg_ctx* c, const float* v, int nt) {
+    RET(ensure_nt(c, nt));
+    return run_seq(c, GK_OBJECTIVE, v, nullptr, nt, [&] { objective_launches(c, v, nt); });
+}
+
+static void gradient_launches(reg_ctx* c, const float* v, float* g, int nt) {
     adjoint_solve(c, v, nt, c->mR, 1.f, mh(c, nt), -1.f, c->bvec, nullptr);
     if (c->shear_model) {
         sp_grad_vec(c, v, c->gtmp);
@@ -397,14 +455,17 @@ static int gradient_dev(reg_ctx* c, const float* v, float* g, int nt) {
     }
     if (v != c->v_lin)
         cudaMemcpyAsync(c->v_lin, v, sizeof(float) * 2 * c->N, cudaMemcpyDeviceToDevice, c->stream);
+}
+
+static int gradient_dev(reg_ctx* c, const float* v, float* g, int nt) {
+    RET(objective_dev(c, v, nt));
+    RET(run_seq(c, GK_GRADIENT, v, g, nt, [&] { gradient_launches(c, v, g, nt); }));
     c->nt_lin = nt;
     c->have_lin = true;
-    CKL();
     return REG_OK;
 }
 
-static int matvec_dev(reg_ctx* c, const float* vt, float* Hvt) {
-    if (!c->have_lin) return reg_fail(REG_ERR_STATE, "reg_hessian_matvec called before reg_gradient");
+static void matvec_launches(reg_ctx* c, const float* vt, float* Hvt) {
     const int nt = c->nt_lin;
     inc_state_solve(c, c->v_lin, vt, nt);
     adjoint_solve(c, c->v_lin, nt, nullptr, 0.f, c->w3, -1.f, c->bvec, nullptr);
@@ -415,8 +476,11 @@ static int matvec_dev(reg_ctx* c, const float* vt, float* Hvt) {
     } else {
         sp_assemble(c, (float)c->beta_v, vt, c->bvec, Hvt);
     }
-    CKL();
-    return REG_OK;
+}
+
+static int matvec_dev(reg_ctx* c, const float* vt, float* Hvt) {
+    if (!c->have_lin) return reg_fail(REG_ERR_STATE, "reg_hessian_matvec called before reg_gradient");
+    return run_seq(c, GK_MATVEC, vt, Hvt, c->nt_lin, [&] { matvec_launches(c, vt, Hvt); });
 }
 
 static void precond_dev(reg_ctx* c, const float* r, float* z) {
@@ -549,41 +613,54 @@ static int nt_for(reg_ctx* c, const float* v, const reg_solve_opts& o, double* c
     return nt;
 }
 
-// PCG (Algorithm 2) on H vt = -g; returns #matvecs
+// PCG (Algorithm 2) on H vt = -g; returns #matvecs.  One PCG iteration is a
+// single launch sequence (matvec, <s, Hs>, updates of vt and r with
+// kappa = <r, z> / <s, Hs> computed on the device, ||r||^2, z = P r,
+// <z, r>, s = z + mu s); the host reads <s, Hs> and ||r|| once per iteration
+// for the curvature check and the stop test (Algorithm 2's break).  The
+// update kernel does nothing when <s, Hs> <= 0, so vt and r keep their values
+// from before that iteration.
 static int pcg_dev(reg_ctx* c, double gnorm, double eta, int maxit, int* hit_max, int* status) {
     const long long n2N = 2 * (long long)c->N;
     const double scale = hh(c);
     *status = REG_OK;
-    launch_fill(c, n2N, c->vt, 0.f);
-    launch_axpby(c, n2N, -1.f, c->g, 0.f, c->r, -1, -1, c->r);  // r = -g
-    precond_dev(c, c->r, c->z);
-    CK(cudaMemcpyAsync(c->s, c->z, sizeof(float) * n2N, cudaMemcpyDeviceToDevice, c->stream));
-    dot_dev(c, c->r, c->z, SL_RZ);
+    RET(run_seq(c, GK_PCG_INIT, nullptr, nullptr, c->nt_lin, [&] {
+        launch_fill(c, n2N, c->vt, 0.f);
+        launch_axpby(c, n2N, -1.f, c->g, 0.f, c->r, -1, -1, c->r);  // r = -g
+        precond_dev(c, c->r, c->z);
+        cudaMemcpyAsync(c->s, c->z, sizeof(float) * n2N, cudaMemcpyDeviceToDevice, c->stream);
+        dot_dev(c, c->r, c->z, SL_RZ);
+    }));
     int it = 0;
     *hit_max = 1;
+    if (!c->have_lin) return reg_fail(REG_ERR_STATE, "PCG without a linearization point");
     for (int l = 0; l < maxit; ++l) {
-        int st = matvec_dev(c, c->s, c->Hs);
+        int st = run_seq(c, GK_PCG_ITER, nullptr, nullptr, c->nt_lin, [&] {
+            matvec_launches(c, c->s, c->Hs);
+            dot_dev(c, c->s, c->Hs, SL_SHS);
+            int np = launch_pcg_update(c, n2N, c->vt, c->s, c->r, c->Hs, c->d_part);
+            launch_finalize(c, c->d_part, np, c->d_scal + SL_RNORM2, scale, 0, 0);
+            precond_dev(c, c->r, c->z);
+            dot_dev(c, c->z, c->r, SL_RZNEW);
+            launch_pcg_dir(c, n2N, c->z, c->s);
+            cudaMemcpyAsync(c->d_scal + SL_RZ, c->d_scal + SL_RZNEW, sizeof(double), cudaMemcpyDeviceToDevice,
+                            c->stream);
+        });
         if (st != REG_OK) { *status = st; return it; }
         ++it;
-        dot_dev(c, c->s, c->Hs, SL_SHS);
         if (read_scalars(c) != REG_OK) { *status = REG_ERR_CUDA; return it; }
         const double sHs = c->h_scal[SL_SHS];
         if (!std::isfinite(sHs)) { *status = REG_ERR_NAN; return it; }
         if (sHs <= 0.0) {
+            // non-positive curvature: the update kernel left vt and r unchanged; in the first
+            // iteration the step is the first direction s_0 = P r_0 (the oracle's choice)
             *hit_max = 0;
-            if (it == 1) CK(cudaMemcpyAsync(c->vt, c->s, sizeof(float) * n2N, cudaMemcpyDeviceToDevice, c->stream));
+            if (it == 1) precond_dev(c, c->r, c->vt);
             break;
         }
-        int np = launch_pcg_update(c, n2N, c->vt, c->s, c->r, c->Hs, c->d_part);
-        launch_finalize(c, c->d_part, np, c->d_scal + SL_RNORM2, scale, 0, 0);
-        if (read_scalars(c) != REG_OK) { *status = REG_ERR_CUDA; return it; }
         const double rn = std::sqrt(c->h_scal[SL_RNORM2]);
         if (!std::isfinite(rn)) { *status = REG_ERR_NAN; return it; }
         if (rn < eta * gnorm) { *hit_max = 0; break; }
-        precond_dev(c, c->r, c->z);
-        dot_dev(c, c->z, c->r, SL_RZNEW);
-        launch_pcg_dir(c, n2N, c->z, c->s);
-        CK(cudaMemcpyAsync(c->d_scal + SL_RZ, c->d_scal + SL_RZNEW, sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
     }
     CKL();
     return it;

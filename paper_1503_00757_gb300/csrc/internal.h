@@ -46,6 +46,17 @@ enum Slot {
 
 struct EventPair { cudaEvent_t a, b; int kclass; double bytes; };
 
+// A captured launch sequence, replayed with cudaGraphLaunch.  Keyed by the
+// kind of sequence, the caller pointers it was captured with and nt.
+struct GraphEntry {
+    int kind;
+    const void* p0;
+    const void* p1;
+    int nt;
+    cudaGraphExec_t exec;
+    long long nkern;
+};
+
 struct reg_ctx {
     int n1, n2, N, log1, log2;
     int nt;          // requested nt
@@ -86,6 +97,8 @@ struct reg_ctx {
     float2* tw;      // twiddle table (REG_TW_N entries)
 
     long long launches;
+    bool use_graphs;
+    std::vector<GraphEntry> graphs;
     bool timing;
     std::vector<EventPair> events;
     std::vector<cudaEvent_t> event_pool;
@@ -146,7 +159,8 @@ void launch_finalize(reg_ctx* ctx, const double* part, int np, double* out, doub
 // y = a * x + b * y, with optional device-scalar factor: if (num >= 0) a *= d_scal[num] / d_scal[den]
 void launch_axpby(reg_ctx* ctx, long long n, float a, const float* x, float b, float* y, int num, int den,
                   float* out);
-// PCG step: vt += kappa s; r -= kappa Hs; partial sum r^2; kappa = d_scal[SL_RZ] / d_scal[SL_SHS]
+// PCG step: vt += kappa s; r -= kappa Hs; partial sum r^2; kappa = d_scal[SL_RZ] / d_scal[SL_SHS];
+// no update when d_scal[SL_SHS] <= 0
 int launch_pcg_update(reg_ctx* ctx, long long n, float* vt, const float* s, float* r, const float* Hs, double* part);
 // s = z + (d_scal[SL_RZNEW] / d_scal[SL_RZ]) s
 void launch_pcg_dir(reg_ctx* ctx, long long n, const float* z, float* s);

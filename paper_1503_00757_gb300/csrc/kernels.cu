@@ -568,7 +568,7 @@ static int cols_per_cta(int W, int L) {
 // Opt in to more than 48 KB of dynamic shared memory once per kernel instantiation and size.
 template <typename K>
 static void set_smem(K kern, size_t bytes) {
-    if (bytes <= 48 * 1024) return;
+    if (bytes <= 32 * 1024) return;  // static shared memory (reductions) also counts toward the 48 KB default
     static std::unordered_map<const void*, size_t> done;
     auto it = done.find((const void*)kern);
     if (it != done.end() && it->second >= bytes) return;
@@ -799,8 +799,13 @@ void launch_axpby(reg_ctx* ctx, long long n, float a, const float* x, float b, f
 
 __global__ void k_pcg_update(long long n, float* vt, const float* __restrict__ s, float* r, const float* __restrict__ Hs,
                              const double* __restrict__ scal, double* part) {
-    const float kappa = (float)(scal[SL_RZ] / scal[SL_SHS]);
+    const double shs = scal[SL_SHS];
+    const float kappa = (float)(scal[SL_RZ] / shs);
     double acc = 0.0;
+    if (!(shs > 0.0)) {  // non-positive curvature: leave vt and r unchanged (the host stops PCG)
+        if (threadIdx.x == 0) part[blockIdx.x] = 0.0;
+        return;
+    }
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
         vt[i] = fmaf(kappa, s[i], vt[i]);
         const float ri = fmaf(-kappa, Hs[i], r[i]);

@@ -113,12 +113,21 @@ def _resample_v(v, n1, n2):
     return np.stack([_resample(v[0], n1, n2), _resample(v[1], n1, n2)])
 
 
+def cfl_scaled(vs, n1, n2, nt, cfl=0.3):
+    """Scale v so that max|v| nt^-1 / h_x = cfl.  Above ~0.3, Heun's per-step
+    amplification of the highest modes, sqrt(1 + z^4/4) with z = pi * CFL,
+    multiplies FP32 round-off by up to |.|^nt in every transport solve (the
+    paper adapts nt to the CFL condition, Sec. 6.1)."""
+    vmax = np.sqrt(vs[0] ** 2 + vs[1] ** 2).max()
+    return vs * (cfl * 2 * np.pi * nt / (max(n1, n2) * vmax))
+
+
 @pytest.mark.parametrize("case", CASES)
 def test_objective_gradient_matvec(case):
     import torch
     n1, n2, nt, regnorm, bv, bw, kind = case
     mT, mR, vs = _pair(kind, n1, n2, 2000)
-    v = 0.5 * vs
+    v = cfl_scaled(vs, n1, n2, nt)
     vt = synth.velocity(n1, n2, min(n1, n2) // 8, 0.3, np.random.default_rng(7), grad_fraction=0.5)
     P = Registration(mT, mR, nt, regnorm=regnorm, beta_v=bv, beta_w=bw)
     ctx = make_ctx(n1, n2, nt, regnorm=regnorm, beta=bv, gamma=bw)
@@ -238,3 +247,36 @@ def test_solve_end_to_end(regnorm, gamma, shear):
     assert rel_l2(to_np(v), v_ref) < 1e-3
     assert abs(st["rnorm_rel_sq"] - st_ref["rnorm_rel_sq"]) < 1e-3 * st_ref["rnorm_rel_sq"]
     ctx.close()
+
+
+def test_graph_path_matches_direct_launches():
+    """On a non-default stream every fixed launch sequence is captured once in a
+    CUDA graph and replayed; results must equal the direct launches bit for bit."""
+    import torch
+    n, nt = 64, 8
+    mT, mR, vs = synth.ellipses_pair(n, 2002, vmax=0.2)
+    v = cfl_scaled(vs, n, n, nt)
+    vt = synth.velocity(n, n, 6, 0.3, np.random.default_rng(9))
+    outs = []
+    for use_stream in (False, True):
+        stream = torch.cuda.Stream() if use_stream else None
+        ctx = make_ctx(n, n, nt, regnorm=1, beta=1e-3, gamma=math.inf)
+        if stream is not None:
+            ctx.set_stream(stream)
+        with torch.cuda.stream(stream) if stream is not None else torch.cuda.stream(torch.cuda.current_stream()):
+            ctx.set_images(to_gpu(mT), to_gpu(mR))
+            g = torch.empty(2, n, n, device="cuda")
+            Hv = torch.empty(2, n, n, device="cuda")
+            vg = to_gpu(v)
+            vtg = to_gpu(vt)
+            for _ in range(2):  # second pass replays the captured graphs
+                J = ctx.gradient(vg, g)
+                ctx.hessian_matvec(vtg, Hv)
+            vsol = torch.zeros(2, n, n, device="cuda")
+            st = ctx.solve(vsol)
+            torch.cuda.synchronize()
+        outs.append((J, to_np(g), to_np(Hv), to_np(vsol), st["n_mv"]))
+        ctx.close()
+    (J0, g0, H0, v0, m0), (J1, g1, H1, v1, m1) = outs
+    assert J0 == J1 and m0 == m1
+    assert np.array_equal(g0, g1) and np.array_equal(H0, H1) and np.array_equal(v0, v1)
