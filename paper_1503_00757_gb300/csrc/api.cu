@@ -98,6 +98,7 @@ extern "C" void reg_destroy(reg_ctx* c) {
     for (int i = 0; i < 6; ++i) cudaFree(c->S[i]);
     free_hist(c);
     clear_graphs(c);
+    for (auto g : c->timing_graphs) cudaGraphExecDestroy(g);
     cudaFree(c->d_scal);
     cudaFree(c->d_part);
     cudaFree(c->tw);
@@ -138,6 +139,7 @@ extern "C" int reg_create(reg_grid grid, int nt, int regnorm, double beta, doubl
     c->stream = 0;
     c->have_lin = false;
     c->launches = 0;
+    c->pdl = true;
     c->use_graphs = true;
     c->timing = false;
     for (int k = 0; k < KC_COUNT; ++k) { c->tcount[k] = 0; c->tms[k] = 0.0; c->tbytes[k] = 0.0; }
@@ -195,6 +197,23 @@ enum GraphKind { GK_OBJECTIVE = 1, GK_GRADIENT = 2, GK_MATVEC = 3, GK_PCG_ITER =
 
 template <typename F>
 static int run_seq(reg_ctx* c, int kind, const void* p0, const void* p1, int nt, F&& body) {
+    if (c->timing && c->stream != 0) {
+        // per-kernel timing: capture the sequence with its event records as graph nodes, so
+        // the events bracket the kernels on the device without host launch gaps in between
+        CK(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeRelaxed));
+        body();
+        cudaGraph_t graph = nullptr;
+        cudaError_t e = cudaStreamEndCapture(c->stream, &graph);
+        if (e != cudaSuccess || graph == nullptr)
+            return reg_fail(REG_ERR_CUDA, std::string("stream capture failed: ") + cudaGetErrorString(e));
+        cudaGraphExec_t exec;
+        e = cudaGraphInstantiate(&exec, graph, 0);
+        cudaGraphDestroy(graph);
+        if (e != cudaSuccess) return reg_fail(REG_ERR_CUDA, std::string("graph instantiate: ") + cudaGetErrorString(e));
+        c->timing_graphs.push_back(exec);
+        CK(cudaGraphLaunch(exec, c->stream));
+        return REG_OK;
+    }
     if (!c->use_graphs || c->timing || c->stream == 0) {
         body();
         CKL();
@@ -393,11 +412,11 @@ static void adjoint_solve(reg_ctx* c, const float* v, int nt, const float* a, fl
 }
 
 // Incremental state (Eq. (e:inc-state-eq-elim)); leaves m~(1) in c->w3.
+// m~(0) = 0 is passed as u_j = nullptr to both stages of the first step.
 static void inc_state_solve(reg_ctx* c, const float* v, const float* vt, int nt) {
     const float h = 1.0f / (float)nt;
     float* mj = c->w3;
     float* ms = c->w0;
-    launch_fill(c, c->N, mj, 0.f);
     const float2* in[1] = {c->S[0]};
     float2* G[2] = {c->S[1], c->S[2]};
     const SpecParams P = spec_params(c, 0.f);
@@ -407,7 +426,7 @@ static void inc_state_solve(reg_ctx* c, const float* v, const float* vt, int nt)
             launch_col(c, OP_GRAD, in, G, P, nullptr);
             a.G1 = c->S[1]; a.G2 = c->S[2];
         }
-        a.uj = mj; a.us = nullptr; a.v = v; a.gm = gmh(c, j); a.vt = vt;
+        a.uj = (j > 0) ? mj : nullptr; a.us = nullptr; a.v = v; a.gm = gmh(c, j); a.vt = vt;
         a.u_out = ms; a.grad_out = nullptr; a.S_out = c->S[0]; a.h = h; a.stage = 1;
         launch_row_adv(c, a);
         launch_col(c, OP_GRAD, in, G, P, nullptr);
@@ -840,8 +859,10 @@ extern "C" int reg_detgrad(reg_ctx* c, const float* v, float* detF, double* stat
 // instrumentation
 // ---------------------------------------------------------------------------
 static void drain_events(reg_ctx* c) {
-    if (c->events.empty()) return;
     cudaStreamSynchronize(c->stream);
+    for (auto g : c->timing_graphs) cudaGraphExecDestroy(g);
+    c->timing_graphs.clear();
+    if (c->events.empty()) return;
     for (auto& e : c->events) {
         float ms = 0.f;
         cudaEventElapsedTime(&ms, e.a, e.b);

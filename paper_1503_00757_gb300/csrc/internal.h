@@ -97,8 +97,10 @@ struct reg_ctx {
     float2* tw;      // twiddle table (REG_TW_N entries)
 
     long long launches;
+    bool pdl;         // launch with programmatic dependent launch (default on)
     bool use_graphs;
     std::vector<GraphEntry> graphs;
+    std::vector<cudaGraphExec_t> timing_graphs;  // one-off captures made while timing is on
     bool timing;
     std::vector<EventPair> events;
     std::vector<cudaEvent_t> event_pool;
@@ -119,7 +121,7 @@ void launch_col(reg_ctx* ctx, int op, const float2* const* in, float2* const* ou
 
 struct AdvArgs {
     const float2 *G1, *G2;  // spectra of d1 u_s, d2 u_s; G1 == nullptr -> zero gradient
-    const float *uj, *us;   // u_j and the stage-2 input u* (stage 1: us unused)
+    const float *uj, *us;   // u_j (nullptr: u_j = 0) and the stage-2 input u* (stage 1: us unused)
     const float* v;         // velocity (2N)
     const float* gm;        // grad m at the source time (2N); nullptr -> no source
     const float* vt;        // incremental velocity (2N)

@@ -24,6 +24,35 @@
 #define NTHREADS 256
 #define NBLK_RED 304  // 2 x 152 SMs
 
+// Programmatic dependent launch: every kernel waits for the grid it depends
+// on (it has completed and its writes are visible after the wait) and then
+// lets the next kernel in the stream begin launching, so the launch, CTA
+// scheduling and prologue of kernel k+1 overlap the tail of kernel k.  Since
+// each kernel triggers only after its own wait, a kernel that starts early
+// may read, before its wait, anything written two or more launches back
+// (the RK2 row-stage kernels prefetch their pointwise operands that way).
+// Without a programmatic dependency both instructions are no-ops.
+__device__ __forceinline__ void pdl_entry() {
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
+// Launch with the programmatic-stream-serialization attribute (ctx->pdl) or plainly.
+template <typename... KArgs, typename... Args>
+static void launch_k(reg_ctx* ctx, void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem, Args... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = ctx->stream;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = ctx->pdl ? 1 : 0;
+    cudaLaunchKernelEx(&cfg, kern, static_cast<KArgs>(args)...);
+}
+
 // ---------------------------------------------------------------------------
 // timing hooks
 // ---------------------------------------------------------------------------
@@ -41,13 +70,14 @@ void ktimer_begin(reg_ctx* ctx, int kclass, double bytes) {
     ep.b = ctx->event_pool[need - 1];
     ep.kclass = kclass;
     ep.bytes = bytes;
-    cudaEventRecord(ep.a, ctx->stream);
+    // external record: inside a stream capture this becomes an event-record node of the graph
+    cudaEventRecordWithFlags(ep.a, ctx->stream, cudaEventRecordExternal);
     ctx->events.push_back(ep);
 }
 
 void ktimer_end(reg_ctx* ctx) {
     if (!ctx->timing) return;
-    cudaEventRecord(ctx->events.back().b, ctx->stream);
+    cudaEventRecordWithFlags(ctx->events.back().b, ctx->stream, cudaEventRecordExternal);
 }
 
 cudaError_t k_init_twiddles(reg_ctx* ctx) {
@@ -112,6 +142,7 @@ __device__ __forceinline__ void stage_chunk(float2* dst, const float2* __restric
 template <int LOGL, bool VEC>
 __global__ void __launch_bounds__(512) k_r2c(const float* __restrict__ f1, const float* __restrict__ f2,
                                              float2* S1, float2* S2, int R, const float2* __restrict__ tw) {
+    pdl_entry();
     extern __shared__ __align__(16) float2 sm[];
     constexpr int L = 1 << LOGL, T = L >> 3, W = L >> 1;
     float2* A = sm;
@@ -157,6 +188,7 @@ template <int LOGL, bool VEC>
 __global__ void __launch_bounds__(512) k_c2r(const float2* __restrict__ S1, const float2* __restrict__ S2,
                                              float* __restrict__ f1, float* __restrict__ f2, int R,
                                              const float2* __restrict__ tw) {
+    pdl_entry();
     extern __shared__ __align__(16) float2 sm[];
     constexpr int L = 1 << LOGL, T = L >> 3, W = L >> 1;
     float2* A = sm;
@@ -211,6 +243,21 @@ __global__ void __launch_bounds__(512) k_row_adv(AdvArgs a, int N, int R, const 
     const int q = threadIdx.x / T, t = threadIdx.x - q * T;
     const int row0 = blockIdx.x * R;
     const size_t base = (size_t)row0 * W;
+    const size_t rowbase = (size_t)(row0 + q) * L;
+    // Operands written at least two launches earlier (u_j, u*, v, grad m, v~) are
+    // loaded before waiting on the preceding column kernel; only G depends on it.
+    // u_j == nullptr stands for u_j = 0 (the incremental state at t = 0).
+    float pv1[8], pv2[8], puj[8], pus[8], psrc[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+        const size_t idx = rowbase + t + k * T;
+        pv1[k] = a.v[idx];
+        pv2[k] = a.v[N + idx];
+        puj[k] = a.uj ? a.uj[idx] : 0.f;
+        pus[k] = (a.stage == 2) ? a.us[idx] : 0.f;
+        psrc[k] = a.gm ? -(a.vt[idx] * a.gm[idx] + a.vt[N + idx] * a.gm[N + idx]) : 0.f;
+    }
+    pdl_entry();
     float2 x[8];
     if (a.G1) {
         stage_chunk<LOGL>(A, a.G1 + base, R * W);
@@ -224,7 +271,6 @@ __global__ void __launch_bounds__(512) k_row_adv(AdvArgs a, int N, int R, const 
         for (int k = 0; k < 8; ++k) x[k] = make_float2(0.f, 0.f);
     }
     float out[8];
-    const size_t rowbase = (size_t)(row0 + q) * L;
 #pragma unroll
     for (int k = 0; k < 8; ++k) {
         const size_t idx = rowbase + t + k * T;
@@ -233,10 +279,8 @@ __global__ void __launch_bounds__(512) k_row_adv(AdvArgs a, int N, int R, const 
             a.grad_out[idx] = d1;
             a.grad_out[N + idx] = d2;
         }
-        float kk = -(a.v[idx] * d1 + a.v[N + idx] * d2);
-        if (a.gm) kk -= a.vt[idx] * a.gm[idx] + a.vt[N + idx] * a.gm[N + idx];
-        const float uj = a.uj[idx];
-        out[k] = (a.stage == 1) ? fmaf(a.h, kk, uj) : 0.5f * (uj + a.us[idx] + a.h * kk);
+        const float kk = psrc[k] - (pv1[k] * d1 + pv2[k] * d2);
+        out[k] = (a.stage == 1) ? fmaf(a.h, kk, puj[k]) : 0.5f * (puj[k] + pus[k] + a.h * kk);
         a.u_out[idx] = out[k];
     }
     if (!a.S_out) return;
@@ -298,6 +342,25 @@ __global__ void __launch_bounds__(512) k_row_adj(AdjArgs a, int N, int R, const 
     float2* X = sm + R * L;
     const int q = threadIdx.x / T, t = threadIdx.x - q * T;
     const int row0 = blockIdx.x * R;
+    const size_t rowbase = (size_t)(row0 + q) * L;
+    // Operands written at least two launches earlier (lam_j, lam*, v, b, grad m)
+    // are loaded before waiting on the preceding column kernel, which writes D.
+    float plj[8], pls[8], pv1[8], pv2[8], pb1[8], pb2[8], pg1[8], pg2[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+        const size_t idx = rowbase + t + k * T;
+        plj[k] = a.lj[idx];
+        pls[k] = (a.stage == 2) ? a.ls[idx] : 0.f;
+        pv1[k] = a.v[idx];
+        pv2[k] = a.v[N + idx];
+        if (a.b) {
+            pb1[k] = a.b[idx];
+            pb2[k] = a.b[N + idx];
+            pg1[k] = a.gm[idx];
+            pg2[k] = a.gm[N + idx];
+        }
+    }
+    pdl_entry();
     stage_chunk<LOGL>(A, a.D + (size_t)row0 * W, R * W);
     __syncthreads();
     const bool act1 = q < R / 2;
@@ -316,21 +379,19 @@ __global__ void __launch_bounds__(512) k_row_adj(AdjArgs a, int N, int R, const 
         }
     }
     __syncthreads();
-    const size_t rowbase = (size_t)(row0 + q) * L;
 #pragma unroll
     for (int k = 0; k < 8; ++k) {
         const int j = t + k * T;
         const size_t idx = rowbase + j;
         const float dv = O[q * L + j];
-        const float lj = a.lj[idx];
-        const float out = (a.stage == 1) ? fmaf(a.h, dv, lj) : 0.5f * (lj + a.ls[idx] + a.h * dv);
+        const float out = (a.stage == 1) ? fmaf(a.h, dv, plj[k]) : 0.5f * (plj[k] + pls[k] + a.h * dv);
         a.l_out[idx] = out;
         if (a.b) {
             const float wl = a.w * out;
-            a.b[idx] = fmaf(wl, a.gm[idx], a.b[idx]);
-            a.b[N + idx] = fmaf(wl, a.gm[N + idx], a.b[N + idx]);
+            a.b[idx] = fmaf(wl, pg1[k], pb1[k]);
+            a.b[N + idx] = fmaf(wl, pg2[k], pb2[k]);
         }
-        x[k] = make_float2(out * a.v[idx], out * a.v[N + idx]);
+        x[k] = make_float2(out * pv1[k], out * pv2[k]);
     }
     if (!a.F1) return;
     flux_fft_store<LOGL>(x, q, t, R, row0, A, X, a.F1, a.F2, tw);
@@ -342,6 +403,7 @@ __global__ void __launch_bounds__(512) k_adj_init(const float* __restrict__ a, f
                                                   float cb, const float* __restrict__ v, float* lam, float* b,
                                                   const float* __restrict__ gm, float w, float2* F1, float2* F2,
                                                   double* part, int N, int R, const float2* __restrict__ tw) {
+    pdl_entry();
     extern __shared__ __align__(16) float2 sm[];
     constexpr int L = 1 << LOGL, T = L >> 3;
     float2* A = sm;
@@ -457,6 +519,7 @@ __device__ __forceinline__ void spec_apply(const SpecParams& P, float k1o, float
 
 template <int LOGL, int NIN, int NOUT, int OP>
 __global__ void __launch_bounds__(256) k_col(ColArgs a, const float2* __restrict__ tw) {
+    pdl_entry();
     extern __shared__ __align__(16) float2 sm[];
     constexpr int L = 1 << LOGL, T = L >> 3, H = L >> 1;
     const int C = a.cpb;
@@ -605,7 +668,7 @@ void launch_r2c_scalar(reg_ctx* ctx, const float* f, float2* S) {
     DISPATCH_LOG(ctx->log2, {
         auto kern = k_r2c<LG, false>;
         set_smem(kern, g.smem);
-        kern<<<g.grid, g.threads, g.smem, ctx->stream>>>(f, nullptr, S, nullptr, g.R, ctx->tw);
+        launch_k(ctx, kern, g.grid, g.threads, g.smem, f, nullptr, S, nullptr, g.R, ctx->tw);
     });
     ktimer_end(ctx);
 }
@@ -616,7 +679,7 @@ void launch_r2c_vec(reg_ctx* ctx, const float* u1, const float* u2, float2* S1, 
     DISPATCH_LOG(ctx->log2, {
         auto kern = k_r2c<LG, true>;
         set_smem(kern, g.smem);
-        kern<<<g.grid, g.threads, g.smem, ctx->stream>>>(u1, u2, S1, S2, g.R, ctx->tw);
+        launch_k(ctx, kern, g.grid, g.threads, g.smem, u1, u2, S1, S2, g.R, ctx->tw);
     });
     ktimer_end(ctx);
 }
@@ -627,7 +690,7 @@ void launch_c2r_scalar(reg_ctx* ctx, const float2* S, float* f) {
     DISPATCH_LOG(ctx->log2, {
         auto kern = k_c2r<LG, false>;
         set_smem(kern, g.smem);
-        kern<<<g.grid, g.threads, g.smem, ctx->stream>>>(S, nullptr, f, nullptr, g.R, ctx->tw);
+        launch_k(ctx, kern, g.grid, g.threads, g.smem, S, nullptr, f, nullptr, g.R, ctx->tw);
     });
     ktimer_end(ctx);
 }
@@ -638,7 +701,7 @@ void launch_c2r_vec(reg_ctx* ctx, const float2* S1, const float2* S2, float* u1,
     DISPATCH_LOG(ctx->log2, {
         auto kern = k_c2r<LG, true>;
         set_smem(kern, g.smem);
-        kern<<<g.grid, g.threads, g.smem, ctx->stream>>>(S1, S2, u1, u2, g.R, ctx->tw);
+        launch_k(ctx, kern, g.grid, g.threads, g.smem, S1, S2, u1, u2, g.R, ctx->tw);
     });
     ktimer_end(ctx);
 }
@@ -653,7 +716,7 @@ void launch_row_adv(reg_ctx* ctx, const AdvArgs& a) {
     DISPATCH_LOG(ctx->log2, {
         auto kern = k_row_adv<LG>;
         set_smem(kern, g.smem);
-        kern<<<g.grid, g.threads, g.smem, ctx->stream>>>(a, ctx->N, g.R, ctx->tw);
+        launch_k(ctx, kern, g.grid, g.threads, g.smem, a, ctx->N, g.R, ctx->tw);
     });
     ktimer_end(ctx);
 }
@@ -666,7 +729,7 @@ void launch_row_adj(reg_ctx* ctx, const AdjArgs& a) {
     DISPATCH_LOG(ctx->log2, {
         auto kern = k_row_adj<LG>;
         set_smem(kern, g.smem);
-        kern<<<g.grid, g.threads, g.smem, ctx->stream>>>(a, ctx->N, g.R, ctx->tw);
+        launch_k(ctx, kern, g.grid, g.threads, g.smem, a, ctx->N, g.R, ctx->tw);
     });
     ktimer_end(ctx);
 }
@@ -679,7 +742,7 @@ void launch_adj_init(reg_ctx* ctx, const float* a, float ca, const float* c, flo
     DISPATCH_LOG(ctx->log2, {
         auto kern = k_adj_init<LG>;
         set_smem(kern, g.smem);
-        kern<<<g.grid, g.threads, g.smem, ctx->stream>>>(a, ca, c, cb, v, lam, b, gm, w, F1, F2, part, ctx->N, g.R,
+        launch_k(ctx, kern, g.grid, g.threads, g.smem, a, ca, c, cb, v, lam, b, gm, w, F1, F2, part, ctx->N, g.R,
                                                            ctx->tw);
     });
     ktimer_end(ctx);
@@ -704,7 +767,7 @@ static void launch_col_t(reg_ctx* ctx, const float2* const* in, float2* const* o
     DISPATCH_LOG(ctx->log1, {
         auto kern = k_col<LG, NIN, NOUT, OP>;
         set_smem(kern, smem);
-        kern<<<W / cpb, cpb * (L / 8), smem, ctx->stream>>>(a, ctx->tw);
+        launch_k(ctx, kern, W / cpb, cpb * (L / 8), smem, a, ctx->tw);
     });
     ktimer_end(ctx);
 }
@@ -733,6 +796,7 @@ void launch_col(reg_ctx* ctx, int op, const float2* const* in, float2* const* ou
 // pointwise and reduction kernels
 // ---------------------------------------------------------------------------
 __global__ void k_dot_partial(const float* __restrict__ x, const float* __restrict__ y, long long n, double* part) {
+    pdl_entry();
     double acc = 0.0;
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
         acc += (double)x[i] * (double)y[i];
@@ -742,12 +806,13 @@ __global__ void k_dot_partial(const float* __restrict__ x, const float* __restri
 
 int launch_dot_partial(reg_ctx* ctx, const float* x, const float* y, long long n, double* part) {
     ktimer_begin(ctx, KC_POINT, 8.0 * n);
-    k_dot_partial<<<NBLK_RED, NTHREADS, 0, ctx->stream>>>(x, y, n, part);
+    launch_k(ctx, k_dot_partial, NBLK_RED, NTHREADS, 0, x, y, n, part);
     ktimer_end(ctx);
     return NBLK_RED;
 }
 
 __global__ void k_maxnorm_partial(const float* __restrict__ v, int N, double* part) {
+    pdl_entry();
     double m = 0.0;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < N; i += gridDim.x * blockDim.x) {
         const double a = v[i], b = v[N + i];
@@ -759,13 +824,14 @@ __global__ void k_maxnorm_partial(const float* __restrict__ v, int N, double* pa
 
 int launch_maxnorm_partial(reg_ctx* ctx, const float* v, int N, double* part) {
     ktimer_begin(ctx, KC_POINT, 8.0 * N);
-    k_maxnorm_partial<<<NBLK_RED, NTHREADS, 0, ctx->stream>>>(v, N, part);
+    launch_k(ctx, k_maxnorm_partial, NBLK_RED, NTHREADS, 0, v, N, part);
     ktimer_end(ctx);
     return NBLK_RED;
 }
 
 template <int OPR>
 __global__ void k_finalize(const double* __restrict__ part, int np, double* out, double scale, int accumulate) {
+    pdl_entry();
     double acc = (OPR == 0) ? 0.0 : part[0];
     for (int i = threadIdx.x; i < np; i += blockDim.x) acc = red_op<OPR>(acc, part[i]);
     const double s = block_reduce<OPR>(acc);
@@ -774,14 +840,15 @@ __global__ void k_finalize(const double* __restrict__ part, int np, double* out,
 
 void launch_finalize(reg_ctx* ctx, const double* part, int np, double* out, double scale, int accumulate, int op) {
     ktimer_begin(ctx, KC_POINT, 8.0 * np);
-    if (op == 0) k_finalize<0><<<1, NTHREADS, 0, ctx->stream>>>(part, np, out, scale, accumulate);
-    else if (op == 1) k_finalize<1><<<1, NTHREADS, 0, ctx->stream>>>(part, np, out, scale, accumulate);
-    else k_finalize<2><<<1, NTHREADS, 0, ctx->stream>>>(part, np, out, scale, accumulate);
+    if (op == 0) launch_k(ctx, k_finalize<0>, 1, NTHREADS, 0, part, np, out, scale, accumulate);
+    else if (op == 1) launch_k(ctx, k_finalize<1>, 1, NTHREADS, 0, part, np, out, scale, accumulate);
+    else launch_k(ctx, k_finalize<2>, 1, NTHREADS, 0, part, np, out, scale, accumulate);
     ktimer_end(ctx);
 }
 
 __global__ void k_axpby(long long n, float a, const float* __restrict__ x, float b, const float* y, float* out,
                         const double* __restrict__ scal, int num, int den) {
+    pdl_entry();
     float aa = a;
     if (num >= 0) aa = (float)((double)a * scal[num] / scal[den]);
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
@@ -793,12 +860,13 @@ __global__ void k_axpby(long long n, float a, const float* __restrict__ x, float
 
 void launch_axpby(reg_ctx* ctx, long long n, float a, const float* x, float b, float* y, int num, int den, float* out) {
     ktimer_begin(ctx, KC_POINT, 4.0 * n * ((a != 0.f) + (b != 0.f) + 1));
-    k_axpby<<<NBLK_RED, NTHREADS, 0, ctx->stream>>>(n, a, x, b, y, out ? out : y, ctx->d_scal, num, den);
+    launch_k(ctx, k_axpby, NBLK_RED, NTHREADS, 0, n, a, x, b, y, out ? out : y, ctx->d_scal, num, den);
     ktimer_end(ctx);
 }
 
 __global__ void k_pcg_update(long long n, float* vt, const float* __restrict__ s, float* r, const float* __restrict__ Hs,
                              const double* __restrict__ scal, double* part) {
+    pdl_entry();
     const double shs = scal[SL_SHS];
     const float kappa = (float)(scal[SL_RZ] / shs);
     double acc = 0.0;
@@ -818,12 +886,13 @@ __global__ void k_pcg_update(long long n, float* vt, const float* __restrict__ s
 
 int launch_pcg_update(reg_ctx* ctx, long long n, float* vt, const float* s, float* r, const float* Hs, double* part) {
     ktimer_begin(ctx, KC_POINT, 4.0 * n * 6);
-    k_pcg_update<<<NBLK_RED, NTHREADS, 0, ctx->stream>>>(n, vt, s, r, Hs, ctx->d_scal, part);
+    launch_k(ctx, k_pcg_update, NBLK_RED, NTHREADS, 0, n, vt, s, r, Hs, ctx->d_scal, part);
     ktimer_end(ctx);
     return NBLK_RED;
 }
 
 __global__ void k_pcg_dir(long long n, const float* __restrict__ z, float* s, const double* __restrict__ scal) {
+    pdl_entry();
     const float mu = (float)(scal[SL_RZNEW] / scal[SL_RZ]);
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
         s[i] = fmaf(mu, s[i], z[i]);
@@ -831,18 +900,19 @@ __global__ void k_pcg_dir(long long n, const float* __restrict__ z, float* s, co
 
 void launch_pcg_dir(reg_ctx* ctx, long long n, const float* z, float* s) {
     ktimer_begin(ctx, KC_POINT, 4.0 * n * 3);
-    k_pcg_dir<<<NBLK_RED, NTHREADS, 0, ctx->stream>>>(n, z, s, ctx->d_scal);
+    launch_k(ctx, k_pcg_dir, NBLK_RED, NTHREADS, 0, n, z, s, ctx->d_scal);
     ktimer_end(ctx);
 }
 
 __global__ void k_fill(long long n, float* y, float val) {
+    pdl_entry();
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
         y[i] = val;
 }
 
 void launch_fill(reg_ctx* ctx, long long n, float* y, float val) {
     ktimer_begin(ctx, KC_POINT, 4.0 * n);
-    k_fill<<<NBLK_RED, NTHREADS, 0, ctx->stream>>>(n, y, val);
+    launch_k(ctx, k_fill, NBLK_RED, NTHREADS, 0, n, y, val);
     ktimer_end(ctx);
 }
 
@@ -851,6 +921,7 @@ void launch_fill(reg_ctx* ctx, long long n, float* y, float val) {
 __global__ void k_defgrad_stage(int N, int stage, const float* __restrict__ F, const float* __restrict__ Fs,
                                 const float* __restrict__ gF, const float* __restrict__ gv,
                                 const float* __restrict__ v, float h, float* out) {
+    pdl_entry();
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < N; i += gridDim.x * blockDim.x) {
         const float* Fin = (stage == 1) ? F : Fs;
         float Fv[4];
@@ -875,11 +946,12 @@ __global__ void k_defgrad_stage(int N, int stage, const float* __restrict__ F, c
 void launch_defgrad_stage(reg_ctx* ctx, int stage, const float* F, const float* Fs, const float* gF, const float* gv,
                           const float* v, float h, float* out) {
     ktimer_begin(ctx, KC_POINT, 4.0 * (4 + (stage == 2 ? 4 : 0) + 8 + 4 + 2 + 4) * ctx->N);
-    k_defgrad_stage<<<NBLK_RED, NTHREADS, 0, ctx->stream>>>(ctx->N, stage, F, Fs, gF, gv, v, h, out);
+    launch_k(ctx, k_defgrad_stage, NBLK_RED, NTHREADS, 0, ctx->N, stage, F, Fs, gF, gv, v, h, out);
     ktimer_end(ctx);
 }
 
 __global__ void k_det_stats(int N, const float* __restrict__ F, float* detF, double* part) {
+    pdl_entry();
     double mn = 1e300, mx = -1e300, sm = 0.0, dmx = 0.0, dsm = 0.0;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < N; i += gridDim.x * blockDim.x) {
         const double f11 = F[i], f12 = F[(size_t)N + i], f21 = F[2 * (size_t)N + i], f22 = F[3 * (size_t)N + i];
@@ -907,7 +979,7 @@ __global__ void k_det_stats(int N, const float* __restrict__ F, float* detF, dou
 
 int launch_det_stats(reg_ctx* ctx, const float* F, float* detF, double* part) {
     ktimer_begin(ctx, KC_POINT, 4.0 * (4 + (detF ? 1 : 0)) * ctx->N);
-    k_det_stats<<<NBLK_RED, NTHREADS, 0, ctx->stream>>>(ctx->N, F, detF, part);
+    launch_k(ctx, k_det_stats, NBLK_RED, NTHREADS, 0, ctx->N, F, detF, part);
     ktimer_end(ctx);
     return NBLK_RED;
 }
@@ -916,6 +988,7 @@ int launch_det_stats(reg_ctx* ctx, const float* F, float* detF, double* part) {
 #define SHEAR_EPS2 1.0e-6f
 __global__ void k_shear_strain(int N, const float* __restrict__ gv, float nu, float* E, float* eta, float* T,
                                double* part) {
+    pdl_entry();
     const float pe = (1.f - nu) / (2.f * nu);
     const float pw = (1.f + nu) / (2.f * nu);
     double acc = 0.0;
@@ -946,13 +1019,14 @@ __global__ void k_shear_strain(int N, const float* __restrict__ gv, float nu, fl
 
 int launch_shear_strain(reg_ctx* ctx, const float* gv, float nu, float* E, float* eta, float* T, double* part) {
     ktimer_begin(ctx, KC_POINT, 4.0 * (4 + (E ? 3 : 0) + (eta ? 1 : 0) + (T ? 3 : 0)) * ctx->N);
-    k_shear_strain<<<NBLK_RED, NTHREADS, 0, ctx->stream>>>(ctx->N, gv, nu, E, eta, T, part);
+    launch_k(ctx, k_shear_strain, NBLK_RED, NTHREADS, 0, ctx->N, gv, nu, E, eta, T, part);
     ktimer_end(ctx);
     return NBLK_RED;
 }
 
 __global__ void k_shear_second(int N, const float* __restrict__ gvt, const float* __restrict__ E,
                                const float* __restrict__ eta, float nu, float* T) {
+    pdl_entry();
     const float cq = (1.f - nu) / nu;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < N; i += gridDim.x * blockDim.x) {
         const float t11 = gvt[i];
@@ -970,6 +1044,6 @@ __global__ void k_shear_second(int N, const float* __restrict__ gvt, const float
 
 void launch_shear_second(reg_ctx* ctx, const float* gvt, const float* E, const float* eta, float nu, float* T) {
     ktimer_begin(ctx, KC_POINT, 4.0 * (4 + 3 + 1 + 3) * ctx->N);
-    k_shear_second<<<NBLK_RED, NTHREADS, 0, ctx->stream>>>(ctx->N, gvt, E, eta, nu, T);
+    launch_k(ctx, k_shear_second, NBLK_RED, NTHREADS, 0, ctx->N, gvt, E, eta, nu, T);
     ktimer_end(ctx);
 }
