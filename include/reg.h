@@ -177,6 +177,30 @@ int reg_register_host(reg_ctx* ctx, const float* mT_host, const float* mR_host, 
  * mean of D = ||F1 - I||_F (Appendix F). */
 int reg_detgrad(reg_ctx* ctx, const float* v, float* detF, double* stats);
 
+/* ---- allocation-free entry point (the paper has no counterpart) ---- */
+
+/* The spectral gradient of reg_spectral_grad for callers that cannot
+ * allocate device memory: for example code whose device memory is owned by
+ * another allocator that reserves it up front, or code that must not call a
+ * synchronizing cudaMalloc / cudaFree.  No context is needed and nothing is
+ * allocated: the scratch (three packed half spectra, 3 MiB) and the FFT
+ * twiddle table are file-scope device arrays that every GPU which loads the
+ * library holds until the process exits.
+ *   grid      n1, n2 powers of two in [16, 1024] with n1 * n2 <= 512 * 512;
+ *             larger grids are rejected with REG_ERR_ARG (the scratch limit).
+ *   f         device, n1*n2 floats (input, row-major, 16-byte aligned);
+ *   grad_f    device, 2*n1*n2 floats (output: d1 f then d2 f);
+ *   stream    cudaStream_t the work is issued on (NULL = legacy default).
+ * The first call on each device does that device's set-up (looks up the
+ * arrays' device addresses and copies the twiddle table with a synchronous
+ * cudaMemcpyToSymbol), so make the first call on a device before any stream
+ * capture begins.  All calls share the one scratch array and it keeps the
+ * last call's contents; nothing in it has to start at zero because every
+ * entry is written before it is read.  Calls that overlap on the GPU (other
+ * streams, other host threads) race on the scratch: serialize them.
+ * Asynchronous; returns REG_OK, REG_ERR_ARG or REG_ERR_CUDA. */
+int reg_spectral_grad_static(reg_grid grid, const float* f, float* grad_f, void* stream);
+
 /* ---- instrumentation ---- */
 
 /* Per-kernel-class CUDA-event timing (off by default).  While enabled, every

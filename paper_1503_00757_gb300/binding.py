@@ -65,6 +65,7 @@ _SIGS = {
     "reg_kernel_timing": ([_P, _I], _I),
     "reg_kernel_time": ([_P, _I, ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(_D), ctypes.POINTER(_D)], _I),
     "reg_launch_count": ([_P], ctypes.c_longlong),
+    "reg_spectral_grad_static": ([reg_grid, _P, _P, _P], _I),
 }
 
 _lib = None
@@ -116,6 +117,15 @@ def default_opts(**kw):
     for k, v in kw.items():
         setattr(o, k, v)
     return o
+
+
+def spectral_grad_static(f, grad_f, stream=None):
+    """Allocation-free spectral gradient (reg_spectral_grad_static): f (n1, n2),
+    grad_f (2, n1, n2) CUDA float32 tensors; no context, no device allocation."""
+    n1, n2 = f.shape[-2], f.shape[-1]
+    handle = None if stream is None else ctypes.c_void_p(stream.cuda_stream)
+    _check(lib().reg_spectral_grad_static(reg_grid(n1, n2), _ptr(f, n1 * n2, "f"), _ptr(grad_f, 2 * n1 * n2, "grad_f"),
+                                          handle))
 
 
 class Context:
