@@ -145,6 +145,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--matvecs", type=int, default=200)
+    ap.add_argument("--no-big", dest="big", action="store_false",
+                    help="skip the 1024^2 matvec measurement")
     ap.add_argument("--profile", action="store_true",
                     help="run --warmup registrations then one registration and exit (for ncu launch lists)")
     args = ap.parse_args()
@@ -280,6 +282,45 @@ def main():
             n, ms, byt = ctx.kernel_time(kc)
             classes[kc] = (n, ms, byt)
         ctx.kernel_timing(False)
+
+        # HBM regime: 1024^2, nt=32 (history 132 MiB + 264 MiB > L2): matvec throughput and per-class roofline
+        big = {}
+        if args.big:
+            nb = 1024
+            from paper_1503_00757_gb300 import synth
+            bT, bR, bv = synth.ellipses_pair(nb, SEED, vmax=0.049)
+            ctxb = Context(nb, nb, NT, regnorm=1, beta=BETA, gamma=math.inf, shear=0.0, stream=stream)
+            ctxb.set_images(torch.from_numpy(bT.astype(np.float32)).to(dev), torch.from_numpy(bR.astype(np.float32)).to(dev))
+            vb = torch.from_numpy((0.5 * bv).astype(np.float32)).to(dev).contiguous()
+            gb = torch.empty_like(vb)
+            ctxb.gradient(vb, gb)
+            vtb = torch.randn_like(vb)
+            Hb = torch.empty_like(vb)
+            for _ in range(3):
+                ctxb.hessian_matvec(vtb, Hb)
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            nmv = 20
+            e0.record(stream)
+            for _ in range(nmv):
+                ctxb.hessian_matvec(vtb, Hb)
+            e1.record(stream)
+            e1.synchronize()
+            big["ms_per_matvec"] = e0.elapsed_time(e1) / nmv
+            ctxb.kernel_timing(True)
+            for _ in range(3):
+                ctxb.hessian_matvec(vtb, Hb)
+            torch.cuda.synchronize()
+            bcls = {kc: ctxb.kernel_time(kc) for kc in range(4)}
+            ctxb.kernel_timing(False)
+            ctxb.close()
+            bd = max(bcls, key=lambda k: bcls[k][1])
+            ach = bcls[bd][2] / (bcls[bd][1] * 1e-3) / 1e9 if bcls[bd][1] > 0 else 0.0
+            big["roofline"] = {"kernel": ["column FFT + multiplier", "row FFT + RK2 stage", "row FFT (other)",
+                                          "pointwise/reduction"][bd], "achieved": ach, "launches": bcls[bd][0]}
+            big["kernel_classes"] = {str(k): {"launches": bcls[k][0], "ms": bcls[k][1], "GB": bcls[k][2] / 1e9}
+                                     for k in bcls}
     dom = max(classes, key=lambda k: classes[k][1])
     n_dom, ms_dom, bytes_dom = classes[dom]
     peak, peak_kind = peaks()
@@ -309,6 +350,11 @@ def main():
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": None, "kernel": names[dom],
                          "launches": n_dom, "ms": ms_dom, "peak_kind": peak_kind},
+            "matvec_1024": ({"ms_per_matvec": big["ms_per_matvec"], "matvec_per_s": 1e3 / big["ms_per_matvec"],
+                             "roofline": {"bound": "hbm", "kernel": big["roofline"]["kernel"],
+                                          "achieved": big["roofline"]["achieved"], "peak": peak,
+                                          "frac": big["roofline"]["achieved"] / peak, "unit": "GB/s"},
+                             "kernel_classes": big["kernel_classes"]} if big else None),
             "kernel_classes": {names[k]: {"launches": classes[k][0], "ms": classes[k][1],
                                           "GB": classes[k][2] / 1e9} for k in classes},
             "clocks": clk,

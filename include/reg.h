@@ -109,6 +109,11 @@ void reg_default_opts(reg_solve_opts* opts);
 int reg_create(reg_grid grid, int nt, int regnorm, double beta, double gamma, double shear, reg_ctx** out);
 void reg_destroy(reg_ctx* ctx);
 
+/* Re-parameterize an existing context for another problem on the same grid
+ * (same meaning and checks as reg_create); keeps the device workspace,
+ * growing the state history if nt grows.  Invalidates the linearization point. */
+int reg_set_params(reg_ctx* ctx, int nt, int regnorm, double beta, double gamma, double shear);
+
 /* Issue all work on `stream` (a cudaStream_t; NULL = legacy default stream). */
 int reg_set_stream(reg_ctx* ctx, void* stream);
 
@@ -169,6 +174,35 @@ int reg_solve(reg_ctx* ctx, float* v_inout, const reg_solve_opts* opts, reg_solv
  * opts->warm_start) back.  Synchronous. */
 int reg_register_host(reg_ctx* ctx, const float* mT_host, const float* mR_host, float* v_host,
                       const reg_solve_opts* opts, reg_solve_stats* stats);
+
+/* ---- row a15: batched registration of many independent pairs ---- */
+
+/* One pair of a batch.  Inputs: grid, nt, regnorm, beta, gamma, shear (as in
+ * reg_create), mT and mR (device, n1*n2 floats each).  In/out: v (device,
+ * 2*n1*n2 floats; the initial guess when opts->warm_start, else ignored;
+ * receives the solution).  Outputs: stats (filled) and status (the
+ * reg_solve return code of this pair). */
+typedef struct {
+    reg_grid grid;
+    int nt;
+    int regnorm;
+    double beta, gamma, shear;
+    const float* mT;
+    const float* mR;
+    float* v;
+    reg_solve_stats stats;
+    int status;
+} reg_batch_item;
+
+/* Solve `count` independent registrations (Algorithm 1 per pair) on the
+ * current device with `nworkers` host workers (<= 0: 8), each issuing its
+ * pairs on its own CUDA stream with per-grid-size contexts it creates once
+ * and re-parameterizes per pair (reg_set_params), so the pairs' kernels run
+ * concurrently.  Pairs are taken largest grid first.  Every pair's result is
+ * identical to reg_solve on that pair alone.  Synchronous.  Returns REG_OK if
+ * every pair returned REG_OK, else the first failing pair's status (each
+ * item's own status is in item.status); REG_ERR_ARG for invalid arguments. */
+int reg_solve_batch(reg_batch_item* items, int count, const reg_solve_opts* opts, int nworkers);
 
 /* ---- row a14: deformation gradient (Eq. (e:def-grad)) ---- */
 

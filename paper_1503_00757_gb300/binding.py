@@ -40,6 +40,13 @@ class reg_solve_stats(ctypes.Structure):
         return {name: getattr(self, name) for name, _ in self._fields_}
 
 
+class reg_batch_item(ctypes.Structure):
+    _fields_ = [("grid", reg_grid), ("nt", ctypes.c_int), ("regnorm", ctypes.c_int), ("beta", ctypes.c_double),
+                ("gamma", ctypes.c_double), ("shear", ctypes.c_double), ("mT", ctypes.c_void_p),
+                ("mR", ctypes.c_void_p), ("v", ctypes.c_void_p), ("stats", reg_solve_stats),
+                ("status", ctypes.c_int)]
+
+
 _P = ctypes.c_void_p
 _I = ctypes.c_int
 _D = ctypes.c_double
@@ -66,6 +73,8 @@ _SIGS = {
     "reg_kernel_time": ([_P, _I, ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(_D), ctypes.POINTER(_D)], _I),
     "reg_launch_count": ([_P], ctypes.c_longlong),
     "reg_spectral_grad_static": ([reg_grid, _P, _P, _P], _I),
+    "reg_set_params": ([_P, _I, _I, _D, _D, _D], _I),
+    "reg_solve_batch": ([ctypes.POINTER(reg_batch_item), _I, ctypes.POINTER(reg_solve_opts), _I], _I),
 }
 
 _lib = None
@@ -128,6 +137,34 @@ def spectral_grad_static(f, grad_f, stream=None):
                                           handle))
 
 
+def solve_batch(pairs, opts=None, nworkers=8, check=True):
+    """Batched registration (reg_solve_batch).  pairs: list of dicts with CUDA
+    float32 tensors mT (n1, n2), mR (n1, n2), v (2, n1, n2) and the problem
+    parameters nt, regnorm, beta, gamma, shear.  v is overwritten with each
+    solution.  Returns (status, list of per-pair stats dicts)."""
+    n = len(pairs)
+    arr = (reg_batch_item * n)()
+    for i, p in enumerate(pairs):
+        n1, n2 = p["mT"].shape[-2], p["mT"].shape[-1]
+        it = arr[i]
+        it.grid = reg_grid(n1, n2)
+        it.nt, it.regnorm = int(p["nt"]), int(p.get("regnorm", REG_H1))
+        it.beta, it.gamma, it.shear = float(p["beta"]), float(p.get("gamma", math.inf)), float(p.get("shear", 0.0))
+        it.mT = _ptr(p["mT"], n1 * n2, "mT")
+        it.mR = _ptr(p["mR"], n1 * n2, "mR")
+        it.v = _ptr(p["v"], 2 * n1 * n2, "v")
+    o = opts if opts is not None else default_opts()
+    rc = lib().reg_solve_batch(arr, n, ctypes.byref(o), int(nworkers))
+    if check:
+        _check(rc)
+    out = []
+    for i in range(n):
+        d = arr[i].stats.as_dict()
+        d["rc"] = arr[i].status
+        out.append(d)
+    return rc, out
+
+
 class Context:
     """Owns one reg_ctx (one registration problem on one grid)."""
 
@@ -149,6 +186,9 @@ class Context:
             self.close()
         except Exception:
             pass
+
+    def set_params(self, nt, regnorm=REG_H1, beta=1e-2, gamma=math.inf, shear=0.0):
+        _check(lib().reg_set_params(self.h, nt, regnorm, beta, gamma, shear))
 
     def set_stream(self, stream):
         """stream: a torch.cuda.Stream (or None for the legacy default stream)."""

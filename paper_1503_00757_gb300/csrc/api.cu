@@ -107,11 +107,7 @@ extern "C" void reg_destroy(reg_ctx* c) {
     delete c;
 }
 
-extern "C" int reg_create(reg_grid grid, int nt, int regnorm, double beta, double gamma, double shear, reg_ctx** out) {
-    if (!out) return reg_fail(REG_ERR_ARG, "out is NULL");
-    *out = nullptr;
-    if (!is_pow2(grid.n1) || !is_pow2(grid.n2) || grid.n1 < 16 || grid.n2 < 16 || grid.n1 > 1024 || grid.n2 > 1024)
-        return reg_fail(REG_ERR_ARG, "n1 and n2 must be powers of two in [16, 1024]");
+static int check_params(int nt, int regnorm, double beta, double gamma, double shear) {
     if (nt < 1 || nt > 100000) return reg_fail(REG_ERR_ARG, "nt must be in [1, 100000]");
     if (regnorm != REG_H1 && regnorm != REG_H2) return reg_fail(REG_ERR_ARG, "regnorm must be REG_H1 or REG_H2");
     if (!(beta > 0.0) || !std::isfinite(beta)) return reg_fail(REG_ERR_ARG, "beta must be finite and > 0");
@@ -119,6 +115,27 @@ extern "C" int reg_create(reg_grid grid, int nt, int regnorm, double beta, doubl
     if (!(shear > -1.0 && shear < 1.0)) return reg_fail(REG_ERR_ARG, "shear must be in (-1, 1)");
     if (shear != 0.0 && (regnorm != REG_H1 || !std::isinf(gamma)))
         return reg_fail(REG_ERR_ARG, "shear control requires REG_H1 and gamma = +INFINITY");
+    return REG_OK;
+}
+
+static void set_params(reg_ctx* c, int nt, int regnorm, double beta, double gamma, double shear) {
+    c->nt = nt;
+    c->regnorm = regnorm;
+    c->beta_v = beta;
+    c->beta_w = gamma;
+    c->shear = shear;
+    c->shear_model = shear != 0.0;
+    c->nu = (1.0 + shear) / (1.0 - shear);
+    c->pmode = (gamma == 0.0) ? PROJ_IDENTITY : (std::isinf(gamma) ? PROJ_LERAY : PROJ_MASS);
+    c->have_lin = false;
+}
+
+extern "C" int reg_create(reg_grid grid, int nt, int regnorm, double beta, double gamma, double shear, reg_ctx** out) {
+    if (!out) return reg_fail(REG_ERR_ARG, "out is NULL");
+    *out = nullptr;
+    if (!is_pow2(grid.n1) || !is_pow2(grid.n2) || grid.n1 < 16 || grid.n2 < 16 || grid.n1 > 1024 || grid.n2 > 1024)
+        return reg_fail(REG_ERR_ARG, "n1 and n2 must be powers of two in [16, 1024]");
+    RET(check_params(nt, regnorm, beta, gamma, shear));
 
     reg_ctx* c = new reg_ctx();
     memset(c->S, 0, sizeof(c->S));
@@ -127,17 +144,9 @@ extern "C" int reg_create(reg_grid grid, int nt, int regnorm, double beta, doubl
     c->N = grid.n1 * grid.n2;
     c->log1 = ilog2(grid.n1);
     c->log2 = ilog2(grid.n2);
-    c->nt = nt;
     c->nt_cap = 0;
-    c->regnorm = regnorm;
-    c->beta_v = beta;
-    c->beta_w = gamma;
-    c->shear = shear;
-    c->shear_model = shear != 0.0;
-    c->nu = (1.0 + shear) / (1.0 - shear);
-    c->pmode = (gamma == 0.0) ? PROJ_IDENTITY : (std::isinf(gamma) ? PROJ_LERAY : PROJ_MASS);
+    set_params(c, nt, regnorm, beta, gamma, shear);
     c->stream = 0;
-    c->have_lin = false;
     c->launches = 0;
     c->pdl = true;
     c->use_graphs = true;
@@ -178,6 +187,14 @@ extern "C" int reg_create(reg_grid grid, int nt, int regnorm, double beta, doubl
     cudaMemset(c->mR, 0, sizeof(float) * N);
     *out = c;
     return REG_OK;
+}
+
+extern "C" int reg_set_params(reg_ctx* c, int nt, int regnorm, double beta, double gamma, double shear) {
+    if (!c) return reg_fail(REG_ERR_ARG, "ctx is NULL");
+    RET(check_params(nt, regnorm, beta, gamma, shear));
+    clear_graphs(c);  // captured sequences bake in nt and the Fourier-multiplier parameters
+    set_params(c, nt, regnorm, beta, gamma, shear);
+    return alloc_hist(c, nt);
 }
 
 extern "C" int reg_set_stream(reg_ctx* c, void* stream) {

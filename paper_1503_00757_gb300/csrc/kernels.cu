@@ -56,6 +56,15 @@ static void launch_k(reg_ctx* ctx, void (*kern)(KArgs...), dim3 grid, dim3 block
 // ---------------------------------------------------------------------------
 // timing hooks
 // ---------------------------------------------------------------------------
+// Inside a stream capture an external record becomes an event-record node of
+// the graph; outside a capture the plain record is used.
+static void ktimer_record(reg_ctx* ctx, cudaEvent_t e) {
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    cudaStreamIsCapturing(ctx->stream, &cs);
+    if (cs == cudaStreamCaptureStatusActive) cudaEventRecordWithFlags(e, ctx->stream, cudaEventRecordExternal);
+    else cudaEventRecord(e, ctx->stream);
+}
+
 void ktimer_begin(reg_ctx* ctx, int kclass, double bytes) {
     ctx->launches++;
     if (!ctx->timing) return;
@@ -70,14 +79,13 @@ void ktimer_begin(reg_ctx* ctx, int kclass, double bytes) {
     ep.b = ctx->event_pool[need - 1];
     ep.kclass = kclass;
     ep.bytes = bytes;
-    // external record: inside a stream capture this becomes an event-record node of the graph
-    cudaEventRecordWithFlags(ep.a, ctx->stream, cudaEventRecordExternal);
+    ktimer_record(ctx, ep.a);
     ctx->events.push_back(ep);
 }
 
 void ktimer_end(reg_ctx* ctx) {
     if (!ctx->timing) return;
-    cudaEventRecordWithFlags(ctx->events.back().b, ctx->stream, cudaEventRecordExternal);
+    ktimer_record(ctx, ctx->events.back().b);
 }
 
 cudaError_t k_init_twiddles(reg_ctx* ctx) {
