@@ -30,12 +30,15 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "registrations/sec and Hessian matvecs/sec at 512² nt=32; warm-start vs plain"
+PAIRS = 5  # independent C3 pairs per step (seeds 3000..3004), solved concurrently
 N_GRID, NT, BETA, SEED, VMAX = 512, 32, 1e-3, 3000, 0.098
 WORKLOAD = ("C3 synthetic brain-like ellipses 512x512, nt=32, H1, beta_v=1e-3, incompressible, "
-            "shear s=0, zero start, tol 1e-2")
-# PDE solves of one registration of this workload as counted by reg_solve
-# (stats n_pde); used to scale the oracle's per-PDE-solve time to a registration.
-PDE_PER_REG_FALLBACK = 200
+            "shear s=0, zero start, tol 1e-2; step = 5 independent pairs solved concurrently + det F1 each")
+# PDE solves of one zero-start registration of this workload as counted by
+# reg_solve on the GPU (stats n_pde: 5 Newton iterations, 38 matvecs, 5
+# line-search evaluations); scales the oracle's per-PDE-solve time to a
+# registration in the reference arm, which runs without a GPU.
+PDE_PER_REG = 93
 
 
 def peaks():
@@ -118,7 +121,7 @@ def run_reference(args):
     if rank != 0:
         return
     mT, mR = images()
-    pde_per_reg = PDE_PER_REG_FALLBACK
+    pde_per_reg = PDE_PER_REG
     for _ in range(args.warmup):
         pass  # the oracle has no warm-up effects worth paying 15 s for
     times = [cpu_oracle_pde_time(mT, mR) for _ in range(args.steps)]
@@ -170,21 +173,32 @@ def main():
         libbuild.build()
     from paper_1503_00757_gb300.binding import Context, default_opts
 
-    mT_np, mR_np = images(SEED + rank)
-    mT = torch.from_numpy(mT_np).to(dev)
-    mR = torch.from_numpy(mR_np).to(dev)
+    from paper_1503_00757_gb300.binding import Executor
+
+    # the step's batch: PAIRS independent registrations of this rank (seeds differ per rank)
+    pairs_np = [images(SEED + rank * PAIRS + i) for i in range(PAIRS)]
+    mT_np, mR_np = pairs_np[0]
+    pairs = [dict(mT=torch.from_numpy(a).to(dev), mR=torch.from_numpy(b).to(dev),
+                  v=torch.zeros(2, N_GRID, N_GRID, device=dev), nt=NT, regnorm=1, beta=BETA,
+                  gamma=math.inf, shear=0.0, detgrad=1) for a, b in pairs_np]
+    mT, mR = pairs[0]["mT"], pairs[0]["mR"]
     stream = torch.cuda.Stream(device=dev)
     ctx = Context(N_GRID, N_GRID, NT, regnorm=1, beta=BETA, gamma=math.inf, shear=0.0, stream=stream)
     v = torch.zeros(2, N_GRID, N_GRID, device=dev)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)  # > 129 MB L2
     opts = default_opts(tol=1e-2)
+    ex = Executor(PAIRS)
     stats = {}
 
-    def step():
+    def single():
         ctx.set_images(mT, mR)
         st = ctx.solve(v, opts)
         det = ctx.detgrad(v)
         return st, det
+
+    def step():
+        _, st = ex.solve(pairs, opts)
+        return st
 
     def barrier():
         if world > 1:
@@ -193,10 +207,10 @@ def main():
     if args.profile:
         with torch.cuda.stream(stream):
             for _ in range(args.warmup):
-                step()
+                single()
             torch.cuda.synchronize()
             l0 = ctx.launch_count()
-            st, _ = step()
+            st, _ = single()
             torch.cuda.synchronize()
         print(json.dumps({"profile": True, "launches_warmup": l0, "launches_step": ctx.launch_count() - l0,
                           "solve": {k: st[k] for k in ("n_newton", "n_mv", "n_pde", "n_ls")}}))
@@ -205,54 +219,83 @@ def main():
 
     with torch.cuda.stream(stream):
         for _ in range(args.warmup):
-            stats, det = step()
+            bstats = step()
         torch.cuda.synchronize()
         barrier()
         torch.cuda.synchronize()
         clocks = Clocks(local)
         clocks.start()
-        l0 = ctx.launch_count()
         total_ms = 0.0
+        wall = 0.0
         for _ in range(args.steps):
             flush.fill_(1.0)
+            torch.cuda.synchronize()
             e0 = torch.cuda.Event(enable_timing=True)
             e1 = torch.cuda.Event(enable_timing=True)
+            t0 = time.perf_counter()
             e0.record(stream)
-            stats, det = step()
+            bstats = step()  # synchronous: returns after every pair's work has finished
             e1.record(stream)
             e1.synchronize()
+            wall += time.perf_counter() - t0
             total_ms += e0.elapsed_time(e1)
         torch.cuda.synchronize()
         barrier()
         torch.cuda.synchronize()
         clk = clocks.stop()
-        launches = ctx.launch_count() - l0
         ms_step = total_ms / args.steps
         t = torch.tensor([ms_step], device=dev, dtype=torch.float64)
         if world > 1:
             dist.all_reduce(t, op=dist.ReduceOp.MAX)
         ms_step = float(t.item())
-        value = world * 1e3 / ms_step
+        value = world * PAIRS * 1e3 / ms_step
 
-        # e2e: same registration from pinned host buffers through reg_register_host
-        hT = torch.from_numpy(mT_np).pin_memory()
-        hR = torch.from_numpy(mR_np).pin_memory()
-        hv = torch.zeros(2 * N_GRID * N_GRID, dtype=torch.float32).pin_memory()
+        # single-registration latency (one pair alone on one stream)
+        for _ in range(2):
+            stats, det = single()
+        torch.cuda.synchronize()
+        lat = 0.0
+        nlat = 3
+        l0 = ctx.launch_count()
+        for _ in range(nlat):
+            flush.fill_(1.0)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            stats, det = single()
+            e1.record(stream)
+            e1.synchronize()
+            lat += e0.elapsed_time(e1)
+        launches_single = (ctx.launch_count() - l0) // nlat
+        launches = launches_single * PAIRS
+        lat /= nlat
+
+        # e2e: the same batch from pinned host buffers (H2D of images, D2H of velocities and stats inside)
+        hpairs = [(torch.from_numpy(a).pin_memory(), torch.from_numpy(b).pin_memory()) for a, b in pairs_np]
+        hv = [torch.empty(2, N_GRID, N_GRID, dtype=torch.float32).pin_memory() for _ in range(PAIRS)]
         torch.cuda.synchronize()
         e2e_ms = 0.0
         for _ in range(args.steps):
             flush.fill_(1.0)
             torch.cuda.synchronize()
-            t0 = time.perf_counter()
-            ctx.register_host(hT, hR, hv, opts)
-            ctx.detgrad(v)
-            torch.cuda.synchronize()
-            e2e_ms += (time.perf_counter() - t0) * 1e3
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for p, (a, b) in zip(pairs, hpairs):
+                p["mT"].copy_(a, non_blocking=True)
+                p["mR"].copy_(b, non_blocking=True)
+            stream.synchronize()
+            step()
+            for p, h in zip(pairs, hv):
+                h.copy_(p["v"], non_blocking=True)
+            e1.record(stream)
+            e1.synchronize()
+            e2e_ms += e0.elapsed_time(e1)
         e2e_ms /= args.steps
         et = torch.tensor([e2e_ms], device=dev, dtype=torch.float64)
         if world > 1:
             dist.all_reduce(et, op=dist.ReduceOp.MAX)
-        e2e_value = world * 1e3 / float(et.item())
+        e2e_value = world * PAIRS * 1e3 / float(et.item())
 
         # Hessian matvec throughput at a fixed linearization point (the converged v)
         g = torch.empty_like(v)
@@ -329,7 +372,7 @@ def main():
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
         t_pde = cpu_oracle_pde_time(mT_np, mR_np)
-        n_pde = stats.get("n_pde", PDE_PER_REG_FALLBACK)
+        n_pde = stats.get("n_pde", PDE_PER_REG)
         cpu = {"value": 1.0 / (t_pde * n_pde), "unit": "registrations/s", "cores": 1, "kind": "oracle",
                "sample": f"one FP64 oracle state solve (512^2, nt=32) = {t_pde:.1f} s, scaled by the "
                          f"{n_pde} PDE solves of the GPU registration"}
@@ -339,13 +382,16 @@ def main():
             "metric": METRIC, "value": value, "unit": "registrations/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "grid": [N_GRID, N_GRID], "nt": NT, "l2": "flushed between steps",
-                       "parallelism": f"replicas x{world}", "start": "zero (plain); warm start not built"},
+            "config": {"workload": WORKLOAD, "grid": [N_GRID, N_GRID], "nt": NT, "pairs_per_step": PAIRS,
+                       "l2": "flushed between steps", "parallelism": f"replicas x{world}, {PAIRS} concurrent streams",
+                       "start": "zero (plain); warm start not built"},
+            "latency_ms_single_registration": lat,
             "matvec_per_s": 1e3 / mv_ms, "ms_per_matvec": mv_ms,
             "solve": {k: stats[k] for k in ("n_newton", "n_mv", "n_pde", "n_ls", "gnorm_rel", "rnorm_rel_sq", "status")},
+            "solve_batch": [{k: b[k] for k in ("n_newton", "n_mv", "gnorm_rel", "rc")} for b in bstats],
             "detF": {"min": det[0], "mean": det[1], "max": det[2], "maxD": det[3]},
-            "e2e": {"value": e2e_value, "unit": "registrations/s", "h2d_bytes_per_step": 2 * 4 * N_GRID * N_GRID,
-                    "d2h_bytes_per_step": 2 * 4 * N_GRID * N_GRID + 5 * 8},
+            "e2e": {"value": e2e_value, "unit": "registrations/s", "h2d_bytes_per_step": PAIRS * 2 * 4 * N_GRID * N_GRID,
+                    "d2h_bytes_per_step": PAIRS * 2 * 4 * N_GRID * N_GRID},
             "gpu_launches": launches,
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": None, "kernel": names[dom],
@@ -362,6 +408,7 @@ def main():
         }
         print(json.dumps(line))
     ctx.close()
+    ex.close()
     if world > 1:
         dist.destroy_process_group()
 

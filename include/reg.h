@@ -178,10 +178,11 @@ int reg_register_host(reg_ctx* ctx, const float* mT_host, const float* mR_host, 
 /* ---- row a15: batched registration of many independent pairs ---- */
 
 /* One pair of a batch.  Inputs: grid, nt, regnorm, beta, gamma, shear (as in
- * reg_create), mT and mR (device, n1*n2 floats each).  In/out: v (device,
- * 2*n1*n2 floats; the initial guess when opts->warm_start, else ignored;
- * receives the solution).  Outputs: stats (filled) and status (the
- * reg_solve return code of this pair). */
+ * reg_create), mT and mR (device, n1*n2 floats each), want_detgrad (1: also
+ * run reg_detgrad on the solution).  In/out: v (device, 2*n1*n2 floats; the
+ * initial guess when opts->warm_start, else ignored; receives the solution).
+ * Outputs: stats, detgrad (min, mean, max det F1, max and mean D, when
+ * want_detgrad) and status (the reg_solve / reg_detgrad return code). */
 typedef struct {
     reg_grid grid;
     int nt;
@@ -190,7 +191,9 @@ typedef struct {
     const float* mT;
     const float* mR;
     float* v;
+    int want_detgrad;
     reg_solve_stats stats;
+    double detgrad[5];
     int status;
 } reg_batch_item;
 
@@ -203,6 +206,15 @@ typedef struct {
  * every pair returned REG_OK, else the first failing pair's status (each
  * item's own status is in item.status); REG_ERR_ARG for invalid arguments. */
 int reg_solve_batch(reg_batch_item* items, int count, const reg_solve_opts* opts, int nworkers);
+
+/* A persistent batch executor: the same scheduling as reg_solve_batch, but
+ * its worker streams, per-grid-size contexts and their captured launch
+ * sequences stay alive across calls (reg_solve_batch builds and frees one per
+ * call).  Create on the device that will run the pairs (nworkers <= 0: 8). */
+typedef struct reg_executor reg_executor;
+int reg_executor_create(int nworkers, reg_executor** out);
+int reg_executor_solve(reg_executor* ex, reg_batch_item* items, int count, const reg_solve_opts* opts);
+void reg_executor_destroy(reg_executor* ex);
 
 /* ---- row a14: deformation gradient (Eq. (e:def-grad)) ---- */
 

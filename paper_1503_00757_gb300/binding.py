@@ -43,8 +43,8 @@ class reg_solve_stats(ctypes.Structure):
 class reg_batch_item(ctypes.Structure):
     _fields_ = [("grid", reg_grid), ("nt", ctypes.c_int), ("regnorm", ctypes.c_int), ("beta", ctypes.c_double),
                 ("gamma", ctypes.c_double), ("shear", ctypes.c_double), ("mT", ctypes.c_void_p),
-                ("mR", ctypes.c_void_p), ("v", ctypes.c_void_p), ("stats", reg_solve_stats),
-                ("status", ctypes.c_int)]
+                ("mR", ctypes.c_void_p), ("v", ctypes.c_void_p), ("want_detgrad", ctypes.c_int),
+                ("stats", reg_solve_stats), ("detgrad", ctypes.c_double * 5), ("status", ctypes.c_int)]
 
 
 _P = ctypes.c_void_p
@@ -75,6 +75,9 @@ _SIGS = {
     "reg_spectral_grad_static": ([reg_grid, _P, _P, _P], _I),
     "reg_set_params": ([_P, _I, _I, _D, _D, _D], _I),
     "reg_solve_batch": ([ctypes.POINTER(reg_batch_item), _I, ctypes.POINTER(reg_solve_opts), _I], _I),
+    "reg_executor_create": ([_I, ctypes.POINTER(_P)], _I),
+    "reg_executor_solve": ([_P, ctypes.POINTER(reg_batch_item), _I, ctypes.POINTER(reg_solve_opts)], _I),
+    "reg_executor_destroy": ([_P], None),
 }
 
 _lib = None
@@ -137,11 +140,7 @@ def spectral_grad_static(f, grad_f, stream=None):
                                           handle))
 
 
-def solve_batch(pairs, opts=None, nworkers=8, check=True):
-    """Batched registration (reg_solve_batch).  pairs: list of dicts with CUDA
-    float32 tensors mT (n1, n2), mR (n1, n2), v (2, n1, n2) and the problem
-    parameters nt, regnorm, beta, gamma, shear.  v is overwritten with each
-    solution.  Returns (status, list of per-pair stats dicts)."""
+def _batch_items(pairs):
     n = len(pairs)
     arr = (reg_batch_item * n)()
     for i, p in enumerate(pairs):
@@ -153,16 +152,63 @@ def solve_batch(pairs, opts=None, nworkers=8, check=True):
         it.mT = _ptr(p["mT"], n1 * n2, "mT")
         it.mR = _ptr(p["mR"], n1 * n2, "mR")
         it.v = _ptr(p["v"], 2 * n1 * n2, "v")
-    o = opts if opts is not None else default_opts()
-    rc = lib().reg_solve_batch(arr, n, ctypes.byref(o), int(nworkers))
-    if check:
-        _check(rc)
+        it.want_detgrad = int(p.get("detgrad", 0))
+    return arr
+
+
+def _batch_stats(arr):
     out = []
-    for i in range(n):
+    for i in range(len(arr)):
         d = arr[i].stats.as_dict()
         d["rc"] = arr[i].status
+        if arr[i].want_detgrad:
+            d["detgrad"] = tuple(arr[i].detgrad)
         out.append(d)
-    return rc, out
+    return out
+
+
+class Executor:
+    """Persistent batch executor (reg_executor_*): worker streams and per-size
+    contexts survive across solve() calls."""
+
+    def __init__(self, nworkers=8):
+        h = ctypes.c_void_p()
+        _check(lib().reg_executor_create(int(nworkers), ctypes.byref(h)))
+        self.h = h
+
+    def solve(self, pairs, opts=None, check=True):
+        """Same arguments and results as solve_batch."""
+        arr = _batch_items(pairs)
+        o = opts if opts is not None else default_opts()
+        rc = lib().reg_executor_solve(self.h, arr, len(pairs), ctypes.byref(o))
+        if check:
+            _check(rc)
+        return rc, _batch_stats(arr)
+
+    def close(self):
+        if self.h:
+            lib().reg_executor_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def solve_batch(pairs, opts=None, nworkers=8, check=True):
+    """Batched registration (reg_solve_batch).  pairs: list of dicts with CUDA
+    float32 tensors mT (n1, n2), mR (n1, n2), v (2, n1, n2), the problem
+    parameters nt, regnorm, beta, gamma, shear and optionally detgrad=1.  v is
+    overwritten with each solution.  Returns (status, list of per-pair stats
+    dicts, with "detgrad" when requested)."""
+    arr = _batch_items(pairs)
+    o = opts if opts is not None else default_opts()
+    rc = lib().reg_solve_batch(arr, len(pairs), ctypes.byref(o), int(nworkers))
+    if check:
+        _check(rc)
+    return rc, _batch_stats(arr)
 
 
 class Context:

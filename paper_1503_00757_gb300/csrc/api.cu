@@ -192,7 +192,9 @@ extern "C" int reg_create(reg_grid grid, int nt, int regnorm, double beta, doubl
 extern "C" int reg_set_params(reg_ctx* c, int nt, int regnorm, double beta, double gamma, double shear) {
     if (!c) return reg_fail(REG_ERR_ARG, "ctx is NULL");
     RET(check_params(nt, regnorm, beta, gamma, shear));
-    clear_graphs(c);  // captured sequences bake in nt and the Fourier-multiplier parameters
+    const bool same = nt == c->nt && regnorm == c->regnorm && beta == c->beta_v && gamma == c->beta_w &&
+                      shear == c->shear;
+    if (!same) clear_graphs(c);  // captured sequences bake in nt and the Fourier-multiplier parameters
     set_params(c, nt, regnorm, beta, gamma, shear);
     return alloc_hist(c, nt);
 }
@@ -210,7 +212,7 @@ extern "C" int reg_set_stream(reg_ctx* c, void* stream) {
 // Sequences run directly on the legacy default stream (it cannot be
 // captured) and while per-kernel timing is on.
 // ---------------------------------------------------------------------------
-enum GraphKind { GK_OBJECTIVE = 1, GK_GRADIENT = 2, GK_MATVEC = 3, GK_PCG_ITER = 4, GK_PCG_INIT = 5 };
+enum GraphKind { GK_OBJECTIVE = 1, GK_GRADIENT = 2, GK_MATVEC = 3, GK_PCG_ITER = 4, GK_PCG_INIT = 5, GK_DETGRAD = 6 };
 
 template <typename F>
 static int run_seq(reg_ctx* c, int kind, const void* p0, const void* p1, int nt, F&& body) {
@@ -839,32 +841,36 @@ extern "C" int reg_register_host(reg_ctx* c, const float* mT_host, const float* 
 // ---------------------------------------------------------------------------
 // deformation gradient (Eq. (e:def-grad)) and its measures (Appendix F)
 // ---------------------------------------------------------------------------
-extern "C" int reg_detgrad(reg_ctx* c, const float* v, float* detF, double* stats) {
-    CTX_CHECK(c);
-    RET(check_ptr(v, "v"));
-    if (detF) RET(check_ptr(detF, "detF"));
+static void detgrad_launches(reg_ctx* c, const float* v, float* detF, int nt) {
     const size_t N = c->N;
-    const int nt = c->nt;
     const float h = 1.0f / (float)nt;
     sp_grad_vec(c, v, c->gv);
-    // F = I
-    launch_fill(c, 4 * (long long)N, c->F, 0.f);
-    launch_fill(c, N, c->F, 1.f);
-    launch_fill(c, N, c->F + 3 * N, 1.f);
+    float* Fa = c->F;     // F_j
+    float* Fb = c->gtmp;  // F_{j+1} (ping-pong)
+    launch_fill(c, 4 * (long long)N, Fa, 0.f);  // F(0) = I
+    launch_fill(c, N, Fa, 1.f);
+    launch_fill(c, N, Fa + 3 * N, 1.f);
     for (int j = 0; j < nt; ++j) {
-        for (int comp = 0; comp < 4; ++comp) sp_grad(c, c->F + comp * N, c->gF + 2 * comp * N);
-        launch_defgrad_stage(c, 1, c->F, nullptr, c->gF, c->gv, v, h, c->Fs);
+        for (int comp = 0; comp < 4; ++comp) sp_grad(c, Fa + comp * N, c->gF + 2 * comp * N);
+        launch_defgrad_stage(c, 1, Fa, nullptr, c->gF, c->gv, v, h, c->Fs);
         for (int comp = 0; comp < 4; ++comp) sp_grad(c, c->Fs + comp * N, c->gF + 2 * comp * N);
-        launch_defgrad_stage(c, 2, c->F, c->Fs, c->gF, c->gv, v, h, c->gtmp);
-        CK(cudaMemcpyAsync(c->F, c->gtmp, sizeof(float) * 4 * N, cudaMemcpyDeviceToDevice, c->stream));
+        launch_defgrad_stage(c, 2, Fa, c->Fs, c->gF, c->gv, v, h, Fb);
+        float* t = Fa; Fa = Fb; Fb = t;
     }
-    const int np = launch_det_stats(c, c->F, detF, c->d_part);
+    const int np = launch_det_stats(c, Fa, detF, c->d_part);
     launch_finalize(c, c->d_part + 0 * np, np, c->d_scal + SL_DET0 + 0, 1.0, 0, 2);
     launch_finalize(c, c->d_part + 1 * np, np, c->d_scal + SL_DET0 + 1, 1.0 / (double)N, 0, 0);
     launch_finalize(c, c->d_part + 2 * np, np, c->d_scal + SL_DET0 + 2, 1.0, 0, 1);
     launch_finalize(c, c->d_part + 3 * np, np, c->d_scal + SL_DET0 + 3, 1.0, 0, 1);
     launch_finalize(c, c->d_part + 4 * np, np, c->d_scal + SL_DET0 + 4, 1.0 / (double)N, 0, 0);
-    CKL();
+}
+
+extern "C" int reg_detgrad(reg_ctx* c, const float* v, float* detF, double* stats) {
+    CTX_CHECK(c);
+    RET(check_ptr(v, "v"));
+    if (detF) RET(check_ptr(detF, "detF"));
+    const int nt = c->nt;
+    RET(run_seq(c, GK_DETGRAD, v, detF, nt, [&] { detgrad_launches(c, v, detF, nt); }));
     if (stats) {
         RET(read_scalars(c));
         for (int q = 0; q < 5; ++q) stats[q] = c->h_scal[SL_DET0 + q];

@@ -23,7 +23,7 @@ def _batch(nt=8):
     rng = np.random.default_rng(4000)
     pairs = []
     for i, n in enumerate([64, 32, 64, 128, 32, 64]):
-        mT, mR, _ = synth.ellipses_pair(n, 4000 + i, vmax=0.25 * 2 * np.pi * nt / n)
+        mT, mR, _ = synth.ellipses_pair(n, 4000 + i, vmax=0.25 * 2 * np.pi * nt / n, kmax=min(16, n // 4))
         regnorm = int(rng.choice([1, 2]))
         gamma = [0.0, 1e-3, math.inf][int(rng.integers(3))]
         beta = [1e-2, 1e-3][int(rng.integers(2))]
