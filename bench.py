@@ -148,6 +148,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--matvecs", type=int, default=200)
+    ap.add_argument("--no-warm", dest="warm", action="store_false",
+                    help="skip the warm-start comparison")
     ap.add_argument("--no-big", dest="big", action="store_false",
                     help="skip the 1024^2 matvec measurement")
     ap.add_argument("--profile", action="store_true",
@@ -364,6 +366,28 @@ def main():
                                           "pointwise/reduction"][bd], "achieved": ach, "launches": bcls[bd][0]}
             big["kernel_classes"] = {str(k): {"launches": bcls[k][0], "ms": bcls[k][1], "GB": bcls[k][2] / 1e9}
                                      for k in bcls}
+        # learned warm start vs plain zero start (C5 workload, 256^2, nt=16) with the committed weights
+        warm = None
+        wpath = os.path.join(ROOT, "paper_1503_00757_gb300", "weights", "warmstart_n256.npy")
+        if args.warm and os.path.exists(wpath):
+            from paper_1503_00757_gb300 import warmstart as ws
+            from paper_1503_00757_gb300.binding import Net
+            xw = ws.make_images(256, range(ws.TEST_SEED, ws.TEST_SEED + 16))
+            exw = Executor(8)
+            netw = Net(256, 256, 8)
+            netw.set_params(torch.from_numpy(np.load(wpath).astype(np.float32)).to(dev))
+            ws.solve_all(xw[:8], exw, opts)  # warm-up (contexts, graphs)
+            _, st0, s0 = ws.solve_all(xw, exw, opts)
+            t0 = time.perf_counter()
+            vp = ws.predict(netw, xw, 8)
+            sp = time.perf_counter() - t0
+            _, st1, s1 = ws.solve_all(xw, exw, default_opts(tol=1e-2, warm_start=1), v0=vp)
+            z, w_ = ws.summarize(st0, s0), ws.summarize(st1, s1 + sp)
+            warm = {"workload": "C5 256x256, nt=16, H1, beta_v=1e-3, incompressible, 16 held-out pairs, tol 1e-2",
+                    "plain": z, "warm": w_, "matvec_reduction": 1.0 - w_["matvec_mean"] / z["matvec_mean"],
+                    "speedup": w_["registrations_per_s"] / z["registrations_per_s"]}
+            netw.close()
+            exw.close()
     dom = max(classes, key=lambda k: classes[k][1])
     n_dom, ms_dom, bytes_dom = classes[dom]
     peak, peak_kind = peaks()
@@ -384,8 +408,9 @@ def main():
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": WORKLOAD, "grid": [N_GRID, N_GRID], "nt": NT, "pairs_per_step": PAIRS,
                        "l2": "flushed between steps", "parallelism": f"replicas x{world}, {PAIRS} concurrent streams",
-                       "start": "zero (plain); warm start not built"},
+                       "start": "zero (plain); warm start reported in warm_start_vs_plain"},
             "latency_ms_single_registration": lat,
+            "warm_start_vs_plain": warm,
             "matvec_per_s": 1e3 / mv_ms, "ms_per_matvec": mv_ms,
             "solve": {k: stats[k] for k in ("n_newton", "n_mv", "n_pde", "n_ls", "gnorm_rel", "rnorm_rel_sq", "status")},
             "solve_batch": [{k: b[k] for k in ("n_newton", "n_mv", "gnorm_rel", "rc")} for b in bstats],

@@ -223,6 +223,34 @@ void reg_executor_destroy(reg_executor* ex);
  * mean of D = ||F1 - I||_F (Appendix F). */
 int reg_detgrad(reg_ctx* ctx, const float* v, float* detF, double* stats);
 
+/* ---- row a16: learned warm start (the paper has no learned component) ---- */
+
+/* An 8-layer 3x3 convolutional network with circular padding (channel
+ * widths 2 -> 32 (x7) -> 2, ReLU between layers) mapping an image pair to a
+ * velocity, Leray-projected (Eq. (e:project-body-force) with w = 0) so that
+ * it satisfies div v = 0.  BF16 activations and weights on the tensor cores
+ * with FP32 accumulation; FP32 master weights; Adam (0.9, 0.999, 1e-8).
+ * Parameters are a flat FP32 array: for each layer W (Cout, Cin, 3, 3), with
+ * W[o, c, dy+1, dx+1] multiplying the input at (y+dy, x+dx), then b (Cout).
+ * images: device, B x 2 x H x W floats (per sample m_T then m_R);
+ * velocities / targets: device, B x 2 x H x W floats (component planes).
+ * H, W powers of two in [32, 1024]; 1 <= B <= max_batch. */
+typedef struct reg_net reg_net;
+int reg_net_create(int H, int W, int max_batch, reg_net** out);
+void reg_net_destroy(reg_net* net);
+long long reg_net_num_params(reg_net* net);
+int reg_net_set_stream(reg_net* net, void* stream);
+/* Copy parameters in (device, num_params floats; resets the Adam state) / out. */
+int reg_net_set_params(reg_net* net, const float* params);
+int reg_net_get_params(reg_net* net, float* params);
+/* Leray-projected prediction v_out. */
+int reg_net_forward(reg_net* net, const float* images, int B, float* v_out);
+/* loss = sum((P net(x) - t)^2) / (2 M) (M = 2 B H W, host double) and, if grads
+ * is not NULL, its gradient w.r.t. the flat parameters (device).  Synchronous. */
+int reg_net_loss_grad(reg_net* net, const float* images, const float* targets, int B, double* loss, float* grads);
+/* One Adam step with learning rate lr on that loss.  Synchronous (loss is read back). */
+int reg_net_train_step(reg_net* net, const float* images, const float* targets, int B, float lr, double* loss);
+
 /* ---- allocation-free entry point (the paper has no counterpart) ---- */
 
 /* The spectral gradient of reg_spectral_grad for callers that cannot

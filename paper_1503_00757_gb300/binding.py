@@ -78,6 +78,15 @@ _SIGS = {
     "reg_executor_create": ([_I, ctypes.POINTER(_P)], _I),
     "reg_executor_solve": ([_P, ctypes.POINTER(reg_batch_item), _I, ctypes.POINTER(reg_solve_opts)], _I),
     "reg_executor_destroy": ([_P], None),
+    "reg_net_create": ([_I, _I, _I, ctypes.POINTER(_P)], _I),
+    "reg_net_destroy": ([_P], None),
+    "reg_net_num_params": ([_P], ctypes.c_longlong),
+    "reg_net_set_stream": ([_P, _P], _I),
+    "reg_net_set_params": ([_P, _P], _I),
+    "reg_net_get_params": ([_P, _P], _I),
+    "reg_net_forward": ([_P, _P, _I, _P], _I),
+    "reg_net_loss_grad": ([_P, _P, _P, _I, ctypes.POINTER(_D), _P], _I),
+    "reg_net_train_step": ([_P, _P, _P, _I, ctypes.c_float, ctypes.POINTER(_D)], _I),
 }
 
 _lib = None
@@ -209,6 +218,74 @@ def solve_batch(pairs, opts=None, nworkers=8, check=True):
     if check:
         _check(rc)
     return rc, _batch_stats(arr)
+
+
+class Net:
+    """Warm-start network (reg_net_*): H x W images, batches of up to max_batch."""
+
+    def __init__(self, H, W, max_batch, stream=None):
+        h = ctypes.c_void_p()
+        _check(lib().reg_net_create(H, W, max_batch, ctypes.byref(h)))
+        self.h, self.H, self.W = h, H, W
+        self.nparams = lib().reg_net_num_params(h)
+        if stream is not None:
+            _check(lib().reg_net_set_stream(h, ctypes.c_void_p(stream.cuda_stream)))
+
+    def close(self):
+        if self.h:
+            lib().reg_net_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_params(self, p):
+        _check(lib().reg_net_set_params(self.h, _ptr(p, self.nparams, "params")))
+
+    def get_params(self, p):
+        _check(lib().reg_net_get_params(self.h, _ptr(p, self.nparams, "params")))
+
+    def forward(self, images, v_out):
+        B = images.shape[0]
+        n = B * 2 * self.H * self.W
+        _check(lib().reg_net_forward(self.h, _ptr(images, n, "images"), B, _ptr(v_out, n, "v_out")))
+
+    def loss_grad(self, images, targets, grads=None):
+        B = images.shape[0]
+        n = B * 2 * self.H * self.W
+        loss = ctypes.c_double()
+        _check(lib().reg_net_loss_grad(self.h, _ptr(images, n, "images"), _ptr(targets, n, "targets"), B,
+                                       ctypes.byref(loss), _ptr(grads, self.nparams, "grads")))
+        return loss.value
+
+    def train_step(self, images, targets, lr):
+        B = images.shape[0]
+        n = B * 2 * self.H * self.W
+        loss = ctypes.c_double()
+        _check(lib().reg_net_train_step(self.h, _ptr(images, n, "images"), _ptr(targets, n, "targets"), B,
+                                        ctypes.c_float(lr), ctypes.byref(loss)))
+        return loss.value
+
+
+def flatten_params(params):
+    """Oracle parameter list [(W, b), ...] -> flat array in the reg_net order."""
+    import numpy as np
+    return np.concatenate([np.concatenate([W.ravel(), b.ravel()]) for W, b in params])
+
+
+def unflatten_params(flat, channels):
+    import numpy as np
+    out, o = [], 0
+    for cin, cout in zip(channels[:-1], channels[1:]):
+        W = np.asarray(flat[o:o + cout * cin * 9]).reshape(cout, cin, 3, 3)
+        o += cout * cin * 9
+        b = np.asarray(flat[o:o + cout])
+        o += cout
+        out.append((W, b))
+    return out
 
 
 class Context:

@@ -1,0 +1,162 @@
+"""Learned warm start for the Newton-Krylov registration (row a16).
+
+Pipeline (all compute on the GPU through the C ABI):
+  1. seeded synthetic pairs (``synth.ellipses_pair``) at n x n;
+  2. targets = the plain zero-start solver's converged velocities
+     (H1, incompressible, beta_v = 1e-3, nt = 16, relative gradient 1e-2),
+     computed with the batch executor (``reg_executor_solve``);
+  3. training of the 8-layer convolutional network (``reg_net_train_step``,
+     Adam, mini-batches) on (m_T, m_R) -> v;
+  4. evaluation on held-out pairs: the same solve from v_0 = 0 and from the
+     network's prediction (``opts.warm_start = 1``; the stopping test keeps
+     g_ref = g(0), so both starts target the same absolute gradient).
+
+Usage (GPU):  python -m paper_1503_00757_gb300.warmstart --train 1000 --test 100
+"""
+import argparse
+import json
+import math
+import os
+import time
+
+import numpy as np
+
+N_DEFAULT, NT, BETA, VMAX = 256, 16, 1e-3, 0.098
+TRAIN_SEED, TEST_SEED = 5_000_000, 6_000_000
+
+
+def make_images(n, seeds, vmax=VMAX):
+    from . import synth
+    x = np.empty((len(seeds), 2, n, n), dtype=np.float32)
+    for i, s in enumerate(seeds):
+        mT, mR, _ = synth.ellipses_pair(n, s, vmax=vmax, kmax=min(16, n // 4))
+        x[i, 0], x[i, 1] = mT, mR
+    return x
+
+
+def solve_all(images, executor, opts, v0=None, chunk=64):
+    """Solve every pair (zero start, or warm start from v0); returns (v, stats, seconds)."""
+    import torch
+    n = images.shape[-1]
+    B = images.shape[0]
+    v_out = torch.empty((B, 2, n, n), dtype=torch.float32, device="cuda")
+    stats = []
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for s in range(0, B, chunk):
+        e = min(B, s + chunk)
+        pairs = []
+        for i in range(s, e):
+            img = torch.from_numpy(images[i]).cuda()
+            v = v_out[i]
+            if v0 is not None:
+                v.copy_(v0[i])
+            pairs.append(dict(mT=img[0].contiguous(), mR=img[1].contiguous(), v=v, nt=NT, regnorm=1, beta=BETA,
+                              gamma=math.inf, shear=0.0))
+        _, st = executor.solve(pairs, opts, check=False)
+        stats.extend(st)
+    torch.cuda.synchronize()
+    return v_out, stats, time.perf_counter() - t0
+
+
+def train(net, images, targets, epochs, batch, lr, seed=0, log=None):
+    import torch
+    rng = np.random.default_rng(seed)
+    B = images.shape[0]
+    x_all = torch.from_numpy(images).cuda()
+    losses = []
+    for ep in range(epochs):
+        perm = rng.permutation(B)
+        tot = 0.0
+        nb = 0
+        for s in range(0, B - batch + 1, batch):
+            idx = torch.from_numpy(perm[s:s + batch]).cuda()
+            xb = x_all.index_select(0, idx).contiguous()
+            tb = targets.index_select(0, idx).contiguous()
+            tot += net.train_step(xb, tb, lr * (0.5 ** (ep // max(1, epochs // 3))))
+            nb += 1
+        losses.append(tot / max(nb, 1))
+        if log:
+            log(f"epoch {ep}: loss {losses[-1]:.4e}")
+    return losses
+
+
+def predict(net, images, batch):
+    import torch
+    B, _, n, _ = images.shape
+    out = torch.empty((B, 2, n, n), dtype=torch.float32, device="cuda")
+    for s in range(0, B, batch):
+        e = min(B, s + batch)
+        xb = torch.from_numpy(images[s:e]).cuda().contiguous()
+        net.forward(xb, out[s:e])
+    torch.cuda.synchronize()
+    return out
+
+
+def summarize(stats, seconds):
+    ok = [s for s in stats if s["rc"] == 0]
+    return {"pairs": len(stats), "converged": len(ok),
+            "newton_mean": float(np.mean([s["n_newton"] for s in stats])),
+            "matvec_mean": float(np.mean([s["n_mv"] for s in stats])),
+            "gnorm_rel_max": float(max(s["gnorm_rel"] for s in stats)),
+            "seconds": seconds, "registrations_per_s": len(stats) / seconds}
+
+
+def main():
+    import torch
+    from oracle import cnn as oracle_cnn  # initial parameters only (He initialisation)
+    from .binding import Executor, Net, default_opts, flatten_params
+
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--n", type=int, default=N_DEFAULT)
+    ap.add_argument("--train", type=int, default=1000)
+    ap.add_argument("--test", type=int, default=100)
+    ap.add_argument("--epochs", type=int, default=30)
+    ap.add_argument("--batch", type=int, default=8)
+    ap.add_argument("--lr", type=float, default=2e-3)
+    ap.add_argument("--workers", type=int, default=8)
+    ap.add_argument("--out", default="gpurun_out/warmstart.json")
+    ap.add_argument("--weights", default="gpurun_out/warmstart_weights.npy")
+    args = ap.parse_args()
+    log = lambda m: print(m, flush=True)
+    n = args.n
+    opts = default_opts(tol=1e-2, maxit_newton=50)
+    ex = Executor(args.workers)
+    t = time.perf_counter()
+    x_tr = make_images(n, range(TRAIN_SEED, TRAIN_SEED + args.train))
+    x_te = make_images(n, range(TEST_SEED, TEST_SEED + args.test))
+    log(f"images: {time.perf_counter() - t:.1f} s")
+    v_tr, st_tr, sec_tr = solve_all(x_tr, ex, opts)
+    log(f"targets: {sec_tr:.1f} s, {summarize(st_tr, sec_tr)}")
+    keep = [i for i, s in enumerate(st_tr) if s["rc"] == 0]
+    x_tr = x_tr[keep]
+    v_tr = v_tr[torch.tensor(keep, device="cuda")].contiguous()
+    net = Net(n, n, args.batch)
+    net.set_params(torch.tensor(flatten_params(oracle_cnn.init_params(1)), dtype=torch.float32, device="cuda"))
+    t = time.perf_counter()
+    losses = train(net, x_tr, v_tr, args.epochs, args.batch, args.lr, log=log)
+    train_s = time.perf_counter() - t
+    # evaluation: zero start vs warm start on held-out pairs
+    _, st_zero, sec_zero = solve_all(x_te, ex, opts)
+    t = time.perf_counter()
+    v_pred = predict(net, x_te, args.batch)
+    pred_s = time.perf_counter() - t
+    wopts = default_opts(tol=1e-2, maxit_newton=50, warm_start=1)
+    _, st_warm, sec_warm = solve_all(x_te, ex, wopts, v0=v_pred)
+    res = {"n": n, "nt": NT, "beta_v": BETA, "train_pairs": len(keep), "test_pairs": args.test,
+           "epochs": args.epochs, "batch": args.batch, "train_seconds": train_s, "loss_first": losses[0],
+           "loss_last": losses[-1], "zero_start": summarize(st_zero, sec_zero),
+           "warm_start": summarize(st_warm, sec_warm + pred_s), "predict_seconds": pred_s}
+    log(json.dumps(res))
+    os.makedirs(os.path.dirname(args.out) or ".", exist_ok=True)
+    with open(args.out, "w") as f:
+        json.dump(res, f, indent=1)
+    p = torch.empty(net.nparams, device="cuda")
+    net.get_params(p)
+    np.save(args.weights, p.cpu().numpy())
+    net.close()
+    ex.close()
+
+
+if __name__ == "__main__":
+    main()
