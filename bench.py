@@ -154,6 +154,8 @@ def main():
                     help="skip the 1024^2 matvec measurement")
     ap.add_argument("--profile", action="store_true",
                     help="run --warmup registrations then one registration and exit (for ncu launch lists)")
+    ap.add_argument("--profile-grid", type=int, default=0,
+                    help="with --profile: instead run a gradient and 3 GN matvecs on this grid (nt=32)")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
@@ -205,6 +207,25 @@ def main():
     def barrier():
         if world > 1:
             dist.barrier()
+
+    if args.profile and args.profile_grid:
+        nb = args.profile_grid
+        from paper_1503_00757_gb300 import synth
+        bT, bR, bv = synth.ellipses_pair(nb, SEED, vmax=VMAX * N_GRID / nb)
+        cb = Context(nb, nb, NT, regnorm=1, beta=BETA, gamma=math.inf, shear=0.0, stream=stream)
+        with torch.cuda.stream(stream):
+            cb.set_images(torch.from_numpy(bT.astype(np.float32)).to(dev), torch.from_numpy(bR.astype(np.float32)).to(dev))
+            vb = torch.from_numpy((0.5 * bv).astype(np.float32)).to(dev).contiguous()
+            gb = torch.empty_like(vb)
+            cb.gradient(vb, gb)
+            vtb = torch.randn_like(vb)
+            Hb = torch.empty_like(vb)
+            for _ in range(3):
+                cb.hessian_matvec(vtb, Hb)
+            torch.cuda.synchronize()
+        print(json.dumps({"profile": True, "grid": nb, "launches": cb.launch_count()}))
+        cb.close()
+        return
 
     if args.profile:
         with torch.cuda.stream(stream):

@@ -57,3 +57,19 @@ def test_invalid_arguments_rejected_without_gpu(lib):
         assert lib.reg_create(*args, ctypes.byref(h)) == 1
         assert not h.value
     assert lib.reg_last_error()
+
+
+def test_new_entry_points_reject_invalid_arguments_without_gpu(lib):
+    from paper_1503_00757_gb300.binding import reg_grid
+    h = ctypes.c_void_p()
+    # warm-start network: sizes must be powers of two in [32, 1024], batch in [1, 256]
+    assert lib.reg_net_create(48, 64, 4, ctypes.byref(h)) == 1
+    assert lib.reg_net_create(64, 64, 0, ctypes.byref(h)) == 1
+    assert lib.reg_net_create(2048, 64, 4, ctypes.byref(h)) == 1
+    # batch executor: at most 256 workers
+    assert lib.reg_executor_create(1000, ctypes.byref(h)) == 1
+    assert lib.reg_solve_batch(None, -1, None, 1) == 1
+    # allocation-free gradient: scratch limit of 512 x 512 nodes
+    assert lib.reg_spectral_grad_static(reg_grid(1024, 512), None, None, None) == 1
+    assert b"scratch" in lib.reg_last_error()
+    assert lib.reg_spectral_grad_static(reg_grid(12, 16), None, None, None) == 1
