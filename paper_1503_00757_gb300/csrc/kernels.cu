@@ -140,6 +140,14 @@ __device__ double block_reduce(double v) {
 // Shared memory: region A (R*L float2: staging) + region X (2*R*L float2:
 // FFT exchange buffers, 2*L per FFT).
 // ---------------------------------------------------------------------------
+// Minimum resident CTAs per SM requested from the compiler for the RK2 row
+// kernels: rows of 1024 use 512-thread CTAs, and two of them per SM keep the
+// 256-CTA grid of a 1024 x 1024 field in one wave.
+template <int LOGL>
+struct RowBlocks {
+    static constexpr int value = LOGL >= 10 ? 2 : 1;
+};
+
 template <int LOGL>
 __device__ __forceinline__ void stage_chunk(float2* dst, const float2* __restrict__ src, int n) {
     const float4* s4 = reinterpret_cast<const float4*>(src);
@@ -243,7 +251,8 @@ __global__ void __launch_bounds__(512) k_c2r(const float2* __restrict__ S1, cons
 // result u_out leaves as its packed spectrum S_out for the next column pass.
 // ---------------------------------------------------------------------------
 template <int LOGL>
-__global__ void __launch_bounds__(512) k_row_adv(AdvArgs a, int N, int R, const float2* __restrict__ tw) {
+__global__ void __launch_bounds__(512, RowBlocks<LOGL>::value) k_row_adv(AdvArgs a, int N, int R,
+                                                                           const float2* __restrict__ tw) {
     extern __shared__ __align__(16) float2 sm[];
     constexpr int L = 1 << LOGL, T = L >> 3, W = L >> 1;
     float2* A = sm;
@@ -254,16 +263,22 @@ __global__ void __launch_bounds__(512) k_row_adv(AdvArgs a, int N, int R, const 
     const size_t rowbase = (size_t)(row0 + q) * L;
     // Operands written at least two launches earlier (u_j, u*, v, grad m, v~) are
     // loaded before waiting on the preceding column kernel; only G depends on it.
-    // u_j == nullptr stands for u_j = 0 (the incremental state at t = 0).
+    // u_j == nullptr stands for u_j = 0 (the incremental state at t = 0).  For
+    // the longest rows the operands are read after the FFT instead, which keeps
+    // the register count low enough for two CTAs per SM.
+    constexpr bool PRE = RowBlocks<LOGL>::value == 1;
     float pv1[8], pv2[8], puj[8], pus[8], psrc[8];
-#pragma unroll
-    for (int k = 0; k < 8; ++k) {
+    auto load_ops = [&](int k) {
         const size_t idx = rowbase + t + k * T;
         pv1[k] = a.v[idx];
         pv2[k] = a.v[N + idx];
         puj[k] = a.uj ? a.uj[idx] : 0.f;
         pus[k] = (a.stage == 2) ? a.us[idx] : 0.f;
         psrc[k] = a.gm ? -(a.vt[idx] * a.gm[idx] + a.vt[N + idx] * a.gm[N + idx]) : 0.f;
+    };
+    if (PRE) {
+#pragma unroll
+        for (int k = 0; k < 8; ++k) load_ops(k);
     }
     pdl_entry();
     float2 x[8];
@@ -281,6 +296,7 @@ __global__ void __launch_bounds__(512) k_row_adv(AdvArgs a, int N, int R, const 
     float out[8];
 #pragma unroll
     for (int k = 0; k < 8; ++k) {
+        if (!PRE) load_ops(k);
         const size_t idx = rowbase + t + k * T;
         const float d1 = x[k].x, d2 = x[k].y;
         if (a.grad_out) {
@@ -343,7 +359,8 @@ __device__ __forceinline__ void flux_fft_store(float2 (&x)[8], int q, int t, int
 }
 
 template <int LOGL>
-__global__ void __launch_bounds__(512) k_row_adj(AdjArgs a, int N, int R, const float2* __restrict__ tw) {
+__global__ void __launch_bounds__(512, RowBlocks<LOGL>::value) k_row_adj(AdjArgs a, int N, int R,
+                                                                           const float2* __restrict__ tw) {
     extern __shared__ __align__(16) float2 sm[];
     constexpr int L = 1 << LOGL, T = L >> 3, W = L >> 1;
     float2* A = sm;
@@ -352,10 +369,11 @@ __global__ void __launch_bounds__(512) k_row_adj(AdjArgs a, int N, int R, const 
     const int row0 = blockIdx.x * R;
     const size_t rowbase = (size_t)(row0 + q) * L;
     // Operands written at least two launches earlier (lam_j, lam*, v, b, grad m)
-    // are loaded before waiting on the preceding column kernel, which writes D.
+    // are loaded before waiting on the preceding column kernel, which writes D
+    // (after the FFT for the longest rows, as in k_row_adv).
+    constexpr bool PRE = RowBlocks<LOGL>::value == 1;
     float plj[8], pls[8], pv1[8], pv2[8], pb1[8], pb2[8], pg1[8], pg2[8];
-#pragma unroll
-    for (int k = 0; k < 8; ++k) {
+    auto load_ops = [&](int k) {
         const size_t idx = rowbase + t + k * T;
         plj[k] = a.lj[idx];
         pls[k] = (a.stage == 2) ? a.ls[idx] : 0.f;
@@ -367,6 +385,10 @@ __global__ void __launch_bounds__(512) k_row_adj(AdjArgs a, int N, int R, const 
             pg1[k] = a.gm[idx];
             pg2[k] = a.gm[N + idx];
         }
+    };
+    if (PRE) {
+#pragma unroll
+        for (int k = 0; k < 8; ++k) load_ops(k);
     }
     pdl_entry();
     stage_chunk<LOGL>(A, a.D + (size_t)row0 * W, R * W);
@@ -389,6 +411,7 @@ __global__ void __launch_bounds__(512) k_row_adj(AdjArgs a, int N, int R, const 
     __syncthreads();
 #pragma unroll
     for (int k = 0; k < 8; ++k) {
+        if (!PRE) load_ops(k);
         const int j = t + k * T;
         const size_t idx = rowbase + j;
         const float dv = O[q * L + j];
