@@ -70,7 +70,9 @@ typedef struct {
     int max_ls;          /* [20]  backtracking steps before REG_ERR_LINESEARCH */
     int nt_policy;       /* [REG_NT_FIXED] or REG_NT_CFL */
     double cfl_max;      /* [0.25] CFL number targeted by REG_NT_CFL */
-    int warm_start;      /* [0] 1: v_inout holds the initial guess; g_ref is g(0) */
+    int warm_start;      /* [0] 1: v_inout holds the initial guess; the stopping test
+                            stays relative to g_ref = g(0), the PCG forcing term is
+                            relative to the gradient at the initial guess */
 } reg_solve_opts;
 
 /* Statistics of one solve (the measures of the paper's Tab. 1 / Appendix F). */

@@ -18,7 +18,9 @@ Readings of passages the paper leaves open or garbles:
     sequence is stated to be relative to the gradient (Appendix E text,
     Dembo/Eisenstat), so the test is ||r_{l+1}|| < eta_k ||g_k||.  The loop
     bound "l < n" is capped at ``maxit_pcg`` (default 100).
-  * Forcing term eta_k = min(0.5, sqrt(||g_k|| / ||g_ref||)) (Algorithm 2).
+  * Forcing term eta_k = min(0.5, sqrt(||g_k|| / ||g_0||)) (Algorithm 2), with
+    g_0 the gradient at the initial iterate v_0 of Algorithm 1 (for a warm
+    start, the gradient at the warm start).
   * Armijo constants: alpha_0 = 1, rho = 1/2, c1 = 1e-4, at most 20
     backtracks.  Acceptance J(v + alpha v~) <= J(v) + c1 alpha <g, v~>.
   * Outer stop: ||g_k|| / ||g_ref|| <= tol (unsquared, quadrature-weighted L2);
@@ -187,6 +189,7 @@ class Registration:
         if v0 is None:
             gref = norm(g)
         gnorm = norm(g)
+        gstart = gnorm
         stats["J0"] = J
         k = 0
         while True:
@@ -195,7 +198,7 @@ class Registration:
             if k >= maxit_newton:
                 stats["status"] = STATUS_MAXIT
                 break
-            eta = min(0.5, math.sqrt(gnorm / gref))
+            eta = min(0.5, math.sqrt(gnorm / gstart))
             vt, it, relres, hit = self.pcg(g, eta, maxit_pcg)
             stats["n_mv"] += it
             stats["n_pcg_maxit"] += int(hit)

@@ -379,27 +379,30 @@ static float* mh(reg_ctx* c, int j) { return c->m_hist + (size_t)j * c->N; }
 static float* gmh(reg_ctx* c, int j) { return c->gm_hist + (size_t)j * 2 * c->N; }
 
 // State equation (Eq. (e:state-eq-elim)), Heun in time: fills m_hist[0..nt], gm_hist[0..nt].
+// The column pass transforms only d1 (OP_GRAD1); d2 is diagonal in the row
+// spectra and is formed by the row kernel from the stage's own spectrum S[0].
 static void state_solve(reg_ctx* c, const float* v, int nt) {
     const float h = 1.0f / (float)nt;
     cudaMemcpyAsync(mh(c, 0), c->mT, sizeof(float) * c->N, cudaMemcpyDeviceToDevice, c->stream);
     launch_r2c_scalar(c, mh(c, 0), c->S[0]);
     const float2* in[1] = {c->S[0]};
-    float2* G[2] = {c->S[1], c->S[2]};
+    float2* G[1] = {c->S[1]};
     const SpecParams P = spec_params(c, 0.f);
     for (int j = 0; j < nt; ++j) {
-        launch_col(c, OP_GRAD, in, G, P, nullptr);
+        launch_col(c, OP_GRAD1, in, G, P, nullptr);
         AdvArgs a = {};
-        a.G1 = c->S[1]; a.G2 = c->S[2];
+        a.G1 = c->S[1]; a.G2 = nullptr; a.Sd2 = c->S[0];
         a.uj = mh(c, j); a.us = nullptr; a.v = v;
         a.gm = nullptr; a.vt = nullptr;
         a.u_out = c->w0; a.grad_out = gmh(c, j); a.S_out = c->S[0];
         a.h = h; a.stage = 1;
         launch_row_adv(c, a);
-        launch_col(c, OP_GRAD, in, G, P, nullptr);
+        launch_col(c, OP_GRAD1, in, G, P, nullptr);
         a.us = c->w0; a.u_out = mh(c, j + 1); a.grad_out = nullptr; a.stage = 2;
         launch_row_adv(c, a);
     }
-    launch_col(c, OP_GRAD, in, G, P, nullptr);
+    float2* G2[2] = {c->S[1], c->S[2]};
+    launch_col(c, OP_GRAD, in, G2, P, nullptr);
     launch_c2r_vec(c, c->S[1], c->S[2], gmh(c, nt), gmh(c, nt) + c->N);
 }
 
@@ -416,12 +419,12 @@ static void adjoint_solve(reg_ctx* c, const float* v, int nt, const float* a, fl
     float2* D[1] = {c->S[0]};
     const SpecParams P = spec_params(c, 0.f);
     for (int j = nt; j >= 1; --j) {
-        launch_col(c, OP_DIV, Fin, D, P, nullptr);
+        launch_col(c, OP_DIV1, Fin, D, P, nullptr);
         AdjArgs s1 = {};
         s1.D = c->S[0]; s1.lj = lam; s1.ls = nullptr; s1.v = v; s1.l_out = lst;
         s1.b = nullptr; s1.gm = nullptr; s1.w = 0.f; s1.F1 = c->S[1]; s1.F2 = c->S[2]; s1.h = h; s1.stage = 1;
         launch_row_adj(c, s1);
-        launch_col(c, OP_DIV, Fin, D, P, nullptr);
+        launch_col(c, OP_DIV1, Fin, D, P, nullptr);
         AdjArgs s2 = s1;
         s2.ls = lst; s2.l_out = lam; s2.stage = 2;
         s2.b = bout; s2.gm = gmh(c, j - 1); s2.w = (j - 1 == 0) ? 0.5f * h : h;
@@ -437,19 +440,19 @@ static void inc_state_solve(reg_ctx* c, const float* v, const float* vt, int nt)
     float* mj = c->w3;
     float* ms = c->w0;
     const float2* in[1] = {c->S[0]};
-    float2* G[2] = {c->S[1], c->S[2]};
+    float2* G[1] = {c->S[1]};
     const SpecParams P = spec_params(c, 0.f);
     for (int j = 0; j < nt; ++j) {
         AdvArgs a = {};
         if (j > 0) {
-            launch_col(c, OP_GRAD, in, G, P, nullptr);
-            a.G1 = c->S[1]; a.G2 = c->S[2];
+            launch_col(c, OP_GRAD1, in, G, P, nullptr);
+            a.G1 = c->S[1]; a.Sd2 = c->S[0];
         }
         a.uj = (j > 0) ? mj : nullptr; a.us = nullptr; a.v = v; a.gm = gmh(c, j); a.vt = vt;
         a.u_out = ms; a.grad_out = nullptr; a.S_out = c->S[0]; a.h = h; a.stage = 1;
         launch_row_adv(c, a);
-        launch_col(c, OP_GRAD, in, G, P, nullptr);
-        a.G1 = c->S[1]; a.G2 = c->S[2];
+        launch_col(c, OP_GRAD1, in, G, P, nullptr);
+        a.G1 = c->S[1]; a.Sd2 = c->S[0];
         a.us = ms; a.gm = gmh(c, j + 1); a.u_out = mj; a.stage = 2;
         a.S_out = (j + 1 < nt) ? c->S[0] : nullptr;
         launch_row_adv(c, a);
@@ -738,6 +741,9 @@ extern "C" int reg_solve(reg_ctx* c, float* v, const reg_solve_opts* opts, reg_s
     double J = c->h_scal[SL_JDATA] + c->h_scal[SL_JREG];
     double gnorm = std::sqrt(c->h_scal[SL_GNORM2]);
     if (!o.warm_start) gref = gnorm;
+    // Algorithm 2's forcing term is relative to the gradient at the initial iterate
+    // (the warm start, if any); the stopping test stays relative to g_ref = g(0).
+    const double gstart = gnorm;
     st.J0 = J;
     int status = REG_OK;
     int k = 0;
@@ -745,7 +751,7 @@ extern "C" int reg_solve(reg_ctx* c, float* v, const reg_solve_opts* opts, reg_s
     while (status == REG_OK) {
         if (gref == 0.0 || gnorm / gref <= o.tol) break;
         if (k >= o.maxit_newton) { status = REG_ERR_MAXIT; break; }
-        const double eta = std::fmin(0.5, std::sqrt(gnorm / gref));
+        const double eta = std::fmin(0.5, std::sqrt(gnorm / gstart));
         int hit = 0, pst = REG_OK;
         const int it = pcg_dev(c, gnorm, eta, o.maxit_pcg, &hit, &pst);
         st.n_mv += it;

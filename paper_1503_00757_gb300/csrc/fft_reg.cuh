@@ -140,6 +140,21 @@ __device__ __forceinline__ float2 merged_entry(const float2* Sa, int ra, const f
     return (e < H) ? make_float2(A.x - B.y, A.y + B.x) : make_float2(A.x + B.y, -A.y + B.x);
 }
 
+// As merged_entry, with the imaginary-part row given implicitly as the x^2
+// derivative of another row: B[e] = i e c S[e] (c = 1/n2), which is zero at
+// e = 0 and at the Nyquist entry (odd symbol).
+template <int LOGL>
+__device__ __forceinline__ float2 merged_entry_d2(const float2* Sa, int ra, const float2* Sd, int rd, int e, float c) {
+    constexpr int L = 1 << LOGL, H = L >> 1;
+    if (e == 0) return make_float2(Sa[sp_idx(ra, 0, H)].x, 0.f);
+    if (e == H) return make_float2(Sa[sp_idx(ra, 0, H)].y, 0.f);
+    const int ee = (e < H) ? e : L - e;
+    const float2 A = Sa[sp_idx(ra, ee, H)], S = Sd[sp_idx(rd, ee, H)];
+    const float ce = c * (float)ee;
+    const float2 B = make_float2(-ce * S.y, ce * S.x);
+    return (e < H) ? make_float2(A.x - B.y, A.y + B.x) : make_float2(A.x + B.y, -A.y + B.x);
+}
+
 // Packed half-spectrum entry e of the real part (part 0) or imaginary part
 // (part 1) of z, given the full spectrum Z (natural order, L entries).
 template <int LOGL>

@@ -17,7 +17,9 @@ enum SpecOp {
     OP_PRECOND = 4,  // 2 in -> 2 out: x / (beta_v A'^(k)), A'(0) = 1
     OP_ASSEMBLE = 5, // 4 in -> 2 out: coefA A^(k) x01 + K^(k) x23
     OP_ENERGY = 6,   // 2 in -> 0 out: FP64 sum of the quadratic regularization energy
-    OP_DIVT_PROJ = 7 // 5 in -> 2 out: P_L(coefA * div(T) + b), T = (T11, T12, T22)
+    OP_DIVT_PROJ = 7, // 5 in -> 2 out: P_L(coefA * div(T) + b), T = (T11, T12, T22)
+    OP_GRAD1 = 8,     // 1 in -> 1 out: i k1~ x (d2 is diagonal in the row spectra; see AdvArgs::Sd2)
+    OP_DIV1 = 9       // in[0] transformed, in[1] raw -> 1 out: i k1~ x0 + (i k2~ / n2) x1 (x1 not transformed)
 };
 
 // Projection modes (Eq. (e:project-body-force)):
@@ -121,6 +123,7 @@ void launch_col(reg_ctx* ctx, int op, const float2* const* in, float2* const* ou
 
 struct AdvArgs {
     const float2 *G1, *G2;  // spectra of d1 u_s, d2 u_s; G1 == nullptr -> zero gradient
+    const float2* Sd2;      // G2 == nullptr: row spectrum of u_s, d2 u_s = (i k2~ / n2) Sd2
     const float *uj, *us;   // u_j (nullptr: u_j = 0) and the stage-2 input u* (stage 1: us unused)
     const float* v;         // velocity (2N)
     const float* gm;        // grad m at the source time (2N); nullptr -> no source

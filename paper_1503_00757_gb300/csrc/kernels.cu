@@ -284,10 +284,16 @@ __global__ void __launch_bounds__(512, RowBlocks<LOGL>::value) k_row_adv(AdvArgs
     float2 x[8];
     if (a.G1) {
         stage_chunk<LOGL>(A, a.G1 + base, R * W);
-        stage_chunk<LOGL>(A + R * W, a.G2 + base, R * W);
+        stage_chunk<LOGL>(A + R * W, (a.G2 ? a.G2 : a.Sd2) + base, R * W);
         __syncthreads();
+        if (a.G2) {
 #pragma unroll
-        for (int k = 0; k < 8; ++k) x[k] = merged_entry<LOGL>(A, q, A + R * W, q, t + k * T);
+            for (int k = 0; k < 8; ++k) x[k] = merged_entry<LOGL>(A, q, A + R * W, q, t + k * T);
+        } else {
+            const float c = 1.0f / (float)L;
+#pragma unroll
+            for (int k = 0; k < 8; ++k) x[k] = merged_entry_d2<LOGL>(A, q, A + R * W, q, t + k * T, c);
+        }
         reg_fft<LOGL, true>(x, t, true, X + 2 * q * L, X + 2 * q * L + L, tw);
     } else {
 #pragma unroll
@@ -535,6 +541,8 @@ __device__ __forceinline__ void spec_apply(const SpecParams& P, float k1o, float
             e += P.ebw * (1.0 + kk) * (dr * dr + di * di);
         }
         eacc += ew * e;
+    } else if (OP == OP_GRAD1 || OP == OP_DIV1) {
+        y[0] = cscale(cmuli(x[0]), k1o * s);
     } else if (OP == OP_DIVT_PROJ) {
         // d = div T:  d1 = i k1 T11 + i k2 T12 ; d2 = i k1 T12 + i k2 T22
         const float2 d1 = cmuli(cadd(cscale(x[0], k1o), cscale(x[1], k2o)));
@@ -631,11 +639,20 @@ __global__ void __launch_bounds__(256) k_col(ColArgs a, const float2* __restrict
         for (int k = 0; k < 8; ++k) A[c * L + t + k * T] = y[o][k];
         __syncthreads();
         float2* dst = a.out[o];
+        const float cd2 = 1.0f / (float)a.n2;
         for (int idx = threadIdx.x; idx < C * L; idx += blockDim.x) {
             const int g = idx / (4 * C);
             const int rem = idx - g * 4 * C;
             const int cc = rem >> 2, rr = rem & 3;
-            dst[((size_t)g * W + e0 + cc) * 4 + rr] = A[cc * L + 4 * g + rr];
+            const size_t gi = ((size_t)g * W + e0 + cc) * 4 + rr;
+            float2 val = A[cc * L + 4 * g + rr];
+            if (OP == OP_DIV1) {
+                // + (i k2~ / n2) F2, diagonal in the row spectra; k2~ = 0 in the packed column 0
+                const float2 f2 = a.in[1][gi];
+                const float ce = cd2 * (float)(e0 + cc);
+                val = make_float2(val.x - ce * f2.y, val.y + ce * f2.x);
+            }
+            dst[gi] = val;
         }
     }
 }
@@ -789,12 +806,13 @@ static void launch_col_t(reg_ctx* ctx, const float2* const* in, float2* const* o
     const size_t smem = 3 * (size_t)cpb * L * sizeof(float2);
     ColArgs a;
     for (int f = 0; f < 5; ++f) a.in[f] = (f < NIN) ? in[f] : nullptr;
+    if (OP == OP_DIV1) a.in[1] = in[1];  // read untransformed in the store phase
     for (int o = 0; o < 2; ++o) a.out[o] = (o < NOUT) ? out[o] : nullptr;
     a.P = P;
     a.part = part;
     a.cpb = cpb;
     a.n2 = ctx->n2;
-    ktimer_begin(ctx, KC_COL, 4.0 * (NIN + NOUT) * ctx->N);
+    ktimer_begin(ctx, KC_COL, 4.0 * (NIN + NOUT + (OP == OP_DIV1 ? 1 : 0)) * ctx->N);
     DISPATCH_LOG(ctx->log1, {
         auto kern = k_col<LG, NIN, NOUT, OP>;
         set_smem(kern, smem);
@@ -819,6 +837,8 @@ void launch_col(reg_ctx* ctx, int op, const float2* const* in, float2* const* ou
         case OP_ASSEMBLE: launch_col_t<4, 2, OP_ASSEMBLE>(ctx, in, out, P, part); break;
         case OP_ENERGY: launch_col_t<2, 0, OP_ENERGY>(ctx, in, out, P, part); break;
         case OP_DIVT_PROJ: launch_col_t<5, 2, OP_DIVT_PROJ>(ctx, in, out, P, part); break;
+        case OP_GRAD1: launch_col_t<1, 1, OP_GRAD1>(ctx, in, out, P, part); break;
+        case OP_DIV1: launch_col_t<1, 1, OP_DIV1>(ctx, in, out, P, part); break;
         default: break;
     }
 }

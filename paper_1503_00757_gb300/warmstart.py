@@ -109,9 +109,9 @@ def main():
 
     ap = argparse.ArgumentParser()
     ap.add_argument("--n", type=int, default=N_DEFAULT)
-    ap.add_argument("--train", type=int, default=1000)
+    ap.add_argument("--train", type=int, default=2000)
     ap.add_argument("--test", type=int, default=100)
-    ap.add_argument("--epochs", type=int, default=30)
+    ap.add_argument("--epochs", type=int, default=40)
     ap.add_argument("--batch", type=int, default=8)
     ap.add_argument("--lr", type=float, default=2e-3)
     ap.add_argument("--workers", type=int, default=8)

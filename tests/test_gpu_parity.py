@@ -280,3 +280,23 @@ def test_graph_path_matches_direct_launches():
     (J0, g0, H0, v0, m0), (J1, g1, H1, v1, m1) = outs
     assert J0 == J1 and m0 == m1
     assert np.array_equal(g0, g1) and np.array_equal(H0, H1) and np.array_equal(v0, v1)
+
+
+def test_warm_start_solve_matches_oracle():
+    """Warm start (opts.warm_start): stopping test relative to g(0), forcing term
+    relative to the gradient at the initial guess (Algorithm 2's g_0)."""
+    import torch
+    from paper_1503_00757_gb300.binding import default_opts
+    n, nt = 64, 4
+    mT, mR, vs = synth.blobs_pair(n, 1000)
+    P = Registration(mT, mR, nt, regnorm=1, beta_v=1e-2, beta_w=math.inf)
+    v0 = S.apply_K(0.3 * vs, 1, 1.0, math.inf)
+    v_ref, st_ref = P.solve(v0=v0, tol=1e-2)
+    ctx = make_ctx(n, n, nt, regnorm=1, beta=1e-2, gamma=math.inf)
+    ctx.set_images(to_gpu(mT), to_gpu(mR))
+    v = to_gpu(v0)
+    st = ctx.solve(v, default_opts(tol=1e-2, warm_start=1))
+    assert st["status"] == 0 and st["gnorm_rel"] <= 1e-2
+    assert st["n_newton"] == st_ref["n_newton"] and st["n_mv"] == st_ref["n_mv"]
+    assert rel_l2(to_np(v), v_ref) < 1e-3
+    ctx.close()
