@@ -41,6 +41,28 @@ WORKLOAD = ("C3 synthetic brain-like ellipses 512x512, nt=32, H1, beta_v=1e-3, i
 PDE_PER_REG = 93
 
 
+def rank_seeds(rank, pairs=None):
+    """Seeds of the pairs one rank registers per step (disjoint across ranks)."""
+    pairs = PAIRS if pairs is None else pairs
+    return [SEED + rank * pairs + i for i in range(pairs)]
+
+
+def aggregate_ms(ms_local, world, dist=None, device=None):
+    """Max over ranks of a per-rank step time (replicas only; no data-path collective)."""
+    if world == 1 or dist is None:
+        return float(ms_local)
+    import torch
+    t = torch.tensor([ms_local], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def throughput(ms_step, world, pairs=None):
+    """Registrations per second of the whole job: all ranks' pairs / max step time."""
+    pairs = PAIRS if pairs is None else pairs
+    return world * pairs * 1e3 / ms_step
+
+
 def peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -180,7 +202,7 @@ def main():
     from paper_1503_00757_gb300.binding import Executor
 
     # the step's batch: PAIRS independent registrations of this rank (seeds differ per rank)
-    pairs_np = [images(SEED + rank * PAIRS + i) for i in range(PAIRS)]
+    pairs_np = [images(s) for s in rank_seeds(rank)]
     mT_np, mR_np = pairs_np[0]
     pairs = [dict(mT=torch.from_numpy(a).to(dev), mR=torch.from_numpy(b).to(dev),
                   v=torch.zeros(2, N_GRID, N_GRID, device=dev), nt=NT, regnorm=1, beta=BETA,
@@ -266,12 +288,8 @@ def main():
         barrier()
         torch.cuda.synchronize()
         clk = clocks.stop()
-        ms_step = total_ms / args.steps
-        t = torch.tensor([ms_step], device=dev, dtype=torch.float64)
-        if world > 1:
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_step = float(t.item())
-        value = world * PAIRS * 1e3 / ms_step
+        ms_step = aggregate_ms(total_ms / args.steps, world, dist if world > 1 else None, dev)
+        value = throughput(ms_step, world)
 
         # single-registration latency (one pair alone on one stream)
         for _ in range(2):
@@ -314,11 +332,7 @@ def main():
             e1.record(stream)
             e1.synchronize()
             e2e_ms += e0.elapsed_time(e1)
-        e2e_ms /= args.steps
-        et = torch.tensor([e2e_ms], device=dev, dtype=torch.float64)
-        if world > 1:
-            dist.all_reduce(et, op=dist.ReduceOp.MAX)
-        e2e_value = world * PAIRS * 1e3 / float(et.item())
+        e2e_value = throughput(aggregate_ms(e2e_ms / args.steps, world, dist if world > 1 else None, dev), world)
 
         # Hessian matvec throughput at a fixed linearization point (the converged v)
         g = torch.empty_like(v)
