@@ -4,23 +4,32 @@ infrastructure only).
 The paper has no learned component; this network is the warm-start predictor
 the registration path is extended with: 8 convolution layers with 3x3
 kernels and circular (periodic) padding, channel widths 2 -> 32 -> ... -> 32
--> 2, ReLU after every layer but the last, and the predicted velocity
-projected onto divergence-free fields with the Leray projection of the
-incompressible model (Eq. (e:project-body-force) with w = 0), so that a warm
-start satisfies the constraint div v = 0 exactly.
+-> 2, ReLU after every layer but the last.  The middle layers are dilated
+(taps d apart) so that the receptive field covers the large-scale motion:
+layer l uses dilation min(DILATION[l], H // 8, W // 32) (the cap keeps every
+dilated sub-grid at least 8 x 32 points).  The raw output is smoothed by a
+Gaussian low-pass G (symbol exp(-sigma^2 |k|^2 / 2), sigma = 2 h with
+h = 2 pi / max(H, W), so the warm start carries no grid-scale noise, which the
+Gauss-Newton-Krylov solve is expensive on) and projected onto divergence-free
+fields with the Leray projection of the incompressible model
+(Eq. (e:project-body-force) with w = 0), so that a warm start satisfies the
+constraint div v = 0 exactly.
 
-Convolution (cross-correlation) with periodic wrap:
-    z[b, o, y, x] = bias[o] + sum_{c, dy, dx in {-1,0,1}} W[o, c, dy+1, dx+1] a[b, c, (y+dy) mod H, (x+dx) mod W]
-Loss: mean squared error between the projected prediction and the target
-velocity, L = sum((P out - t)^2) / (2 M), M = number of target entries.
-Backward passes are the adjoints of these maps written out (np.roll is the
-periodic shift; the Leray projection is symmetric and idempotent).
+Convolution (cross-correlation) with periodic wrap and dilation d:
+    z[b, o, y, x] = bias[o] + sum_{c, dy, dx in {-1,0,1}} W[o, c, dy+1, dx+1] a[b, c, (y+d dy) mod H, (x+d dx) mod W]
+Loss: mean squared error between the filtered, projected prediction and the
+target velocity, L = sum((P G out - t)^2) / (2 M), M = number of target
+entries.  Backward passes are the adjoints of these maps written out (np.roll
+is the periodic shift; P and G are symmetric Fourier multipliers that commute,
+so (P G)^T = G P).
 """
 import numpy as np
 
-from .spectral import H1, apply_K
+from .fft import fft2, ifft2
+from .spectral import H1, apply_K, symbols
 
 CHANNELS = (2, 32, 32, 32, 32, 32, 32, 32, 2)
+DILATION = (1, 2, 4, 8, 8, 4, 2, 1)
 
 
 def init_params(seed, channels=CHANNELS, scale=1.0):
@@ -33,27 +42,33 @@ def init_params(seed, channels=CHANNELS, scale=1.0):
     return params
 
 
+def dilations(H, W, nlayers=len(DILATION)):
+    """Per-layer dilation on an H x W grid (the schedule capped by H // 8 and W // 32)."""
+    return [max(1, min(DILATION[l % len(DILATION)], H // 8, W // 32)) for l in range(nlayers)]
+
+
 def _shift(a, dy, dx):
     """s[..., y, x] = a[..., (y + dy) mod H, (x + dx) mod W]."""
     return np.roll(a, shift=(-dy, -dx), axis=(-2, -1))
 
 
-def conv3x3(a, W, b):
+def conv3x3(a, W, b, d=1):
     out = np.zeros((a.shape[0], W.shape[0]) + a.shape[2:])
     for dy in (-1, 0, 1):
         for dx in (-1, 0, 1):
-            out += np.einsum("oc,bchw->bohw", W[:, :, dy + 1, dx + 1], _shift(a, dy, dx))
+            out += np.einsum("oc,bchw->bohw", W[:, :, dy + 1, dx + 1], _shift(a, d * dy, d * dx))
     return out + b[None, :, None, None]
 
 
-def conv3x3_backward(a, W, dz):
-    """Gradients of conv3x3 w.r.t. its input a, weights W and bias."""
+def conv3x3_backward(a, W, dz, d=1):
+    """Gradients of conv3x3 (dilation d) w.r.t. its input a, weights W and bias."""
     da = np.zeros_like(a)
     dW = np.zeros_like(W)
     for dy in (-1, 0, 1):
         for dx in (-1, 0, 1):
-            da += np.roll(np.einsum("oc,bohw->bchw", W[:, :, dy + 1, dx + 1], dz), shift=(dy, dx), axis=(-2, -1))
-            dW[:, :, dy + 1, dx + 1] = np.einsum("bohw,bchw->oc", dz, _shift(a, dy, dx))
+            da += np.roll(np.einsum("oc,bohw->bchw", W[:, :, dy + 1, dx + 1], dz), shift=(d * dy, d * dx),
+                          axis=(-2, -1))
+            dW[:, :, dy + 1, dx + 1] = np.einsum("bohw,bchw->oc", dz, _shift(a, d * dy, d * dx))
     return da, dW, dz.sum(axis=(0, 2, 3))
 
 
@@ -62,34 +77,58 @@ def leray(u):
     return np.stack([apply_K(u[i], H1, 1.0, np.inf) for i in range(u.shape[0])])
 
 
+def gauss_sigma(H, W):
+    """Width of the output low-pass: two grid spacings of the finer axis."""
+    return 2.0 * (2.0 * np.pi / max(H, W))
+
+
+def gauss(u):
+    """Gaussian low-pass exp(-sigma^2 |k|^2 / 2) of each field u[b, c] (full |k|^2, Nyquist kept)."""
+    H, W = u.shape[-2:]
+    _, _, KK = symbols(H, W)
+    s = gauss_sigma(H, W)
+    mult = np.exp(-0.5 * s * s * KK)
+    out = np.empty_like(u, dtype=np.float64)
+    for i in np.ndindex(*u.shape[:-2]):
+        out[i] = np.real(ifft2(mult * fft2(u[i])))
+    return out
+
+
+def output_map(u):
+    """Divergence-free warm start from the raw network output: P G u."""
+    return leray(gauss(u))
+
+
 def forward(params, x, cache=False):
     """x: (B, 2, H, W) -> raw output (B, 2, H, W) and, if cache, the layer inputs."""
     acts = [x]
     a = x
+    dil = dilations(x.shape[-2], x.shape[-1], len(params))
     for l, (W, b) in enumerate(params):
-        z = conv3x3(a, W, b)
+        z = conv3x3(a, W, b, dil[l])
         a = np.maximum(z, 0.0) if l < len(params) - 1 else z
         acts.append(a)
     return (a, acts) if cache else a
 
 
 def predict(params, x):
-    """Divergence-free warm-start velocity P(net(x))."""
-    return leray(forward(params, x))
+    """Divergence-free warm-start velocity P G net(x)."""
+    return output_map(forward(params, x))
 
 
 def loss_and_grads(params, x, t):
-    """MSE loss of the projected prediction against t and its parameter gradients."""
+    """MSE loss of the filtered, projected prediction against t and its parameter gradients."""
     out, acts = forward(params, x, cache=True)
-    r = leray(out) - t
+    dil = dilations(x.shape[-2], x.shape[-1], len(params))
+    r = output_map(out) - t
     M = t.size
     loss = 0.5 * float(np.sum(r * r)) / M
-    d = leray(r) / M  # dL/d out (P symmetric and idempotent)
+    d = gauss(leray(r)) / M  # dL/d out = (P G)^T r / M = G P r / M
     grads = [None] * len(params)
     for l in range(len(params) - 1, -1, -1):
         W, b = params[l]
         a_in = acts[l]
-        da, dW, db = conv3x3_backward(a_in, W, d)
+        da, dW, db = conv3x3_backward(a_in, W, d, dil[l])
         grads[l] = (dW, db)
         if l > 0:
             d = da * (acts[l] > 0.0)  # ReLU of layer l-1 (acts[l] is its output)
