@@ -78,6 +78,88 @@ def images(seed=SEED):
     return mT.astype(np.float32), mR.astype(np.float32)
 
 
+C4_SIZES = (128, 256, 512)
+C4_COUNTS = (147, 73, 36)  # 4 : 2 : 1 over 256 pairs
+C4_VMAX = {128: 0.196, 256: 0.098, 512: 0.049}  # CFL 0.25 at nt = 16
+C4_NT = 16
+
+
+def c4_specs():
+    """The mixed batch: 256 pairs (seeds 4000-4255), grid sizes 128^2 : 256^2 : 512^2 = 4 : 2 : 1,
+    per pair a seeded random seminorm (H1 / H2), beta_v in {1e-2, 1e-3} and beta_w in {0, 1e-3, inf}."""
+    rng = np.random.default_rng(4000)
+    sizes = [n for n, c in zip(C4_SIZES, C4_COUNTS) for _ in range(c)]
+    specs = []
+    for i, n in enumerate(sizes):
+        specs.append(dict(n=n, seed=4000 + i, regnorm=int(rng.choice([1, 2])), beta=[1e-2, 1e-3][int(rng.integers(2))],
+                          gamma=[0.0, 1e-3, math.inf][int(rng.integers(3))]))
+    return specs
+
+
+def run_batched_mixed(dev, stream, opts, nworkers=16):
+    """C4: the mixed batch through the executor (autotuned tiles, concurrent streams) against a
+    sequential per-pair loop of the same library (one context per grid size, one pair at a time)."""
+    import torch
+    from paper_1503_00757_gb300 import synth
+    from paper_1503_00757_gb300.binding import Context, Executor, autotune
+    specs = c4_specs()
+    t0 = time.perf_counter()
+    imgs = synth.ellipses_images([(s["n"], s["seed"], C4_VMAX[s["n"]]) for s in specs],
+                                 workers=max(1, min(16, os.cpu_count() or 1)))
+    gen_s = time.perf_counter() - t0
+    tiles = {}
+    for n in C4_SIZES:
+        R, C, ms = autotune(n, n, nt=4)
+        tiles[str(n)] = {"rows_per_cta": R, "cols_per_cta": C}
+    pairs = []
+    for s, (a, b) in zip(specs, imgs):
+        n = s["n"]
+        pairs.append(dict(mT=torch.from_numpy(a).to(dev), mR=torch.from_numpy(b).to(dev),
+                          v=torch.zeros(2, n, n, device=dev), nt=C4_NT, regnorm=s["regnorm"], beta=s["beta"],
+                          gamma=s["gamma"], shear=0.0))
+    ex = Executor(nworkers)
+
+    def batched():
+        for p in pairs:
+            p["v"].zero_()
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        _, st = ex.solve(pairs, opts, check=False)
+        return st, time.perf_counter() - t
+
+    batched()  # warm-up: contexts, captured graphs
+    st_b, sec_b = batched()
+    ctxs = {n: Context(n, n, C4_NT, stream=stream) for n in C4_SIZES}
+
+    def sequential(subset):
+        for p in subset:
+            p["v"].zero_()
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        out = []
+        for p in subset:
+            c = ctxs[p["mT"].shape[0]]
+            c.set_params(C4_NT, regnorm=p["regnorm"], beta=p["beta"], gamma=p["gamma"])
+            c.set_images(p["mT"], p["mR"])
+            out.append(c.solve(p["v"], opts, check=False))
+        stream.synchronize()
+        return out, time.perf_counter() - t
+
+    sequential([p for p in pairs if p["beta"] == 1e-2][:12])  # warm-up
+    st_s, sec_s = sequential(pairs)
+    for c in ctxs.values():
+        c.close()
+    ex.close()
+    ok_b = sum(1 for s in st_b if s["rc"] == 0)
+    ok_s = sum(1 for s in st_s if s["rc"] == 0)
+    return {"workload": "C4 mixed batch: 256 pairs, 128^2:256^2:512^2 = 147:73:36, nt=16, seeded random "
+                        "H1/H2, beta_v in {1e-2,1e-3}, beta_w in {0,1e-3,inf}, zero start, tol 1e-2",
+            "batched": {"pairs_per_s": len(pairs) / sec_b, "seconds": sec_b, "converged": ok_b, "workers": nworkers},
+            "sequential": {"pairs_per_s": len(pairs) / sec_s, "seconds": sec_s, "converged": ok_s},
+            "speedup": sec_s / sec_b, "tiles": tiles, "image_generation_s": gen_s,
+            "matvecs_total": int(sum(s["n_mv"] for s in st_b))}
+
+
 class Clocks:
     """Samples nvidia-smi clocks and throttle reasons during the timed region."""
 
@@ -174,6 +256,8 @@ def main():
                     help="skip the warm-start comparison")
     ap.add_argument("--no-big", dest="big", action="store_false",
                     help="skip the 1024^2 matvec measurement")
+    ap.add_argument("--no-batched", dest="batched", action="store_false",
+                    help="skip the mixed-size batch (256 pairs) against the sequential loop")
     ap.add_argument("--profile", action="store_true",
                     help="run --warmup registrations then one registration and exit (for ncu launch lists)")
     ap.add_argument("--profile-grid", type=int, default=0,
@@ -199,7 +283,11 @@ def main():
         libbuild.build()
     from paper_1503_00757_gb300.binding import Context, default_opts
 
-    from paper_1503_00757_gb300.binding import Executor
+    from paper_1503_00757_gb300.binding import Executor, autotune
+
+    # FFT tiles of the workload's grid, picked once by the autotuner before any context exists
+    # (with --profile-grid: the tiles of that grid instead)
+    tR, tC, _ = autotune(args.profile_grid or N_GRID, args.profile_grid or N_GRID, nt=4)
 
     # the step's batch: PAIRS independent registrations of this rank (seeds differ per rank)
     pairs_np = [images(s) for s in rank_seeds(rank)]
@@ -423,6 +511,7 @@ def main():
                     "speedup": w_["registrations_per_s"] / z["registrations_per_s"]}
             netw.close()
             exw.close()
+        batched_mixed = run_batched_mixed(dev, stream, opts) if (args.batched and rank == 0) else None
     dom = max(classes, key=lambda k: classes[k][1])
     n_dom, ms_dom, bytes_dom = classes[dom]
     peak, peak_kind = peaks()
@@ -442,10 +531,12 @@ def main():
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": WORKLOAD, "grid": [N_GRID, N_GRID], "nt": NT, "pairs_per_step": PAIRS,
+                       "tiles": {"rows_per_cta": tR, "cols_per_cta": tC},
                        "l2": "flushed between steps", "parallelism": f"replicas x{world}, {PAIRS} concurrent streams",
                        "start": "zero (plain); warm start reported in warm_start_vs_plain"},
             "latency_ms_single_registration": lat,
             "warm_start_vs_plain": warm,
+            "batched_mixed_vs_sequential": batched_mixed,
             "matvec_per_s": 1e3 / mv_ms, "ms_per_matvec": mv_ms,
             "solve": {k: stats[k] for k in ("n_newton", "n_mv", "n_pde", "n_ls", "gnorm_rel", "rnorm_rel_sq", "status")},
             "solve_batch": [{k: b[k] for k in ("n_newton", "n_mv", "gnorm_rel", "rc")} for b in bstats],

@@ -7,7 +7,7 @@
  * Conventions shared by every entry point
  * ---------------------------------------
  * Grid.  n1 x n2 nodes on the periodic domain [0, 2 pi)^2 (the paper's
- *   (-pi, pi)^2 shifted by a period, Sec. 2); node (i, j) is at
+ *   (-pi, pi)^2 shifted by a period, Sec. 1.5); node (i, j) is at
  *   x = (2 pi i / n1, 2 pi j / n2).  n1 and n2 are powers of two in [16, 1024].
  * Layout.  A scalar field is n1*n2 floats, row-major, index i*n2 + j (x^2
  *   fastest).  A vector field is two scalar planes back to back (component 1
@@ -59,7 +59,7 @@ enum reg_status {
 
 enum reg_nt_policy { REG_NT_FIXED = 0, REG_NT_CFL = 1 };
 
-/* Options of the Newton-Krylov solve (Algorithm 1, Algorithm 2, Sec. 5).
+/* Options of the Newton-Krylov solve (Algorithm 1, Algorithm 2, Sec. 4).
  * reg_default_opts fills the defaults given in brackets. */
 typedef struct {
     double tol;          /* [1e-2] stop when ||g_k|| / ||g_ref|| <= tol */
@@ -97,7 +97,7 @@ const char* reg_last_error(void);
 void reg_default_opts(reg_solve_opts* opts);
 
 /* Create a context.  Problem (Eq. (e:objective)-(e:constraint-divv)):
- *   nt       time steps of the RK2 transport solves (Sec. 5), >= 1;
+ *   nt       time steps of the RK2 transport solves (Sec. 4), >= 1;
  *   regnorm  REG_H1 or REG_H2 seminorm on v (Eq. (e:reg-v));
  *   beta     beta_v > 0;
  *   gamma    beta_w of the mass-source H1 norm (Eq. (e:reg-w)); 0 disables the
@@ -123,7 +123,7 @@ int reg_set_stream(reg_ctx* ctx, void* stream);
  * context (Eq. (e:objective), (e:init-transport-eq)). */
 int reg_set_images(reg_ctx* ctx, const float* mT, const float* mR);
 
-/* ---- rows a1-a4: spectral operators (Sec. 5, pseudospectral discretization) ---- */
+/* ---- rows a1-a4: spectral operators (Sec. 4, pseudospectral discretization) ---- */
 
 /* grad f (2*n1*n2 out) of a scalar field f; odd symbol i k with the Nyquist
  * wavenumber set to 0. */
@@ -153,13 +153,13 @@ int reg_gradient(reg_ctx* ctx, const float* v, float* g, double* J);
 /* ---- rows a8-a10: Gauss-Newton Hessian matvec ---- */
 
 /* H v~ = beta_v B[v~] + L[b~] (Eq. (e:inc-control-eq-elim)) with the
- * Gauss-Newton approximation (lambda terms dropped, Sec. 5), at the v of the
+ * Gauss-Newton approximation (lambda terms dropped, Sec. 4), at the v of the
  * last reg_gradient call (REG_ERR_STATE otherwise). */
 int reg_hessian_matvec(reg_ctx* ctx, const float* vt, float* Hvt);
 
-/* Body force of the last reg_gradient (b = int lam grad m dt, Sec. 4.1) or
+/* Body force of the last reg_gradient (b = int lam grad m dt, Sec. 3.1) or
  * incremental body force of the last reg_hessian_matvec (b~ with the
- * Gauss-Newton approximation, Sec. 4.2 / Sec. 5), before the projection K:
+ * Gauss-Newton approximation, Sec. 3.2 / Sec. 4), before the projection K:
  * b_out (device, 2*n1*n2).  REG_ERR_STATE if neither has run. */
 int reg_body_force(reg_ctx* ctx, float* b_out);
 
@@ -203,8 +203,10 @@ typedef struct {
  * current device with `nworkers` host workers (<= 0: 8), each issuing its
  * pairs on its own CUDA stream with per-grid-size contexts it creates once
  * and re-parameterizes per pair (reg_set_params), so the pairs' kernels run
- * concurrently.  Pairs are taken largest grid first.  Every pair's result is
- * identical to reg_solve on that pair alone.  Synchronous.  Returns REG_OK if
+ * concurrently.  Pairs are taken largest grid first.  Before the first pair
+ * of a grid size is solved, reg_autotune picks that size's FFT tiles (once
+ * per process and device).  Every pair's result is identical to reg_solve on
+ * that pair alone with a context created after that tuning.  Synchronous.  Returns REG_OK if
  * every pair returned REG_OK, else the first failing pair's status (each
  * item's own status is in item.status); REG_ERR_ARG for invalid arguments. */
 int reg_solve_batch(reg_batch_item* items, int count, const reg_solve_opts* opts, int nworkers);
@@ -217,6 +219,31 @@ typedef struct reg_executor reg_executor;
 int reg_executor_create(int nworkers, reg_executor** out);
 int reg_executor_solve(reg_executor* ex, reg_batch_item* items, int count, const reg_solve_opts* opts);
 void reg_executor_destroy(reg_executor* ex);
+
+/* ---- row a15: autotuner of the FFT tiles ---- */
+
+/* Times one Gauss-Newton Hessian matvec (Algorithm 2's inner product with H,
+ * two transport solves of nt steps) on an n1 x n2 grid for every valid pair
+ * (rows per row-kernel CTA R, spectrum columns per column-kernel CTA C) on the
+ * current device (zero images and velocity, a private stream) and records
+ * the fastest pair in a process-wide table; contexts created afterwards on
+ * this device and grid use it (existing contexts keep their tiles).  Valid:
+ * R a multiple of 4 dividing n1, 32 <= R n2 / 8 <= 512 threads; C a power of
+ * two >= 2 dividing n2 / 2, 32 <= C n1 / 8 <= 256 threads; at most 227 KB of
+ * shared memory.  A grid already in the table is not re-measured unless
+ * force != 0 (then *ms_per_matvec < 0).  Outputs are host pointers, each
+ * nullable.  Synchronous.  REG_ERR_ARG for a grid outside powers of two in
+ * [16, 1024] or nt outside [1, 4096]. */
+int reg_autotune(reg_grid grid, int nt, int force, int* rows_per_cta, int* cols_per_cta, double* ms_per_matvec);
+
+/* The tiles a context launches with (tuned, else the default rule:
+ * the smallest R, C with at least 64 threads). */
+int reg_tile_config(reg_ctx* ctx, int* rows_per_cta, int* cols_per_cta);
+
+/* Sets a context's tiles (validity as for reg_autotune; 0, 0 restores the
+ * default rule).  Results do not depend on the tiles except for the summation
+ * order of FP64 reductions (objective, norms).  REG_ERR_ARG for invalid tiles. */
+int reg_set_tiles(reg_ctx* ctx, int rows_per_cta, int cols_per_cta);
 
 /* ---- row a14: deformation gradient (Eq. (e:def-grad)) ---- */
 

@@ -78,6 +78,9 @@ _SIGS = {
     "reg_executor_create": ([_I, ctypes.POINTER(_P)], _I),
     "reg_executor_solve": ([_P, ctypes.POINTER(reg_batch_item), _I, ctypes.POINTER(reg_solve_opts)], _I),
     "reg_executor_destroy": ([_P], None),
+    "reg_autotune": ([reg_grid, _I, _I, ctypes.POINTER(_I), ctypes.POINTER(_I), ctypes.POINTER(_D)], _I),
+    "reg_tile_config": ([_P, ctypes.POINTER(_I), ctypes.POINTER(_I)], _I),
+    "reg_set_tiles": ([_P, _I, _I], _I),
     "reg_net_create": ([_I, _I, _I, ctypes.POINTER(_P)], _I),
     "reg_net_destroy": ([_P], None),
     "reg_net_num_params": ([_P], ctypes.c_longlong),
@@ -147,6 +150,15 @@ def spectral_grad_static(f, grad_f, stream=None):
     handle = None if stream is None else ctypes.c_void_p(stream.cuda_stream)
     _check(lib().reg_spectral_grad_static(reg_grid(n1, n2), _ptr(f, n1 * n2, "f"), _ptr(grad_f, 2 * n1 * n2, "grad_f"),
                                           handle))
+
+
+def autotune(n1, n2, nt=4, force=False):
+    """FFT tiles for an n1 x n2 grid (reg_autotune): (rows per row CTA, columns per
+    column CTA, ms per matvec of the winner, or -1 if the grid was already tuned)."""
+    R, C, ms = ctypes.c_int(), ctypes.c_int(), ctypes.c_double()
+    _check(lib().reg_autotune(reg_grid(n1, n2), nt, 1 if force else 0, ctypes.byref(R), ctypes.byref(C),
+                              ctypes.byref(ms)))
+    return R.value, C.value, ms.value
 
 
 def _batch_items(pairs):
@@ -410,3 +422,13 @@ class Context:
 
     def launch_count(self):
         return lib().reg_launch_count(self.h)
+
+    def tile_config(self):
+        """(rows per row-kernel CTA, spectrum columns per column-kernel CTA) of this context."""
+        R, C = ctypes.c_int(), ctypes.c_int()
+        _check(lib().reg_tile_config(self.h, ctypes.byref(R), ctypes.byref(C)))
+        return R.value, C.value
+
+    def set_tiles(self, R, C):
+        """Launch this context's row / column kernels with R rows and C spectrum columns per CTA (0, 0: default)."""
+        _check(lib().reg_set_tiles(self.h, R, C))

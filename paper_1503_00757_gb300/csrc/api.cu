@@ -148,6 +148,14 @@ extern "C" int reg_create(reg_grid grid, int nt, int regnorm, double beta, doubl
     set_params(c, nt, regnorm, beta, gamma, shear);
     c->stream = 0;
     c->launches = 0;
+    c->tileR = c->tileC = 0;
+    {
+        int dev = 0, R, C;
+        if (cudaGetDevice(&dev) == cudaSuccess && tuned_tiles(dev, c->n1, c->n2, &R, &C)) {
+            c->tileR = R;
+            c->tileC = C;
+        }
+    }
     c->pdl = true;
     c->use_graphs = true;
     c->timing = false;
@@ -197,6 +205,21 @@ extern "C" int reg_set_params(reg_ctx* c, int nt, int regnorm, double beta, doub
     if (!same) clear_graphs(c);  // captured sequences bake in nt and the Fourier-multiplier parameters
     set_params(c, nt, regnorm, beta, gamma, shear);
     return alloc_hist(c, nt);
+}
+
+extern "C" int reg_set_tiles(reg_ctx* c, int rows_per_cta, int cols_per_cta) {
+    if (!c) return reg_fail(REG_ERR_ARG, "ctx is NULL");
+    if (rows_per_cta == 0 && cols_per_cta == 0) {
+        if (c->tileR != 0 || c->tileC != 0) clear_graphs(c);
+        c->tileR = c->tileC = 0;
+        return REG_OK;
+    }
+    if (!tiles_valid(c->n1, c->n2, rows_per_cta, cols_per_cta))
+        return reg_fail(REG_ERR_ARG, "tiles outside the launch limits of this grid");
+    if (rows_per_cta != c->tileR || cols_per_cta != c->tileC) clear_graphs(c);  // captures bake in launch shapes
+    c->tileR = rows_per_cta;
+    c->tileC = cols_per_cta;
+    return REG_OK;
 }
 
 extern "C" int reg_set_stream(reg_ctx* c, void* stream) {
@@ -577,6 +600,14 @@ extern "C" int reg_apply_proj(reg_ctx* c, const float* b, float* out) {
     CTX_CHECK(c);
     RET(check_ptr(b, "b")); RET(check_ptr(out, "out"));
     sp_vec(c, OP_PROJ, 0.f, b, out);
+    CKL();
+    return REG_OK;
+}
+
+int apply_smooth_proj(reg_ctx* c, float a, const float* b, float* out) {
+    CTX_CHECK(c);
+    RET(check_ptr(b, "b")); RET(check_ptr(out, "out"));
+    sp_vec(c, OP_SMOOTH_PROJ, a, b, out);
     CKL();
     return REG_OK;
 }

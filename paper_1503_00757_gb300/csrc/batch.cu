@@ -62,6 +62,16 @@ extern "C" int reg_executor_solve(reg_executor* ex, reg_batch_item* items, int c
         items[i].status = -1;
     }
     const int nworkers = std::min<int>((int)ex->workers.size(), count);
+    // FFT tiles of every grid size in the batch (measured once per process and device)
+    {
+        cudaSetDevice(ex->dev);
+        std::map<std::pair<int, int>, int> sizes;
+        for (int i = 0; i < count; ++i) sizes[std::make_pair(items[i].grid.n1, items[i].grid.n2)] = 1;
+        for (const auto& kv : sizes) {
+            const int st = reg_autotune(reg_grid{kv.first.first, kv.first.second}, 4, 0, nullptr, nullptr, nullptr);
+            if (st != REG_OK) return st;
+        }
+    }
     // largest grids first (longest-processing-time-first scheduling)
     std::vector<int> order(count);
     for (int i = 0; i < count; ++i) order[i] = i;

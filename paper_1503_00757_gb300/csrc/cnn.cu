@@ -1,10 +1,19 @@
 // Learned warm start (row a16): an 8-layer 3x3 convolutional network with
 // circular padding (channel widths 2 -> 32 x 7 -> 2, ReLU between layers)
 // that predicts the velocity of a registration from the image pair
-// (m_T, m_R); the prediction is Leray-projected (Eq. (e:project-body-force)
-// with w = 0) so that a warm start satisfies div v = 0.  The paper has no
+// (m_T, m_R).  The middle layers are dilated (layer l samples its taps
+// d_l = min(DIL[l], H / TH, W / TW) pixels apart), so the receptive field
+// covers the large-scale motion.  The raw output is low-pass filtered by a
+// Gaussian (symbol exp(-sigma^2 |k|^2 / 2), sigma = 2 h, h = 2 pi / max(H, W))
+// and Leray-projected (Eq. (e:project-body-force) with w = 0), so that a warm
+// start carries no grid-scale noise and satisfies div v = 0.  The paper has no
 // learned component; the network only seeds reg_solve, whose tolerance test
 // is unchanged.
+//
+// A convolution of dilation d on an H x W periodic grid is an ordinary 3x3
+// circular convolution on each of the d^2 interleaved sub-grids
+// {(Y d + ry, X d + rx)} of size (H/d) x (W/d); each CTA tile lives in one
+// sub-grid, so the halo staging and the tensor-core loop are those of d = 1.
 //
 // Arithmetic: BF16 activations and weights, FP32 accumulation on the tensor
 // cores (mma.sync m16n8k16), FP32 master weights, Adam.  Layouts:
@@ -29,6 +38,35 @@ constexpr int TH = 8;    // output rows per CTA tile
 constexpr int TW = 32;   // output columns per CTA tile
 constexpr int NLAYER = 8;
 constexpr int CH[NLAYER + 1] = {2, 32, 32, 32, 32, 32, 32, 32, 2};
+constexpr int DIL[NLAYER] = {1, 2, 4, 8, 8, 4, 2, 1};
+
+// dilation of layer l on an H x W grid (every sub-grid at least TH x TW)
+int layer_dil(int l, int H, int W) {
+    int d = DIL[l];
+    while (d > 1 && (H / d < TH || W / d < TW)) d >>= 1;
+    return d;
+}
+
+// CTA tile -> sub-grid (ry, rx) of dilation d and tile origin (Y0, X0) in
+// sub-grid coordinates; grid point of sub-grid point (Y, X): (Y d + ry, X d + rx).
+struct TileMap {
+    int d, Hs, Ws, ry, rx, Y0, X0;
+    __device__ __forceinline__ int gy(int Y) const { return (Y & (Hs - 1)) * d + ry; }
+    __device__ __forceinline__ int gx(int X) const { return (X & (Ws - 1)) * d + rx; }
+};
+__device__ __forceinline__ TileMap tile_map(int tile, int H, int W, int d) {
+    TileMap m;
+    m.d = d;
+    m.Hs = H / d;
+    m.Ws = W / d;
+    const int tx = m.Ws / TW, per = (m.Hs / TH) * tx;
+    const int r = tile / per, tt = tile - r * per;
+    m.ry = r / d;
+    m.rx = r - m.ry * d;
+    m.Y0 = (tt / tx) * TH;
+    m.X0 = (tt - (tt / tx) * tx) * TW;
+    return m;
+}
 
 __host__ __device__ constexpr int padc(int c) { return c <= 16 ? 16 : 32; }
 
@@ -60,23 +98,21 @@ __device__ __forceinline__ uint32_t pack_h(bf16 lo, bf16 hi) {
 template <int CIN, int COUT, int MODE>
 __global__ void __launch_bounds__(256) k_conv3x3(const bf16* __restrict__ in, const bf16* __restrict__ w,
                                                  const float* __restrict__ bias, void* out,
-                                                 const bf16* __restrict__ mask, int H, int W) {
+                                                 const bf16* __restrict__ mask, int H, int W, int dil) {
     constexpr int SP = CIN + 8;            // smem pixel stride (halves), conflict-free fragment loads
     constexpr int KW = 9 * CIN + 8;        // smem weight row stride (halves)
     constexpr int HP = (TH + 2) * (TW + 2);
     extern __shared__ __align__(16) unsigned char smraw[];
     bf16* s_in = reinterpret_cast<bf16*>(smraw);
     bf16* s_w = s_in + HP * SP;
-    const int tiles_x = W / TW;
-    const int tile = blockIdx.x;
+    const TileMap tm = tile_map(blockIdx.x, H, W, dil);
     const int b = blockIdx.y;
-    const int y0 = (tile / tiles_x) * TH, x0 = (tile % tiles_x) * TW;
-    // stage the input tile with a one-pixel circular halo (16-byte pieces)
+    // stage the input tile with a one-point circular halo of its sub-grid (16-byte pieces)
     constexpr int V = CIN / 8;  // uint4 per pixel
     for (int i = threadIdx.x; i < HP * V; i += blockDim.x) {
         const int hp = i / V, part = i - hp * V;
         const int hy = hp / (TW + 2), hx = hp - hy * (TW + 2);
-        const int gy = (y0 + hy - 1 + H) & (H - 1), gx = (x0 + hx - 1 + W) & (W - 1);
+        const int gy = tm.gy(tm.Y0 + hy - 1 + tm.Hs), gx = tm.gx(tm.X0 + hx - 1 + tm.Ws);
         const uint4 val = reinterpret_cast<const uint4*>(in + (((size_t)b * H + gy) * W + gx) * CIN)[part];
         *reinterpret_cast<uint4*>(s_in + hp * SP + part * 8) = val;
     }
@@ -125,12 +161,12 @@ __global__ void __launch_bounds__(256) k_conv3x3(const bf16* __restrict__ in, co
             }
         }
     }
-    const int y = y0 + warp;
+    const int y = tm.gy(tm.Y0 + warp);
 #pragma unroll
     for (int m = 0; m < 2; ++m) {
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
-            const int x = x0 + m * 16 + g + 8 * h;
+            const int x = tm.gx(tm.X0 + m * 16 + g + 8 * h);
             const size_t pix = ((size_t)b * H + y) * W + x;
 #pragma unroll
             for (int n = 0; n < NT; ++n) {
@@ -168,7 +204,7 @@ __global__ void __launch_bounds__(256) k_conv3x3(const bf16* __restrict__ in, co
 // ---------------------------------------------------------------------------
 template <int CIN, int COUT>
 __global__ void __launch_bounds__(288) k_wgrad(const bf16* __restrict__ a, const bf16* __restrict__ dz,
-                                               float* partial, float* bpartial, int H, int W, int B) {
+                                               float* partial, float* bpartial, int H, int W, int B, int dil) {
     constexpr int HP = (TH + 2) * (TW + 2);
     constexpr int PT = TH * TW;        // pixels per tile
     constexpr int DZS = PT + 8;        // smem stride of dz^T rows (halves)
@@ -189,22 +225,21 @@ __global__ void __launch_bounds__(288) k_wgrad(const bf16* __restrict__ a, const
 #pragma unroll
             for (int q = 0; q < 4; ++q) acc[m][n][q] = 0.f;
     float bacc = 0.f;
-    const int tiles_x = W / TW, tiles = (H / TH) * tiles_x * B;
+    const int per_img = (H / TH) * (W / TW), tiles = per_img * B;
     const uint32_t* s_dz32 = reinterpret_cast<const uint32_t*>(s_dz);
     for (int ti = blockIdx.x; ti < tiles; ti += gridDim.x) {
-        const int b = ti / ((H / TH) * tiles_x);
-        const int tt = ti - b * (H / TH) * tiles_x;
-        const int y0 = (tt / tiles_x) * TH, x0 = (tt % tiles_x) * TW;
+        const int b = ti / per_img;
+        const TileMap tm = tile_map(ti - b * per_img, H, W, dil);
         __syncthreads();
         for (int i = threadIdx.x; i < PT * COUT; i += blockDim.x) {
             const int p = i / COUT, co = i - p * COUT;
-            const size_t pix = ((size_t)b * H + y0 + p / TW) * W + x0 + (p % TW);
+            const size_t pix = ((size_t)b * H + tm.gy(tm.Y0 + p / TW)) * W + tm.gx(tm.X0 + (p % TW));
             s_dz[co * DZS + p] = dz[pix * COUT + co];
         }
         for (int i = threadIdx.x; i < HP * CIN; i += blockDim.x) {
             const int hp = i / CIN, ci = i - hp * CIN;
             const int hy = hp / (TW + 2), hx = hp - hy * (TW + 2);
-            const int gy = (y0 + hy - 1 + H) & (H - 1), gx = (x0 + hx - 1 + W) & (W - 1);
+            const int gy = tm.gy(tm.Y0 + hy - 1 + tm.Hs), gx = tm.gx(tm.X0 + hx - 1 + tm.Ws);
             s_a[ci * AS + hp] = a[(((size_t)b * H + gy) * W + gx) * CIN + ci];
         }
         __syncthreads();
@@ -535,10 +570,13 @@ extern "C" int reg_net_get_params(reg_net* n, float* params) {
     return e == cudaSuccess ? REG_OK : reg_fail(REG_ERR_CUDA, cudaGetErrorString(e));
 }
 
+// out = P G in per velocity (the output map; also its adjoint G P, since P and G
+// are commuting symmetric Fourier multipliers)
 static int leray_batch(reg_net* n, const float* in, float* out, int B) {
     const size_t f = (size_t)2 * n->H * n->W;
+    const double sigma = 2.0 * (2.0 * M_PI / (double)(n->H > n->W ? n->H : n->W));
     for (int b = 0; b < B; ++b) {
-        const int st = reg_apply_proj(n->proj, in + b * f, out + b * f);
+        const int st = apply_smooth_proj(n->proj, (float)(0.5 * sigma * sigma), in + b * f, out + b * f);
         if (st != REG_OK) return st;
     }
     return REG_OK;
@@ -551,12 +589,13 @@ static int net_forward(reg_net* n, const float* images, int B) {
     for (int l = 0; l < NLAYER; ++l) {
         const float* bias = n->bpad + 32 * l;
         const bf16* wl = n->wf + n->wfoff[l];
+        const int d = layer_dil(l, H, W);
         if (l == 0)
-            k_conv3x3<16, 32, 0><<<grid, 256, conv_smem(16, 32), n->stream>>>(n->act[0], wl, bias, n->act[1], nullptr, H, W);
+            k_conv3x3<16, 32, 0><<<grid, 256, conv_smem(16, 32), n->stream>>>(n->act[0], wl, bias, n->act[1], nullptr, H, W, d);
         else if (l < NLAYER - 1)
-            k_conv3x3<32, 32, 0><<<grid, 256, conv_smem(32, 32), n->stream>>>(n->act[l], wl, bias, n->act[l + 1], nullptr, H, W);
+            k_conv3x3<32, 32, 0><<<grid, 256, conv_smem(32, 32), n->stream>>>(n->act[l], wl, bias, n->act[l + 1], nullptr, H, W, d);
         else
-            k_conv3x3<32, 16, 1><<<grid, 256, conv_smem(32, 16), n->stream>>>(n->act[l], wl, bias, n->out, nullptr, H, W);
+            k_conv3x3<32, 16, 1><<<grid, 256, conv_smem(32, 16), n->stream>>>(n->act[l], wl, bias, n->out, nullptr, H, W, d);
     }
     const cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return reg_fail(REG_ERR_CUDA, std::string("net forward: ") + cudaGetErrorString(e));
@@ -581,7 +620,7 @@ static int net_loss_grad(reg_net* n, const float* images, const float* targets, 
     const long long M = 2LL * B * H * W;
     k_residual<<<256, 256, 0, n->stream>>>(n->pred, targets, n->res, M, n->d_part);
     cudaMemcpyAsync(n->h_part, n->d_part, sizeof(double) * 256, cudaMemcpyDeviceToHost, n->stream);
-    st = leray_batch(n, n->res, n->dout, B);  // dL/d out = P r / M (scaled below)
+    st = leray_batch(n, n->res, n->dout, B);  // dL/d out = G P r / M (scaled below)
     if (st != REG_OK) return st;
     k_pack_grad<<<304, 256, 0, n->stream>>>(n->dout, n->dzA, B, H, W);
     const dim3 grid((H / TH) * (W / TW), B);
@@ -592,21 +631,22 @@ static int net_loss_grad(reg_net* n, const float* images, const float* targets, 
         const LayerDesc& L = n->layers[l];
         float* gWl = n->gW + n->gwoff[l];
         float* gbl = n->gb + n->gboff[l];
+        const int d = layer_dil(l, H, W);
         if (l == NLAYER - 1)
-            k_wgrad<32, 16><<<n->nwg, 288, wgrad_smem(32, 16), n->stream>>>(n->act[l], dz, n->partial, n->bpartial, H, W, B);
+            k_wgrad<32, 16><<<n->nwg, 288, wgrad_smem(32, 16), n->stream>>>(n->act[l], dz, n->partial, n->bpartial, H, W, B, d);
         else if (l > 0)
-            k_wgrad<32, 32><<<n->nwg, 288, wgrad_smem(32, 32), n->stream>>>(n->act[l], dz, n->partial, n->bpartial, H, W, B);
+            k_wgrad<32, 32><<<n->nwg, 288, wgrad_smem(32, 32), n->stream>>>(n->act[l], dz, n->partial, n->bpartial, H, W, B, d);
         else
-            k_wgrad<16, 32><<<n->nwg, 288, wgrad_smem(16, 32), n->stream>>>(n->act[0], dz, n->partial, n->bpartial, H, W, B);
+            k_wgrad<16, 32><<<n->nwg, 288, wgrad_smem(16, 32), n->stream>>>(n->act[0], dz, n->partial, n->bpartial, H, W, B, d);
         const int nw = L.coutp * 9 * L.cinp, nb = L.coutp;
         k_wgrad_reduce<<<(nw + nb + 255) / 256, 256, 0, n->stream>>>(n->partial, n->bpartial, n->nwg, nw, nb, gWl, gbl);
         if (l > 0) {
             // input gradient through the ReLU of layer l-1: correlation with the flipped, transposed kernel
             const bf16* wtl = n->wt + n->wfoff[l];
             if (l == NLAYER - 1)
-                k_conv3x3<16, 32, 2><<<grid, 256, conv_smem(16, 32), n->stream>>>(dz, wtl, nullptr, dnext, n->act[l], H, W);
+                k_conv3x3<16, 32, 2><<<grid, 256, conv_smem(16, 32), n->stream>>>(dz, wtl, nullptr, dnext, n->act[l], H, W, d);
             else
-                k_conv3x3<32, 32, 2><<<grid, 256, conv_smem(32, 32), n->stream>>>(dz, wtl, nullptr, dnext, n->act[l], H, W);
+                k_conv3x3<32, 32, 2><<<grid, 256, conv_smem(32, 32), n->stream>>>(dz, wtl, nullptr, dnext, n->act[l], H, W, d);
             bf16* tmp = dz; dz = dnext; dnext = tmp;
         }
     }

@@ -1,5 +1,5 @@
 // Shared-memory FFT building blocks for the pseudospectral discretization
-// (Sec. 5 of Mang & Biros: Fourier basis in space).
+// (Sec. 4 of Mang & Biros: Fourier basis in space).
 //
 // Transforms are unnormalized Stockham auto-sort FFTs (decimation in
 // frequency, radix 4 with a final radix-2 pass when log2(L) is odd) over

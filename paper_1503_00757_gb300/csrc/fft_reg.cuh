@@ -1,4 +1,4 @@
-// Register-resident radix-8 FFTs for the pseudospectral operators (Sec. 5 of
+// Register-resident radix-8 FFTs for the pseudospectral operators (Sec. 4 of
 // Mang & Biros: Fourier basis in space).
 //
 // A length-L transform (L = 2^LOGL, 16 <= L <= 1024) is computed by T = L/8

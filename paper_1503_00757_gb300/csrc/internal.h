@@ -19,7 +19,8 @@ enum SpecOp {
     OP_ENERGY = 6,   // 2 in -> 0 out: FP64 sum of the quadratic regularization energy
     OP_DIVT_PROJ = 7, // 5 in -> 2 out: P_L(coefA * div(T) + b), T = (T11, T12, T22)
     OP_GRAD1 = 8,     // 1 in -> 1 out: i k1~ x (d2 is diagonal in the row spectra; see AdvArgs::Sd2)
-    OP_DIV1 = 9       // in[0] transformed, in[1] raw -> 1 out: i k1~ x0 + (i k2~ / n2) x1 (x1 not transformed)
+    OP_DIV1 = 9,      // in[0] transformed, in[1] raw -> 1 out: i k1~ x0 + (i k2~ / n2) x1 (x1 not transformed)
+    OP_SMOOTH_PROJ = 10  // 2 in -> 2 out: exp(-coefA |k|^2) P_L x (Gaussian low-pass, then Leray)
 };
 
 // Projection modes (Eq. (e:project-body-force)):
@@ -98,6 +99,8 @@ struct reg_ctx {
 
     float2* tw;      // twiddle table (REG_TW_N entries)
 
+    int tileR, tileC;  // rows per row-kernel CTA, spectrum columns per column-kernel CTA (0: default)
+
     long long launches;
     bool pdl;         // launch with programmatic dependent launch (default on)
     bool use_graphs;
@@ -110,6 +113,12 @@ struct reg_ctx {
     double tms[KC_COUNT];
     double tbytes[KC_COUNT];
 };
+
+// ---- FFT tile choices (kernels.cu: defaults and limits; tune.cu: autotuner table) ----
+void default_tiles(int n1, int n2, int* R, int* C);
+bool tiles_valid(int n1, int n2, int R, int C);
+// tuned (R, C) for this device and grid, if reg_autotune has measured it
+bool tuned_tiles(int dev, int n1, int n2, int* R, int* C);
 
 // ---- launchers (kernels.cu); all asynchronous on ctx->stream ----
 cudaError_t k_init_twiddles(reg_ctx* ctx);
@@ -189,3 +198,7 @@ void ktimer_begin(reg_ctx* ctx, int kclass, double bytes);
 void ktimer_end(reg_ctx* ctx);
 
 int reg_fail(int status, const std::string& msg);
+
+// out = exp(-a |k|^2) P_L b on the context's grid (velocity fields, device):
+// the output map of the warm-start network (Gaussian low-pass, then Leray).
+int apply_smooth_proj(reg_ctx* ctx, float a, const float* b, float* out);

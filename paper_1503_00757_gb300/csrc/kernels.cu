@@ -4,7 +4,7 @@
 // A 2-D transform of an n1 x n2 real field is split into two passes over HBM:
 //   * row kernels: one CTA owns R consecutive rows; real FFTs along x^2
 //     (two real rows, or two real fields of one row, per complex FFT), fused
-//     with the pointwise work of an RK2 stage (Sec. 5) on the physical side;
+//     with the pointwise work of an RK2 stage (Sec. 4) on the physical side;
 //   * column kernels: one CTA owns C consecutive columns of the packed half
 //     spectra (row-quad tiled layout, see fft_reg.cuh); forward FFT along x^1,
 //     a Fourier multiplier (gradient, divergence, A, K, preconditioner,
@@ -14,6 +14,7 @@
 // deformation gradient (Eq. (e:def-grad)); FP64 accumulation for all sums.
 #include <cmath>
 #include <cstdio>
+#include <mutex>
 #include <unordered_map>
 #include <vector>
 
@@ -344,7 +345,7 @@ __global__ void __launch_bounds__(512, RowBlocks<LOGL>::value) k_row_adv(AdvArgs
 // time (Eq. (e:adj-eq-elim), (e:inc-adj-eq-elim) without the lambda term):
 //   k = div(lam_s v); stage 1: lam* = lam_j + h k; stage 2: lam_{j-1} = (lam_j + lam* + h k) / 2
 // Stage 2 also accumulates the body force b += w lam_{j-1} grad m_{j-1}
-// (trapezoidal rule, Sec. 4.1 / Sec. 5); the flux lam_out v leaves as two
+// (trapezoidal rule, Sec. 3.1 / Sec. 4); the flux lam_out v leaves as two
 // packed spectra for the next divergence.
 // ---------------------------------------------------------------------------
 template <int LOGL>
@@ -519,6 +520,12 @@ __device__ __forceinline__ void spec_apply(const SpecParams& P, float k1o, float
         proj_sym(P, P.pmode, k1o, k2o, kk, K11, K12, K22);
         y[0] = cscale(cadd(cscale(x[0], K11), cscale(x[1], K12)), s);
         y[1] = cscale(cadd(cscale(x[0], K12), cscale(x[1], K22)), s);
+    } else if (OP == OP_SMOOTH_PROJ) {
+        float K11, K12, K22;
+        proj_sym(P, PROJ_LERAY, k1o, k2o, kk, K11, K12, K22);
+        const float gs = expf(-P.coefA * kk) * s;
+        y[0] = cscale(cadd(cscale(x[0], K11), cscale(x[1], K12)), gs);
+        y[1] = cscale(cadd(cscale(x[0], K12), cscale(x[1], K22)), gs);
     } else if (OP == OP_PRECOND) {
         float a = reg_sym(P.regnorm, kk);
         if (kk == 0.f) a = 1.f;
@@ -660,27 +667,52 @@ __global__ void __launch_bounds__(256) k_col(ColArgs a, const float2* __restrict
 // ---------------------------------------------------------------------------
 // launch helpers
 // ---------------------------------------------------------------------------
-// R rows per row CTA: a multiple of 4 with at least 64 threads (T = L/8 per row)
-static int rows_per_cta(int n1, int L) {
-    const int T = L / 8;
+// Default tile choices.  R rows per row CTA: a multiple of 4 with at least 64
+// threads (T = L/8 per row); C spectrum columns per column CTA: at least 2
+// (64-byte segments) and 64 threads.  reg_autotune may replace both per grid.
+void default_tiles(int n1, int n2, int* R_out, int* C_out) {
     int R = 4;
-    while (R * T < 64 && R * 2 <= n1) R *= 2;
-    return R;
+    while (R * (n2 / 8) < 64 && R * 2 <= n1) R *= 2;
+    const int W = n2 / 2;
+    int C = 2;
+    while (C * (n1 / 8) < 64 && C * 2 <= W) C *= 2;
+    *R_out = R;
+    *C_out = C > W ? W : C;
 }
 
-// C columns per column CTA: at least 2 (64-byte segments) and 64 threads
-static int cols_per_cta(int W, int L) {
-    const int T = L / 8;
-    int c = 2;
-    while (c * T < 64 && c * 2 <= W) c *= 2;
-    return c > W ? W : c;
+// Launch limits of the row kernels (32 to 512 threads; 2 CTAs per SM for
+// 1024-point rows) and the column kernel (32 to 256 threads), and 227 KB of
+// shared memory (3 complex buffers of R rows or C columns).
+bool tiles_valid(int n1, int n2, int R, int C) {
+    const size_t smax = 227 * 1024;
+    const int W = n2 / 2;
+    if (R < 4 || (R & 3) || R > n1 || (n1 % R)) return false;
+    if (R * (n2 / 8) < 32 || R * (n2 / 8) > 512 || 3 * (size_t)R * n2 * sizeof(float2) > smax) return false;
+    if (C < 2 || (C & (C - 1)) || C > W || (W % C)) return false;
+    if (C * (n1 / 8) < 32 || C * (n1 / 8) > 256 || 3 * (size_t)C * n1 * sizeof(float2) > smax) return false;
+    return true;
 }
 
-// Opt in to more than 48 KB of dynamic shared memory once per kernel instantiation and size.
+static int rows_per_cta(const reg_ctx* ctx) {
+    int R, C;
+    default_tiles(ctx->n1, ctx->n2, &R, &C);
+    return ctx->tileR > 0 ? ctx->tileR : R;
+}
+
+static int cols_per_cta(const reg_ctx* ctx) {
+    int R, C;
+    default_tiles(ctx->n1, ctx->n2, &R, &C);
+    return ctx->tileC > 0 ? ctx->tileC : C;
+}
+
+// Opt in to more than 48 KB of dynamic shared memory once per kernel instantiation and size
+// (contexts on several host threads launch concurrently, hence the lock).
 template <typename K>
 static void set_smem(K kern, size_t bytes) {
     if (bytes <= 32 * 1024) return;  // static shared memory (reductions) also counts toward the 48 KB default
+    static std::mutex mu;
     static std::unordered_map<const void*, size_t> done;
+    std::lock_guard<std::mutex> lock(mu);
     auto it = done.find((const void*)kern);
     if (it != done.end() && it->second >= bytes) return;
     cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
@@ -703,7 +735,7 @@ struct RowCfg { int R, threads; size_t smem; int grid; };
 static RowCfg row_cfg(reg_ctx* ctx) {
     RowCfg c;
     const int L = ctx->n2;
-    c.R = rows_per_cta(ctx->n1, L);
+    c.R = rows_per_cta(ctx);
     c.threads = c.R * (L / 8);
     c.smem = 3 * (size_t)c.R * L * sizeof(float2);
     c.grid = ctx->n1 / c.R;
@@ -802,7 +834,7 @@ template <int NIN, int NOUT, int OP>
 static void launch_col_t(reg_ctx* ctx, const float2* const* in, float2* const* out, const SpecParams& P,
                          double* part) {
     const int L = ctx->n1, W = ctx->n2 / 2;
-    const int cpb = cols_per_cta(W, L);
+    const int cpb = cols_per_cta(ctx);
     const size_t smem = 3 * (size_t)cpb * L * sizeof(float2);
     ColArgs a;
     for (int f = 0; f < 5; ++f) a.in[f] = (f < NIN) ? in[f] : nullptr;
@@ -823,7 +855,7 @@ static void launch_col_t(reg_ctx* ctx, const float2* const* in, float2* const* o
 
 int col_blocks(reg_ctx* ctx) {
     const int L = ctx->n1, W = ctx->n2 / 2;
-    return W / cols_per_cta(W, L);
+    return W / cols_per_cta(ctx);
 }
 
 void launch_col(reg_ctx* ctx, int op, const float2* const* in, float2* const* out, const SpecParams& P,
@@ -839,6 +871,7 @@ void launch_col(reg_ctx* ctx, int op, const float2* const* in, float2* const* ou
         case OP_DIVT_PROJ: launch_col_t<5, 2, OP_DIVT_PROJ>(ctx, in, out, P, part); break;
         case OP_GRAD1: launch_col_t<1, 1, OP_GRAD1>(ctx, in, out, P, part); break;
         case OP_DIV1: launch_col_t<1, 1, OP_DIV1>(ctx, in, out, P, part); break;
+        case OP_SMOOTH_PROJ: launch_col_t<2, 2, OP_SMOOTH_PROJ>(ctx, in, out, P, part); break;
         default: break;
     }
 }

@@ -13,12 +13,12 @@ Workloads (stand-ins for the paper's image data, which are not available):
     modes |k| <= 4.
   * ``labels_pair``: smoothed piecewise-constant 4-label images (level sets of
     a low-mode random field, label intensities U[0, 1]), Gaussian noise
-    sigma = 0.01, then Gaussian pre-smoothing with width 2 h (Sec. 5 of the
+    sigma = 0.01, then Gaussian pre-smoothing with width 2 h (Sec. 4 of the
     paper pre-smooths its data); velocity with modes |k| <= 8 and a
     compressible (gradient) part.
   * ``ellipses_pair``: "brain-like" nested smoothed ellipses with 5 labels and
     random contrasts in [0.1, 1]; divergence-free velocity with |k| <= 16.
-All images are rescaled to [0, 1] (Sec. 5).
+All images are rescaled to [0, 1] (Sec. 4).
 """
 import numpy as np
 
@@ -192,3 +192,38 @@ def labels_pair(n, seed, vmax=0.8, kmax=8, nlabels=4, noise=0.01, grad_fraction=
     mT = gaussian_smooth(render(fT) + noise * rng.standard_normal((n, n)), 2.0 * h)
     mR = gaussian_smooth(render(fR) + noise * rng.standard_normal((n, n)), 2.0 * h)
     return rescale01(mT), rescale01(mR), v
+
+
+def _ellipses_job(job):
+    n, seed, vmax = job
+    mT, mR, _ = ellipses_pair(n, seed, vmax=vmax, kmax=min(16, n // 4))
+    return mT.astype(np.float32), mR.astype(np.float32)
+
+
+def ellipses_images(jobs, workers=1):
+    """[(m_T, m_R)] float32 for jobs [(n, seed, vmax)] (``ellipses_pair`` with
+    kmax = min(16, n/4)); workers > 1 uses spawned worker processes, which is safe
+    after CUDA has been initialised in the calling process.  The calling script
+    must guard its top level with ``if __name__ == "__main__":`` (spawned workers
+    import it); a worker that dies raises BrokenProcessPool here instead of being
+    replaced."""
+    jobs = list(jobs)
+    if workers > 1 and len(jobs) > 32:
+        import multiprocessing as mp
+        import os
+        from concurrent.futures import ProcessPoolExecutor
+        # one BLAS thread per worker process (the children inherit this environment)
+        keys = ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS")
+        saved = {k: os.environ.get(k) for k in keys}
+        for k in keys:
+            os.environ[k] = "1"
+        try:
+            with ProcessPoolExecutor(max_workers=workers, mp_context=mp.get_context("spawn")) as pool:
+                return list(pool.map(_ellipses_job, jobs, chunksize=8))
+        finally:
+            for k, v in saved.items():
+                if v is None:
+                    os.environ.pop(k, None)
+                else:
+                    os.environ[k] = v
+    return [_ellipses_job(j) for j in jobs]

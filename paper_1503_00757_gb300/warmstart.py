@@ -11,7 +11,7 @@ Pipeline (all compute on the GPU through the C ABI):
      network's prediction (``opts.warm_start = 1``; the stopping test keeps
      g_ref = g(0), so both starts target the same absolute gradient).
 
-Usage (GPU):  python -m paper_1503_00757_gb300.warmstart --train 1000 --test 100
+Usage (GPU):  python -m paper_1503_00757_gb300.warmstart --train 20000 --test 1000
 """
 import argparse
 import json
@@ -25,11 +25,12 @@ N_DEFAULT, NT, BETA, VMAX = 256, 16, 1e-3, 0.098
 TRAIN_SEED, TEST_SEED = 5_000_000, 6_000_000
 
 
-def make_images(n, seeds, vmax=VMAX):
+def make_images(n, seeds, vmax=VMAX, workers=1):
+    """Image pairs (len(seeds), 2, n, n) of ``synth.ellipses_pair`` (workers > 1: spawned process pool)."""
     from . import synth
+    seeds = list(seeds)
     x = np.empty((len(seeds), 2, n, n), dtype=np.float32)
-    for i, s in enumerate(seeds):
-        mT, mR, _ = synth.ellipses_pair(n, s, vmax=vmax, kmax=min(16, n // 4))
+    for i, (mT, mR) in enumerate(synth.ellipses_images([(n, s, vmax) for s in seeds], workers)):
         x[i, 0], x[i, 1] = mT, mR
     return x
 
@@ -109,12 +110,13 @@ def main():
 
     ap = argparse.ArgumentParser()
     ap.add_argument("--n", type=int, default=N_DEFAULT)
-    ap.add_argument("--train", type=int, default=2000)
-    ap.add_argument("--test", type=int, default=100)
-    ap.add_argument("--epochs", type=int, default=40)
+    ap.add_argument("--train", type=int, default=20000)
+    ap.add_argument("--test", type=int, default=1000)
+    ap.add_argument("--epochs", type=int, default=20)
     ap.add_argument("--batch", type=int, default=8)
     ap.add_argument("--lr", type=float, default=2e-3)
     ap.add_argument("--workers", type=int, default=8)
+    ap.add_argument("--init", default=None, help="initial parameters (.npy, flat FP32); default: He initialisation")
     ap.add_argument("--out", default="gpurun_out/warmstart.json")
     ap.add_argument("--weights", default="gpurun_out/warmstart_weights.npy")
     args = ap.parse_args()
@@ -123,8 +125,9 @@ def main():
     opts = default_opts(tol=1e-2, maxit_newton=50)
     ex = Executor(args.workers)
     t = time.perf_counter()
-    x_tr = make_images(n, range(TRAIN_SEED, TRAIN_SEED + args.train))
-    x_te = make_images(n, range(TEST_SEED, TEST_SEED + args.test))
+    nproc = max(1, min(16, os.cpu_count() or 1))
+    x_tr = make_images(n, range(TRAIN_SEED, TRAIN_SEED + args.train), workers=nproc)
+    x_te = make_images(n, range(TEST_SEED, TEST_SEED + args.test), workers=nproc)
     log(f"images: {time.perf_counter() - t:.1f} s")
     v_tr, st_tr, sec_tr = solve_all(x_tr, ex, opts)
     log(f"targets: {sec_tr:.1f} s, {summarize(st_tr, sec_tr)}")
@@ -132,21 +135,27 @@ def main():
     x_tr = x_tr[keep]
     v_tr = v_tr[torch.tensor(keep, device="cuda")].contiguous()
     net = Net(n, n, args.batch)
-    net.set_params(torch.tensor(flatten_params(oracle_cnn.init_params(1)), dtype=torch.float32, device="cuda"))
+    if args.init:
+        p0 = torch.from_numpy(np.load(args.init).astype(np.float32)).cuda()
+    else:
+        p0 = torch.tensor(flatten_params(oracle_cnn.init_params(1)), dtype=torch.float32, device="cuda")
+    net.set_params(p0)
     t = time.perf_counter()
     losses = train(net, x_tr, v_tr, args.epochs, args.batch, args.lr, log=log)
     train_s = time.perf_counter() - t
     # evaluation: zero start vs warm start on held-out pairs
-    _, st_zero, sec_zero = solve_all(x_te, ex, opts)
+    v_zero, st_zero, sec_zero = solve_all(x_te, ex, opts)
     t = time.perf_counter()
     v_pred = predict(net, x_te, args.batch)
     pred_s = time.perf_counter() - t
+    rel = ((v_pred - v_zero).flatten(1).norm(dim=1) / v_zero.flatten(1).norm(dim=1).clamp_min(1e-30))
     wopts = default_opts(tol=1e-2, maxit_newton=50, warm_start=1)
     _, st_warm, sec_warm = solve_all(x_te, ex, wopts, v0=v_pred)
     res = {"n": n, "nt": NT, "beta_v": BETA, "train_pairs": len(keep), "test_pairs": args.test,
            "epochs": args.epochs, "batch": args.batch, "train_seconds": train_s, "loss_first": losses[0],
            "loss_last": losses[-1], "zero_start": summarize(st_zero, sec_zero),
-           "warm_start": summarize(st_warm, sec_warm + pred_s), "predict_seconds": pred_s}
+           "warm_start": summarize(st_warm, sec_warm + pred_s), "predict_seconds": pred_s,
+           "prediction_rel_error_mean": float(rel.mean())}
     log(json.dumps(res))
     os.makedirs(os.path.dirname(args.out) or ".", exist_ok=True)
     with open(args.out, "w") as f:

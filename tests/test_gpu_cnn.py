@@ -40,21 +40,35 @@ def _rel(a, b):
     return float(np.linalg.norm(a - b) / np.linalg.norm(b))
 
 
-def test_forward_and_gradients_match_oracle():
+def _random_data(H, W, B, seed):
+    """Smooth random images and a divergence-free random target on a non-square grid."""
+    rng = np.random.default_rng(seed)
+    x = np.stack([np.stack([synth.gaussian_smooth(rng.random((H, W)), 0.1) for _ in range(2)]) for _ in range(B)])
+    t = cnn.leray(0.1 * np.stack([np.stack([synth.gaussian_smooth(rng.standard_normal((H, W)), 0.3)
+                                            for _ in range(2)]) for _ in range(B)]))
+    return x, t
+
+
+@pytest.mark.parametrize("H,W,B", [(64, 64, 2), (64, 256, 1)])
+def test_forward_and_gradients_match_oracle(H, W, B):
+    """(64, 64): dilations 1, 2, ..., 2, 1; (64, 256): the full schedule 1, 2, 4, 8, 8, 4, 2, 1
+    (8 x 32 sub-grids, one tile each at d = 8)."""
     import torch
     from paper_1503_00757_gb300.binding import Net, flatten_params, unflatten_params
-    n, B = 64, 2
     params = cnn.init_params(11)
     rng = np.random.default_rng(12)
-    params = [(bf16_round(W), rng.standard_normal(b.shape) * 0.05) for W, b in params]
-    x, t = _data(n, B, 5000)
+    params = [(bf16_round(W_), rng.standard_normal(b.shape) * 0.05) for W_, b in params]
+    if H == W:
+        x, t = _data(H, B, 5000)
+    else:
+        x, t = _random_data(H, W, B, 5050)
     x = bf16_round(x)
-    net = Net(n, n, B)
+    net = Net(H, W, B)
     flat = flatten_params(params)
     net.set_params(torch.tensor(flat, dtype=torch.float32, device="cuda"))
     xg = torch.tensor(x, dtype=torch.float32, device="cuda").contiguous()
     tg = torch.tensor(t, dtype=torch.float32, device="cuda").contiguous()
-    v = torch.empty(B, 2, n, n, device="cuda")
+    v = torch.empty(B, 2, H, W, device="cuda")
     net.forward(xg, v)
     torch.cuda.synchronize()
     v_ref = cnn.predict(params, x)

@@ -117,7 +117,7 @@ def cfl_scaled(vs, n1, n2, nt, cfl=0.3):
     """Scale v so that max|v| nt^-1 / h_x = cfl.  Above ~0.3, Heun's per-step
     amplification of the highest modes, sqrt(1 + z^4/4) with z = pi * CFL,
     multiplies FP32 round-off by up to |.|^nt in every transport solve (the
-    paper adapts nt to the CFL condition, Sec. 6.1)."""
+    paper adapts nt to the CFL condition, Sec. 5.1)."""
     vmax = np.sqrt(vs[0] ** 2 + vs[1] ** 2).max()
     return vs * (cfl * 2 * np.pi * nt / (max(n1, n2) * vmax))
 

@@ -20,7 +20,7 @@ def test_nu_mapping():
 
 def test_nu_one_reduces_to_linear_stokes():
     """nu = 1: eta = 1 and Q = 0, so A = -div 2E = -Lap on divergence-free
-    band-limited fields (Sec. 3: linear Stokes regularization)."""
+    band-limited fields (Sec. 2: linear Stokes regularization)."""
     v = synth.velocity(32, 32, 6, 0.5, np.random.default_rng(0))
     Av = SH.first_variation(v, 1.0)
     assert np.abs(Av - S.apply_A(v, S.H1)).max() < 1e-10 * np.abs(Av).max()
