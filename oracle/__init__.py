@@ -11,7 +11,7 @@ holds none of the method's arithmetic.
 
 Everything here is plain, slow and written to be checked against the paper by
 eye: FP64 numpy arrays, an own radix-2 FFT (``oracle.fft``), the spectral
-operators of Sec. 4.3 / Eq. (e:project-body-force) (``oracle.spectral``), the
+operators of Sec. 3.3 / Eq. (e:project-body-force) (``oracle.spectral``), the
 RK2 transport solves of Eqs. (e:state-eq-elim)-(e:inc-adj-eq-elim)
 (``oracle.transport``), the reduced gradient, Gauss-Newton Hessian matvec,
 PCG (Algorithm 2), Armijo line search and Newton outer loop (Algorithm 1)

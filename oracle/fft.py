@@ -1,6 +1,6 @@
 """Own radix-2 fast Fourier transform in FP64 (oracle; test infrastructure only).
 
-The paper discretizes space with a pseudospectral Fourier basis (Sec. 5,
+The paper discretizes space with a pseudospectral Fourier basis (Sec. 4,
 "Numerics").  The oracle does not rely on a library FFT for this: it runs a
 textbook iterative Cooley-Tukey decimation-in-time transform (bit-reversal
 permutation, then log2(n) butterfly sweeps), vectorized over all other axes.

@@ -7,10 +7,10 @@ Follows, in the paper's order and notation:
   * reduced gradient g = beta_v A[v] + K[b] (Eq. (e:control-eq-elim)), with
     the state solve, adjoint solve and body force of Algorithm 1;
   * Gauss-Newton Hessian matvec H v~ = beta_v B[v~] + L[b~]
-    (Eq. (e:inc-control-eq-elim)) with the lambda terms dropped (Sec. 5);
+    (Eq. (e:inc-control-eq-elim)) with the lambda terms dropped (Sec. 4);
   * PCG inner iteration, Algorithm 2, preconditioned by (beta_v A)^-1
     (Appendix E);
-  * Armijo backtracking line search (Sec. 5: Nocedal-Wright Algorithm 3.1,
+  * Armijo backtracking line search (Sec. 4: Nocedal-Wright Algorithm 3.1,
     default parameters) and the Newton outer iteration, Algorithm 1.
 
 Readings of passages the paper leaves open or garbles:
@@ -32,12 +32,12 @@ Readings of passages the paper leaves open or garbles:
     w = div v (Eq. (e:reg-w)).
   * If PCG meets a non-positive curvature <s, H s> <= 0 it stops (a plain
     safeguard; the Gauss-Newton Hessian is positive definite in exact
-    arithmetic, Sec. 5).  If the returned step is not a descent direction
+    arithmetic, Sec. 4).  If the returned step is not a descent direction
     (<g, v~> >= 0) the preconditioned steepest-descent step -(beta_v A)^-1 g
     is used instead.
   * nt policy: "fixed" uses nt as given; "cfl" uses, at every outer
     iteration, nt_used = max(nt, ceil(max|v| n / (2 pi c_max))) with
-    c_max = 0.25 and n = max(n1, n2) (Sec. 6.1 adapts nt to the CFL
+    c_max = 0.25 and n = max(n1, n2) (Sec. 5.1 adapts nt to the CFL
     condition).
 """
 import math

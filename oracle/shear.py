@@ -1,7 +1,7 @@
 """Nonlinear Stokes ("shear control") regularization (oracle; test
 infrastructure only).
 
-Model (Sec. 3, Eq. (e:shear-control-reg-v)): with the strain rate tensor
+Model (Sec. 2, Eq. (e:shear-control-reg-v)): with the strain rate tensor
 E[v] = (grad v + grad v^T)/2 and flow-law exponent nu > 0,
 
     R[v] = beta_v * (2 nu / (nu + 1)) * int (E:E + eps^2)^((1 + nu) / (2 nu)) dx.
@@ -19,7 +19,7 @@ Readings the paper leaves open:
     nu = (1 + s) / (1 - s) (s = 0: linear Stokes, s = 1/2: nu = 3, the paper's
     shear-thinning value, s = -1/2: nu = 1/3, shear thickening).
   * Only the incompressible case (w = 0) is supported; the paper reports no
-    results for the mass-source variant (Sec. 6.2).  For divergence-free
+    results for the mass-source variant (Sec. 5.2).  For divergence-free
     v and v~ the paper's K[b, v] and L(v)[b~, v~] (Eqs. (e:control-eq-ns),
     (e:project-inc-body-force-nls)) equal the Leray projection of
     beta_v A[v] + b and beta_v B(v)[v~] + b~: the mean-viscosity parts cancel

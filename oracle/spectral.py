@@ -2,11 +2,11 @@
 infrastructure only).
 
 Domain and grid.  The paper's domain is Omega = (-pi, pi)^2 with periodic
-boundary conditions (notation table, Sec. 2).  On a periodic grid this is the
+boundary conditions (notation, Sec. 1.5).  On a periodic grid this is the
 same as [0, 2 pi)^2; node (i, j) sits at x = (2 pi i / n1, 2 pi j / n2).  Arrays
 are indexed [i, j]: axis 0 is x^1 ("rows"), axis 1 is x^2 ("columns").
 
-Quadrature.  Inner products use the trapezoidal rule the paper names in Sec. 5,
+Quadrature.  Inner products use the trapezoidal rule the paper names in Sec. 4,
 which on a periodic grid is <f, g> = h1 h2 sum f g with h = 2 pi / n.
 
 Fourier symbols (readings the paper leaves open, stated once here):

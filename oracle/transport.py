@@ -2,14 +2,14 @@
 infrastructure only).
 
 Time integration: the paper uses "an explicit second order Runge-Kutta
-method" (Sec. 5) without naming the variant.  The oracle uses Heun's method
+method" (Sec. 4) without naming the variant.  The oracle uses Heun's method
 (explicit trapezoid):  y* = y_j + h f(t_j, y_j),  y_{j+1} = y_j + h/2 (f(t_j, y_j)
 + f(t_{j+1}, y*)), h = 1/nt.  For a stationary velocity every two-stage RK2
 gives the same update for the homogeneous equations; the variant only matters
 for the source term of the incremental state equation, which is evaluated at
 t_j and t_{j+1} from the stored state history.
 
-Time quadrature: trapezoidal rule (Sec. 5), weights h (1/2, 1, ..., 1, 1/2).
+Time quadrature: trapezoidal rule (Sec. 4), weights h (1/2, 1, ..., 1, 1/2).
 """
 import numpy as np
 
@@ -48,7 +48,7 @@ def adjoint_solve(lam_final, v, nt):
     backward in time from lam(1) = lam_final.  With tau = 1 - t this is
     d_tau lam = div(lam v).  Returns lam[j] = lam(t_j), j = 0..nt.  The same
     routine solves the Gauss-Newton incremental adjoint equation
-    (Eq. (e:inc-adj-eq-elim) with the lambda term dropped, Sec. 5)."""
+    (Eq. (e:inc-adj-eq-elim) with the lambda term dropped, Sec. 4)."""
     h = 1.0 / nt
     lam = np.empty((nt + 1,) + lam_final.shape)
     lam[nt] = lam_final
@@ -61,7 +61,7 @@ def adjoint_solve(lam_final, v, nt):
 
 
 def body_force(lam, gradm):
-    """b = int_0^1 lam grad m dt (Sec. 4.1), trapezoidal rule in time.
+    """b = int_0^1 lam grad m dt (Sec. 3.1), trapezoidal rule in time.
     lam: (nt+1, n1, n2); gradm: (nt+1, 2, n1, n2)."""
     nt = lam.shape[0] - 1
     w = trapezoid_weights(nt)
