@@ -140,6 +140,12 @@ int reg_apply_proj(reg_ctx* ctx, const float* b, float* out);
  * inverse vector Laplacian for the shear model. */
 int reg_apply_precond(reg_ctx* ctx, const float* r, float* out);
 
+/* Square root of the preconditioner, Q = (beta_v A')^(1/2) with A'(0) = 1
+ * (App. E.2): out = Q x (inverse = 0) or Q^-1 x (inverse != 0), per Fourier
+ * mode, on a velocity field (2 n1 n2 floats, device).  reg_solve iterates on
+ * y = Q v for the H2 seminorm. */
+int reg_apply_precond_sqrt(reg_ctx* ctx, const float* x, float* out, int inverse);
+
 /* ---- rows a5-a7: state solve, objective, adjoint, reduced gradient ---- */
 
 /* Forward state solve (Eq. (e:state-eq-elim)) and objective J[v]
@@ -204,8 +210,8 @@ typedef struct {
  * pairs on its own CUDA stream with per-grid-size contexts it creates once
  * and re-parameterizes per pair (reg_set_params), so the pairs' kernels run
  * concurrently.  Pairs are taken largest grid first.  Before the first pair
- * of a grid size is solved, reg_autotune picks that size's FFT tiles (once
- * per process and device).  Every pair's result is identical to reg_solve on
+ * of a grid size is solved, reg_autotune picks that size's FFT tiles for
+ * min(nworkers, 8) concurrent solves (once per process and device).  Every pair's result is identical to reg_solve on
  * that pair alone with a context created after that tuning.  Synchronous.  Returns REG_OK if
  * every pair returned REG_OK, else the first failing pair's status (each
  * item's own status is in item.status); REG_ERR_ARG for invalid arguments. */
@@ -222,28 +228,35 @@ void reg_executor_destroy(reg_executor* ex);
 
 /* ---- row a15: autotuner of the FFT tiles ---- */
 
-/* Times one Gauss-Newton Hessian matvec (Algorithm 2's inner product with H,
- * two transport solves of nt steps) on an n1 x n2 grid for every valid pair
- * (rows per row-kernel CTA R, spectrum columns per column-kernel CTA C) on the
- * current device (zero images and velocity, a private stream) and records
- * the fastest pair in a process-wide table; contexts created afterwards on
- * this device and grid use it (existing contexts keep their tiles).  Valid:
- * R a multiple of 4 dividing n1, 32 <= R n2 / 8 <= 512 threads; C a power of
- * two >= 2 dividing n2 / 2, 32 <= C n1 / 8 <= 256 threads; at most 227 KB of
- * shared memory.  A grid already in the table is not re-measured unless
- * force != 0 (then *ms_per_matvec < 0).  Outputs are host pointers, each
- * nullable.  Synchronous.  REG_ERR_ARG for a grid outside powers of two in
- * [16, 1024] or nt outside [1, 4096]. */
-int reg_autotune(reg_grid grid, int nt, int force, int* rows_per_cta, int* cols_per_cta, double* ms_per_matvec);
+/* Times the Gauss-Newton Hessian matvec (Algorithm 2's product with H, two
+ * transport solves of nt steps) on an n1 x n2 grid with `concurrency` solves
+ * running at once on their own streams (1: latency of one solve; > 1: the
+ * throughput of that many, as in the batch executor), for every valid tile
+ * choice (R rows per row-kernel CTA, C spectrum columns per column-kernel
+ * CTA, P = 1 if the RK2 row kernels prefetch their operands before waiting on
+ * the preceding kernel), on the current device with zero images and velocity
+ * and private streams, and records the fastest in a process-wide table;
+ * contexts created afterwards on this device and grid use it (existing
+ * contexts keep theirs).  Valid: R a multiple of 4 dividing n1,
+ * 32 <= R n2 / 8 <= 512 threads; C a power of two >= 2 dividing n2 / 2,
+ * 32 <= C n1 / 8 <= 256 threads; at most 227 KB of shared memory; P = 1 only
+ * for n2 <= 512.  A grid already in the table is not re-measured unless
+ * force != 0 (then *ms_per_matvec < 0); *ms_per_matvec is per matvec of the
+ * whole group.  Outputs are host pointers, each nullable.  Synchronous.
+ * REG_ERR_ARG for a grid outside powers of two in [16, 1024], nt outside
+ * [1, 4096] or concurrency outside [1, 16]. */
+int reg_autotune(reg_grid grid, int nt, int concurrency, int force, int* rows_per_cta, int* cols_per_cta,
+                 int* prefetch, double* ms_per_matvec);
 
-/* The tiles a context launches with (tuned, else the default rule:
- * the smallest R, C with at least 64 threads). */
-int reg_tile_config(reg_ctx* ctx, int* rows_per_cta, int* cols_per_cta);
+/* The tiles a context launches with (tuned, else the default rule: the
+ * smallest R, C with at least 64 threads, P = 1 for n2 <= 512). */
+int reg_tile_config(reg_ctx* ctx, int* rows_per_cta, int* cols_per_cta, int* prefetch);
 
-/* Sets a context's tiles (validity as for reg_autotune; 0, 0 restores the
- * default rule).  Results do not depend on the tiles except for the summation
- * order of FP64 reductions (objective, norms).  REG_ERR_ARG for invalid tiles. */
-int reg_set_tiles(reg_ctx* ctx, int rows_per_cta, int cols_per_cta);
+/* Sets a context's tiles (validity as for reg_autotune; R = C = 0 restores
+ * the default rule).  Results do not depend on the tiles except for the
+ * summation order of FP64 reductions (objective, norms).  REG_ERR_ARG for
+ * invalid tiles. */
+int reg_set_tiles(reg_ctx* ctx, int rows_per_cta, int cols_per_cta, int prefetch);
 
 /* ---- row a14: deformation gradient (Eq. (e:def-grad)) ---- */
 

@@ -62,6 +62,7 @@ _SIGS = {
     "reg_apply_reg": ([_P, _P, _P], _I),
     "reg_apply_proj": ([_P, _P, _P], _I),
     "reg_apply_precond": ([_P, _P, _P], _I),
+    "reg_apply_precond_sqrt": ([_P, _P, _P, _I], _I),
     "reg_objective": ([_P, _P, _P, ctypes.POINTER(_D)], _I),
     "reg_gradient": ([_P, _P, _P, ctypes.POINTER(_D)], _I),
     "reg_hessian_matvec": ([_P, _P, _P], _I),
@@ -78,9 +79,10 @@ _SIGS = {
     "reg_executor_create": ([_I, ctypes.POINTER(_P)], _I),
     "reg_executor_solve": ([_P, ctypes.POINTER(reg_batch_item), _I, ctypes.POINTER(reg_solve_opts)], _I),
     "reg_executor_destroy": ([_P], None),
-    "reg_autotune": ([reg_grid, _I, _I, ctypes.POINTER(_I), ctypes.POINTER(_I), ctypes.POINTER(_D)], _I),
-    "reg_tile_config": ([_P, ctypes.POINTER(_I), ctypes.POINTER(_I)], _I),
-    "reg_set_tiles": ([_P, _I, _I], _I),
+    "reg_autotune": ([reg_grid, _I, _I, _I, ctypes.POINTER(_I), ctypes.POINTER(_I), ctypes.POINTER(_I),
+                      ctypes.POINTER(_D)], _I),
+    "reg_tile_config": ([_P, ctypes.POINTER(_I), ctypes.POINTER(_I), ctypes.POINTER(_I)], _I),
+    "reg_set_tiles": ([_P, _I, _I, _I], _I),
     "reg_net_create": ([_I, _I, _I, ctypes.POINTER(_P)], _I),
     "reg_net_destroy": ([_P], None),
     "reg_net_num_params": ([_P], ctypes.c_longlong),
@@ -152,13 +154,14 @@ def spectral_grad_static(f, grad_f, stream=None):
                                           handle))
 
 
-def autotune(n1, n2, nt=4, force=False):
-    """FFT tiles for an n1 x n2 grid (reg_autotune): (rows per row CTA, columns per
-    column CTA, ms per matvec of the winner, or -1 if the grid was already tuned)."""
-    R, C, ms = ctypes.c_int(), ctypes.c_int(), ctypes.c_double()
-    _check(lib().reg_autotune(reg_grid(n1, n2), nt, 1 if force else 0, ctypes.byref(R), ctypes.byref(C),
-                              ctypes.byref(ms)))
-    return R.value, C.value, ms.value
+def autotune(n1, n2, nt=4, concurrency=1, force=False):
+    """FFT tiles for an n1 x n2 grid (reg_autotune) timed with `concurrency` solves at once:
+    (rows per row CTA, columns per column CTA, prefetch flag, ms per matvec of the winner,
+    or -1 if the grid was already tuned)."""
+    R, C, P, ms = ctypes.c_int(), ctypes.c_int(), ctypes.c_int(), ctypes.c_double()
+    _check(lib().reg_autotune(reg_grid(n1, n2), nt, concurrency, 1 if force else 0, ctypes.byref(R), ctypes.byref(C),
+                              ctypes.byref(P), ctypes.byref(ms)))
+    return R.value, C.value, P.value, ms.value
 
 
 def _batch_items(pairs):
@@ -348,6 +351,9 @@ class Context:
     def apply_precond(self, r, out):
         _check(lib().reg_apply_precond(self.h, _ptr(r, 2 * self.N), _ptr(out, 2 * self.N)))
 
+    def apply_precond_sqrt(self, x, out, inverse=False):
+        _check(lib().reg_apply_precond_sqrt(self.h, _ptr(x, 2 * self.N), _ptr(out, 2 * self.N), 1 if inverse else 0))
+
     def objective(self, v, m1=None):
         J = ctypes.c_double()
         _check(lib().reg_objective(self.h, _ptr(v, 2 * self.N), _ptr(m1, self.N), ctypes.byref(J)))
@@ -424,11 +430,12 @@ class Context:
         return lib().reg_launch_count(self.h)
 
     def tile_config(self):
-        """(rows per row-kernel CTA, spectrum columns per column-kernel CTA) of this context."""
-        R, C = ctypes.c_int(), ctypes.c_int()
-        _check(lib().reg_tile_config(self.h, ctypes.byref(R), ctypes.byref(C)))
-        return R.value, C.value
+        """(rows per row-kernel CTA, spectrum columns per column-kernel CTA, prefetch flag) of this context."""
+        R, C, P = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+        _check(lib().reg_tile_config(self.h, ctypes.byref(R), ctypes.byref(C), ctypes.byref(P)))
+        return R.value, C.value, P.value
 
-    def set_tiles(self, R, C):
-        """Launch this context's row / column kernels with R rows and C spectrum columns per CTA (0, 0: default)."""
-        _check(lib().reg_set_tiles(self.h, R, C))
+    def set_tiles(self, R, C, P=0):
+        """Launch with R rows per row-kernel CTA, C spectrum columns per column-kernel CTA and
+        operand prefetch P in the RK2 row kernels (R = C = 0: default rule)."""
+        _check(lib().reg_set_tiles(self.h, R, C, P))

@@ -93,7 +93,7 @@ extern "C" void reg_destroy(reg_ctx* c) {
     if (!c) return;
     float** fl[] = {&c->mT, &c->mR, &c->v_lin, &c->E_lin, &c->eta_lin, &c->w0, &c->w1, &c->w2, &c->w3,
                     &c->bvec, &c->vtmp, &c->vtmp2, &c->gtmp, &c->T3, &c->g, &c->r, &c->z, &c->s, &c->Hs,
-                    &c->vt, &c->vtrial, &c->F, &c->Fs, &c->gF, &c->gv};
+                    &c->vt, &c->vtrial, &c->F, &c->Fs, &c->gF, &c->gv, &c->ybuf, &c->ytrial, &c->vtil};
     for (auto p : fl) cudaFree(*p);
     for (int i = 0; i < 6; ++i) cudaFree(c->S[i]);
     free_hist(c);
@@ -127,6 +127,7 @@ static void set_params(reg_ctx* c, int nt, int regnorm, double beta, double gamm
     c->shear_model = shear != 0.0;
     c->nu = (1.0 + shear) / (1.0 - shear);
     c->pmode = (gamma == 0.0) ? PROJ_IDENTITY : (std::isinf(gamma) ? PROJ_LERAY : PROJ_MASS);
+    c->ypath = regnorm == REG_H2 && !c->shear_model;
     c->have_lin = false;
 }
 
@@ -148,12 +149,13 @@ extern "C" int reg_create(reg_grid grid, int nt, int regnorm, double beta, doubl
     set_params(c, nt, regnorm, beta, gamma, shear);
     c->stream = 0;
     c->launches = 0;
-    c->tileR = c->tileC = 0;
+    c->tileR = c->tileC = c->tileP = 0;
     {
-        int dev = 0, R, C;
-        if (cudaGetDevice(&dev) == cudaSuccess && tuned_tiles(dev, c->n1, c->n2, &R, &C)) {
+        int dev = 0, R, C, P;
+        if (cudaGetDevice(&dev) == cudaSuccess && tuned_tiles(dev, c->n1, c->n2, &R, &C, &P)) {
             c->tileR = R;
             c->tileC = C;
+            c->tileP = P;
         }
     }
     c->pdl = true;
@@ -169,6 +171,7 @@ extern "C" int reg_create(reg_grid grid, int nt, int regnorm, double beta, doubl
     A(&c->bvec, 2 * N); A(&c->vtmp, 2 * N); A(&c->vtmp2, 2 * N); A(&c->gtmp, 4 * N); A(&c->T3, 3 * N);
     A(&c->g, 2 * N); A(&c->r, 2 * N); A(&c->z, 2 * N); A(&c->s, 2 * N); A(&c->Hs, 2 * N);
     A(&c->vt, 2 * N); A(&c->vtrial, 2 * N);
+    A(&c->ybuf, 2 * N); A(&c->ytrial, 2 * N); A(&c->vtil, 2 * N);
     A(&c->F, 4 * N); A(&c->Fs, 4 * N); A(&c->gF, 8 * N); A(&c->gv, 4 * N);
     for (int i = 0; i < 6 && ok; ++i)
         if (cudaMalloc(&c->S[i], sizeof(float2) * N / 2) != cudaSuccess) ok = false;
@@ -207,18 +210,20 @@ extern "C" int reg_set_params(reg_ctx* c, int nt, int regnorm, double beta, doub
     return alloc_hist(c, nt);
 }
 
-extern "C" int reg_set_tiles(reg_ctx* c, int rows_per_cta, int cols_per_cta) {
+extern "C" int reg_set_tiles(reg_ctx* c, int rows_per_cta, int cols_per_cta, int prefetch) {
     if (!c) return reg_fail(REG_ERR_ARG, "ctx is NULL");
     if (rows_per_cta == 0 && cols_per_cta == 0) {
         if (c->tileR != 0 || c->tileC != 0) clear_graphs(c);
-        c->tileR = c->tileC = 0;
+        c->tileR = c->tileC = c->tileP = 0;
         return REG_OK;
     }
-    if (!tiles_valid(c->n1, c->n2, rows_per_cta, cols_per_cta))
+    if (!tiles_valid(c->n1, c->n2, rows_per_cta, cols_per_cta, prefetch))
         return reg_fail(REG_ERR_ARG, "tiles outside the launch limits of this grid");
-    if (rows_per_cta != c->tileR || cols_per_cta != c->tileC) clear_graphs(c);  // captures bake in launch shapes
+    if (rows_per_cta != c->tileR || cols_per_cta != c->tileC || prefetch != c->tileP)
+        clear_graphs(c);  // captures bake in launch shapes and kernels
     c->tileR = rows_per_cta;
     c->tileC = cols_per_cta;
+    c->tileP = prefetch;
     return REG_OK;
 }
 
@@ -235,7 +240,10 @@ extern "C" int reg_set_stream(reg_ctx* c, void* stream) {
 // Sequences run directly on the legacy default stream (it cannot be
 // captured) and while per-kernel timing is on.
 // ---------------------------------------------------------------------------
-enum GraphKind { GK_OBJECTIVE = 1, GK_GRADIENT = 2, GK_MATVEC = 3, GK_PCG_ITER = 4, GK_PCG_INIT = 5, GK_DETGRAD = 6 };
+enum GraphKind {
+    GK_OBJECTIVE = 1, GK_GRADIENT = 2, GK_MATVEC = 3, GK_PCG_ITER = 4, GK_PCG_INIT = 5, GK_DETGRAD = 6,
+    GK_GRADIENT_Y = 7, GK_PCG_ITER_Y = 8, GK_PCG_INIT_Y = 9
+};
 
 template <typename F>
 static int run_seq(reg_ctx* c, int kind, const void* p0, const void* p1, int nt, F&& body) {
@@ -365,6 +373,25 @@ static void sp_assemble(reg_ctx* c, float coefA, const float* u, const float* b,
     launch_c2r_vec(c, c->S[4], c->S[5], out, out + c->N);
 }
 
+// ---- preconditioned coordinates y = Q v, Q^ = (beta_v A'^)^(1/2), A'(0) = 1 ----
+// out = Pi0 y + Q^-1 K b (the gradient, or with y = s and b = b~ the Hessian product, in y)
+static void sp_assemble_y(reg_ctx* c, const float* y, const float* b, float* out) {
+    launch_r2c_vec(c, y, y + c->N, c->S[0], c->S[1]);
+    launch_r2c_vec(c, b, b + c->N, c->S[2], c->S[3]);
+    const float2* in[4] = {c->S[0], c->S[1], c->S[2], c->S[3]};
+    float2* o[2] = {c->S[4], c->S[5]};
+    launch_col(c, OP_ASSEMBLE_Y, in, o, spec_params(c, 0.f), nullptr);
+    launch_c2r_vec(c, c->S[4], c->S[5], out, out + c->N);
+}
+
+// device slot <- h1 h2 sum |Q x|^2 = ||Q x||^2 (the v-space norm of a y-space gradient / residual)
+static void sp_qnorm(reg_ctx* c, const float* x, int slot) {
+    launch_r2c_vec(c, x, x + c->N, c->S[0], c->S[1]);
+    const float2* in[2] = {c->S[0], c->S[1]};
+    launch_col(c, OP_QNORM, in, nullptr, spec_params(c, 0.f), c->d_part);
+    launch_finalize(c, c->d_part, col_blocks(c), c->d_scal + slot, 1.0, 0, 0);
+}
+
 // grad of a vector field: gv planes (d1 u1, d2 u1, d1 u2, d2 u2)
 static void sp_grad_vec(reg_ctx* c, const float* u, float* gv) {
     sp_grad(c, u, gv);
@@ -473,7 +500,11 @@ static void inc_state_solve(reg_ctx* c, const float* v, const float* vt, int nt)
         }
         a.uj = (j > 0) ? mj : nullptr; a.us = nullptr; a.v = v; a.gm = gmh(c, j); a.vt = vt;
         a.u_out = ms; a.grad_out = nullptr; a.S_out = c->S[0]; a.h = h; a.stage = 1;
+        // the first launch of the solve: v~ may come from the launch just before (Q^-1 s in
+        // preconditioned coordinates, or a caller's kernel), so it is read after the wait
+        a.late = (j == 0) ? 1 : 0;
         launch_row_adv(c, a);
+        a.late = 0;
         launch_col(c, OP_GRAD1, in, G, P, nullptr);
         a.G1 = c->S[1]; a.Sd2 = c->S[0];
         a.us = ms; a.gm = gmh(c, j + 1); a.u_out = mj; a.stage = 2;
@@ -494,18 +525,30 @@ static int read_scalars(reg_ctx* c) {
 static int ensure_nt(reg_ctx* c, int nt) { return alloc_hist(c, nt); }
 
 // forward solve + J (device slots SL_JDATA, SL_JREG)
-static void objective_launches(reg_ctx* c, const float* v, int nt) {
+// Regularization energy from y = Q v (reg_solve in preconditioned coordinates)
+static void reg_energy_y(reg_ctx* c, const float* y) {
+    launch_r2c_vec(c, y, y + c->N, c->S[0], c->S[1]);
+    const float2* in[2] = {c->S[0], c->S[1]};
+    launch_col(c, OP_ENERGY_Y, in, nullptr, spec_params(c, 0.f), c->d_part);
+    launch_finalize(c, c->d_part, col_blocks(c), c->d_scal + SL_JREG, 1.0, 0, 0);
+}
+
+// y != nullptr: v = Q^-1 y and the regularization energy is taken from y
+static void objective_launches(reg_ctx* c, const float* v, int nt, const float* y = nullptr) {
     state_solve(c, v, nt);
     // J_data = 0.5 ||m_R - m_1||^2
     launch_axpby(c, c->N, 1.f, c->mR, -1.f, mh(c, nt), -1, -1, c->w1);
     int np = launch_dot_partial(c, c->w1, c->w1, c->N, c->d_part);
     launch_finalize(c, c->d_part, np, c->d_scal + SL_JDATA, 0.5 * hh(c), 0, 0);
-    reg_energy(c, v);
+    if (y)
+        reg_energy_y(c, y);
+    else
+        reg_energy(c, v);
 }
 
-static int objective_dev(reg_ctx* c, const float* v, int nt) {
+static int objective_dev(reg_ctx* c, const float* v, int nt, const float* y = nullptr) {
     RET(ensure_nt(c, nt));
-    return run_seq(c, GK_OBJECTIVE, v, nullptr, nt, [&] { objective_launches(c, v, nt); });
+    return run_seq(c, GK_OBJECTIVE, v, y, nt, [&] { objective_launches(c, v, nt, y); });
 }
 
 static void gradient_launches(reg_ctx* c, const float* v, float* g, int nt) {
@@ -527,6 +570,29 @@ static int gradient_dev(reg_ctx* c, const float* v, float* g, int nt) {
     c->nt_lin = nt;
     c->have_lin = true;
     return REG_OK;
+}
+
+// Gradient in preconditioned coordinates: g_y = Q^-1 g_v = Pi0 y + Q^-1 K b, at v = Q^-1 y
+static int gradient_dev_y(reg_ctx* c, const float* v, const float* y, float* gy, int nt) {
+    RET(objective_dev(c, v, nt, y));
+    RET(run_seq(c, GK_GRADIENT_Y, v, y, nt, [&] {  // gy is always c->g
+        adjoint_solve(c, v, nt, c->mR, 1.f, mh(c, nt), -1.f, c->bvec, nullptr);
+        sp_assemble_y(c, y, c->bvec, gy);
+        if (v != c->v_lin)
+            cudaMemcpyAsync(c->v_lin, v, sizeof(float) * 2 * c->N, cudaMemcpyDeviceToDevice, c->stream);
+    }));
+    c->nt_lin = nt;
+    c->have_lin = true;
+    return REG_OK;
+}
+
+// Hessian product in preconditioned coordinates: H_y s = Q^-1 H_v Q^-1 s = Pi0 s + Q^-1 K b~(v~ = Q^-1 s)
+static void matvec_launches_y(reg_ctx* c, const float* s, float* Hs) {
+    const int nt = c->nt_lin;
+    sp_vec(c, OP_QINV, 0.f, s, c->vtil);
+    inc_state_solve(c, c->v_lin, c->vtil, nt);
+    adjoint_solve(c, c->v_lin, nt, nullptr, 0.f, c->w3, -1.f, c->bvec, nullptr);
+    sp_assemble_y(c, s, c->bvec, Hs);
 }
 
 static void matvec_launches(reg_ctx* c, const float* vt, float* Hvt) {
@@ -600,6 +666,14 @@ extern "C" int reg_apply_proj(reg_ctx* c, const float* b, float* out) {
     CTX_CHECK(c);
     RET(check_ptr(b, "b")); RET(check_ptr(out, "out"));
     sp_vec(c, OP_PROJ, 0.f, b, out);
+    CKL();
+    return REG_OK;
+}
+
+extern "C" int reg_apply_precond_sqrt(reg_ctx* c, const float* x, float* out, int inverse) {
+    CTX_CHECK(c);
+    RET(check_ptr(x, "x")); RET(check_ptr(out, "out"));
+    sp_vec(c, inverse ? OP_QINV : OP_QMUL, 0.f, x, out);
     CKL();
     return REG_OK;
 }
@@ -692,29 +766,49 @@ static int nt_for(reg_ctx* c, const float* v, const reg_solve_opts& o, double* c
 // for the curvature check and the stop test (Algorithm 2's break).  The
 // update kernel does nothing when <s, Hs> <= 0, so vt and r keep their values
 // from before that iteration.
+//
+// In preconditioned coordinates (c->ypath) the same iteration is CG on
+// H_y = Q^-1 H Q^-1 without a preconditioner (z = r): its iterates are Q times
+// those of PCG with P = Q^2 = beta_v A', and the stop test uses the v-space
+// residual norm ||Q r_y|| = ||r_v||.
 static int pcg_dev(reg_ctx* c, double gnorm, double eta, int maxit, int* hit_max, int* status) {
     const long long n2N = 2 * (long long)c->N;
     const double scale = hh(c);
+    const bool yp = c->ypath;
     *status = REG_OK;
-    RET(run_seq(c, GK_PCG_INIT, nullptr, nullptr, c->nt_lin, [&] {
+    RET(run_seq(c, yp ? GK_PCG_INIT_Y : GK_PCG_INIT, nullptr, nullptr, c->nt_lin, [&] {
         launch_fill(c, n2N, c->vt, 0.f);
         launch_axpby(c, n2N, -1.f, c->g, 0.f, c->r, -1, -1, c->r);  // r = -g
-        precond_dev(c, c->r, c->z);
-        cudaMemcpyAsync(c->s, c->z, sizeof(float) * n2N, cudaMemcpyDeviceToDevice, c->stream);
-        dot_dev(c, c->r, c->z, SL_RZ);
+        if (yp) {
+            cudaMemcpyAsync(c->s, c->r, sizeof(float) * n2N, cudaMemcpyDeviceToDevice, c->stream);
+            dot_dev(c, c->r, c->r, SL_RZ);
+        } else {
+            precond_dev(c, c->r, c->z);
+            cudaMemcpyAsync(c->s, c->z, sizeof(float) * n2N, cudaMemcpyDeviceToDevice, c->stream);
+            dot_dev(c, c->r, c->z, SL_RZ);
+        }
     }));
     int it = 0;
     *hit_max = 1;
     if (!c->have_lin) return reg_fail(REG_ERR_STATE, "PCG without a linearization point");
     for (int l = 0; l < maxit; ++l) {
-        int st = run_seq(c, GK_PCG_ITER, nullptr, nullptr, c->nt_lin, [&] {
-            matvec_launches(c, c->s, c->Hs);
+        int st = run_seq(c, yp ? GK_PCG_ITER_Y : GK_PCG_ITER, nullptr, nullptr, c->nt_lin, [&] {
+            if (yp)
+                matvec_launches_y(c, c->s, c->Hs);
+            else
+                matvec_launches(c, c->s, c->Hs);
             dot_dev(c, c->s, c->Hs, SL_SHS);
             int np = launch_pcg_update(c, n2N, c->vt, c->s, c->r, c->Hs, c->d_part);
-            launch_finalize(c, c->d_part, np, c->d_scal + SL_RNORM2, scale, 0, 0);
-            precond_dev(c, c->r, c->z);
-            dot_dev(c, c->z, c->r, SL_RZNEW);
-            launch_pcg_dir(c, n2N, c->z, c->s);
+            if (yp) {
+                sp_qnorm(c, c->r, SL_RNORM2);
+                dot_dev(c, c->r, c->r, SL_RZNEW);
+                launch_pcg_dir(c, n2N, c->r, c->s);
+            } else {
+                launch_finalize(c, c->d_part, np, c->d_scal + SL_RNORM2, scale, 0, 0);
+                precond_dev(c, c->r, c->z);
+                dot_dev(c, c->z, c->r, SL_RZNEW);
+                launch_pcg_dir(c, n2N, c->z, c->s);
+            }
             cudaMemcpyAsync(c->d_scal + SL_RZ, c->d_scal + SL_RZNEW, sizeof(double), cudaMemcpyDeviceToDevice,
                             c->stream);
         });
@@ -727,7 +821,12 @@ static int pcg_dev(reg_ctx* c, double gnorm, double eta, int maxit, int* hit_max
             // non-positive curvature: the update kernel left vt and r unchanged; in the first
             // iteration the step is the first direction s_0 = P r_0 (the oracle's choice)
             *hit_max = 0;
-            if (it == 1) precond_dev(c, c->r, c->vt);
+            if (it == 1) {
+                if (yp)
+                    cudaMemcpyAsync(c->vt, c->r, sizeof(float) * n2N, cudaMemcpyDeviceToDevice, c->stream);
+                else
+                    precond_dev(c, c->r, c->vt);
+            }
             break;
         }
         const double rn = std::sqrt(c->h_scal[SL_RNORM2]);
@@ -754,9 +853,33 @@ extern "C" int reg_solve(reg_ctx* c, float* v, const reg_solve_opts* opts, reg_s
     int n_pde = 0;
     double gref;
     if (!o.warm_start) launch_fill(c, n2N, v, 0.f);
+    // Quadratic H2 regularization iterates on y = Q v (Q^2 = beta_v A' is the
+    // preconditioner): the FP32 rounding of v, amplified by beta_v |k|^4 in the
+    // reduced gradient, would otherwise put a floor of about u beta_v max|k|^4 ||v||
+    // under ||g|| (above 1e-2 ||g(0)|| from 128^2 on); in y the regularization
+    // term is the identity and every other operator applied is smoothing.
+    const bool yp = c->ypath;
+    float* y = c->ybuf;
+    if (yp) {
+        if (o.warm_start) {
+            sp_vec(c, OP_QMUL, 0.f, v, y);
+            sp_vec(c, OP_QINV, 0.f, y, v);
+        } else {
+            launch_fill(c, n2N, y, 0.f);
+        }
+    }
     double cfl = 0.0;
     int nt = nt_for(c, v, o, &cfl);
     if (nt < 0) return reg_fail(REG_ERR_CUDA, "scalar readback failed");
+    auto grad_at = [&](const float* vv, const float* yy) {
+        return yp ? gradient_dev_y(c, vv, yy, c->g, nt) : gradient_dev(c, vv, c->g, nt);
+    };
+    auto gnorm2_to_slot = [&]() {
+        if (yp)
+            sp_qnorm(c, c->g, SL_GNORM2);  // ||g_v|| = ||Q g_y||
+        else
+            dot_dev(c, c->g, c->g, SL_GNORM2);
+    };
     if (o.warm_start) {
         launch_fill(c, n2N, c->vtrial, 0.f);
         RET(gradient_dev(c, c->vtrial, c->g, c->nt));
@@ -765,9 +888,9 @@ extern "C" int reg_solve(reg_ctx* c, float* v, const reg_solve_opts* opts, reg_s
         RET(read_scalars(c));
         gref = std::sqrt(c->h_scal[SL_GNORM2]);
     }
-    RET(gradient_dev(c, v, c->g, nt));
+    RET(grad_at(v, y));
     n_pde += 2;
-    dot_dev(c, c->g, c->g, SL_GNORM2);
+    gnorm2_to_slot();
     RET(read_scalars(c));
     double J = c->h_scal[SL_JDATA] + c->h_scal[SL_JREG];
     double gnorm = std::sqrt(c->h_scal[SL_GNORM2]);
@@ -793,7 +916,11 @@ extern "C" int reg_solve(reg_ctx* c, float* v, const reg_solve_opts* opts, reg_s
         RET(read_scalars(c));
         double gv = c->h_scal[SL_GV];
         if (!(gv < 0.0)) {
-            precond_dev(c, c->g, c->vt);
+            // preconditioned steepest descent: -P^-1 g_v, i.e. -g_y in y
+            if (yp)
+                cudaMemcpyAsync(c->vt, c->g, vb, cudaMemcpyDeviceToDevice, c->stream);
+            else
+                precond_dev(c, c->g, c->vt);
             launch_axpby(c, n2N, 0.f, c->vt, -1.f, c->vt, -1, -1, c->vt);
             dot_dev(c, c->g, c->vt, SL_GV);
             RET(read_scalars(c));
@@ -803,8 +930,14 @@ extern "C" int reg_solve(reg_ctx* c, float* v, const reg_solve_opts* opts, reg_s
         bool accepted = false;
         double Jt = J;
         for (int ls = 0; ls < o.max_ls; ++ls) {
-            launch_axpby(c, n2N, (float)alpha, c->vt, 1.f, v, -1, -1, c->vtrial);
-            RET(objective_dev(c, c->vtrial, nt));
+            if (yp) {
+                launch_axpby(c, n2N, (float)alpha, c->vt, 1.f, y, -1, -1, c->ytrial);
+                sp_vec(c, OP_QINV, 0.f, c->ytrial, c->vtrial);
+                RET(objective_dev(c, c->vtrial, nt, c->ytrial));
+            } else {
+                launch_axpby(c, n2N, (float)alpha, c->vt, 1.f, v, -1, -1, c->vtrial);
+                RET(objective_dev(c, c->vtrial, nt));
+            }
             n_pde += 1;
             st.n_ls += 1;
             RET(read_scalars(c));
@@ -815,17 +948,18 @@ extern "C" int reg_solve(reg_ctx* c, float* v, const reg_solve_opts* opts, reg_s
         if (!accepted) {
             status = REG_ERR_LINESEARCH;
             // restore the linearization data of the current iterate for a consistent return
-            RET(gradient_dev(c, v, c->g, nt));
+            RET(grad_at(v, y));
             n_pde += 2;
             break;
         }
         CK(cudaMemcpyAsync(v, c->vtrial, vb, cudaMemcpyDeviceToDevice, c->stream));
+        if (yp) CK(cudaMemcpyAsync(y, c->ytrial, vb, cudaMemcpyDeviceToDevice, c->stream));
         ++k;
         nt = nt_for(c, v, o, &cfl);
         if (nt < 0) return reg_fail(REG_ERR_CUDA, "scalar readback failed");
-        RET(gradient_dev(c, v, c->g, nt));
+        RET(grad_at(v, y));
         n_pde += 2;
-        dot_dev(c, c->g, c->g, SL_GNORM2);
+        gnorm2_to_slot();
         RET(read_scalars(c));
         J = c->h_scal[SL_JDATA] + c->h_scal[SL_JREG];
         gnorm = std::sqrt(c->h_scal[SL_GNORM2]);

@@ -20,7 +20,13 @@ enum SpecOp {
     OP_DIVT_PROJ = 7, // 5 in -> 2 out: P_L(coefA * div(T) + b), T = (T11, T12, T22)
     OP_GRAD1 = 8,     // 1 in -> 1 out: i k1~ x (d2 is diagonal in the row spectra; see AdvArgs::Sd2)
     OP_DIV1 = 9,      // in[0] transformed, in[1] raw -> 1 out: i k1~ x0 + (i k2~ / n2) x1 (x1 not transformed)
-    OP_SMOOTH_PROJ = 10  // 2 in -> 2 out: exp(-coefA |k|^2) P_L x (Gaussian low-pass, then Leray)
+    OP_SMOOTH_PROJ = 10, // 2 in -> 2 out: exp(-coefA |k|^2) P_L x (Gaussian low-pass, then Leray)
+    // Preconditioned coordinates y = Q v, Q^ = (beta_v A'^)^(1/2), A'(0) = 1 (reg_solve, quadratic regularization):
+    OP_QINV = 11,        // 2 in -> 2 out: Q^-1 x
+    OP_QMUL = 12,        // 2 in -> 2 out: Q x
+    OP_ASSEMBLE_Y = 13,  // 4 in -> 2 out: Pi0 x01 + Q^-1 K^ x23 (Pi0 drops k = 0): gradient / Hessian in y
+    OP_QNORM = 14,       // 2 in -> 0 out: FP64 sum of |Q x|^2 (the v-norm of a y-space gradient or residual)
+    OP_ENERGY_Y = 15     // 2 in -> 0 out: FP64 regularization energy of v = Q^-1 x from x
 };
 
 // Projection modes (Eq. (e:project-body-force)):
@@ -89,6 +95,9 @@ struct reg_ctx {
     float *bvec, *vtmp, *vtmp2, *gtmp, *T3;  // T3: 3 planes
     // PCG / solve workspace (2N each)
     float *g, *r, *z, *s, *Hs, *vt, *vtrial;
+    // preconditioned coordinates y = Q v of reg_solve (2N each): iterate, trial iterate, Q^-1 of a direction
+    float *ybuf, *ytrial, *vtil;
+    bool ypath;      // reg_solve iterates on y (quadratic H2 regularization, see reg_solve)
     // det F workspace
     float *F, *Fs, *gF, *gv;  // 4N, 4N, 8N, 4N
 
@@ -100,6 +109,7 @@ struct reg_ctx {
     float2* tw;      // twiddle table (REG_TW_N entries)
 
     int tileR, tileC;  // rows per row-kernel CTA, spectrum columns per column-kernel CTA (0: default)
+    int tileP;         // 1: RK2 row kernels prefetch their operands (used when tileR > 0)
 
     long long launches;
     bool pdl;         // launch with programmatic dependent launch (default on)
@@ -115,10 +125,10 @@ struct reg_ctx {
 };
 
 // ---- FFT tile choices (kernels.cu: defaults and limits; tune.cu: autotuner table) ----
-void default_tiles(int n1, int n2, int* R, int* C);
-bool tiles_valid(int n1, int n2, int R, int C);
-// tuned (R, C) for this device and grid, if reg_autotune has measured it
-bool tuned_tiles(int dev, int n1, int n2, int* R, int* C);
+void default_tiles(int n1, int n2, int* R, int* C, int* P);
+bool tiles_valid(int n1, int n2, int R, int C, int P);
+// tuned (R, C, P) for this device and grid, if reg_autotune has measured it
+bool tuned_tiles(int dev, int n1, int n2, int* R, int* C, int* P);
 
 // ---- launchers (kernels.cu); all asynchronous on ctx->stream ----
 cudaError_t k_init_twiddles(reg_ctx* ctx);
@@ -142,6 +152,8 @@ struct AdvArgs {
     float2* S_out;          // nullable: packed spectrum of u_out
     float h;
     int stage;
+    int late;               // 1: load every operand after waiting on the preceding kernel (an operand
+                            // may have been written by the launch just before this one)
 };
 void launch_row_adv(reg_ctx* ctx, const AdvArgs& a);
 

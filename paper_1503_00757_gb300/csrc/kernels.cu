@@ -141,12 +141,16 @@ __device__ double block_reduce(double v) {
 // Shared memory: region A (R*L float2: staging) + region X (2*R*L float2:
 // FFT exchange buffers, 2*L per FFT).
 // ---------------------------------------------------------------------------
-// Minimum resident CTAs per SM requested from the compiler for the RK2 row
-// kernels: rows of 1024 use 512-thread CTAs, and two of them per SM keep the
-// 256-CTA grid of a 1024 x 1024 field in one wave.
-template <int LOGL>
+// The RK2 row kernels come in two variants.  PRE = true loads the operands
+// written two or more launches back (u_j, u*, v, grad m, v~, lambda, b)
+// before waiting on the preceding column kernel, which overlaps those loads
+// with its tail but holds ~40 more registers per thread (one CTA of 512
+// threads per SM).  PRE = false loads them after the FFT and is compiled for
+// two CTAs of 512 threads per SM (64 registers), which is what concurrent
+// solves and 1024-point rows want.  The autotuner chooses per grid.
+template <bool PRE>
 struct RowBlocks {
-    static constexpr int value = LOGL >= 10 ? 2 : 1;
+    static constexpr int value = PRE ? 1 : 2;
 };
 
 template <int LOGL>
@@ -251,8 +255,8 @@ __global__ void __launch_bounds__(512) k_c2r(const float2* __restrict__ S1, cons
 // grad u_s arrives as packed spectra (G1, G2) from the column pass; the stage
 // result u_out leaves as its packed spectrum S_out for the next column pass.
 // ---------------------------------------------------------------------------
-template <int LOGL>
-__global__ void __launch_bounds__(512, RowBlocks<LOGL>::value) k_row_adv(AdvArgs a, int N, int R,
+template <int LOGL, bool PRE>
+__global__ void __launch_bounds__(512, RowBlocks<PRE>::value) k_row_adv(AdvArgs a, int N, int R,
                                                                            const float2* __restrict__ tw) {
     extern __shared__ __align__(16) float2 sm[];
     constexpr int L = 1 << LOGL, T = L >> 3, W = L >> 1;
@@ -264,10 +268,9 @@ __global__ void __launch_bounds__(512, RowBlocks<LOGL>::value) k_row_adv(AdvArgs
     const size_t rowbase = (size_t)(row0 + q) * L;
     // Operands written at least two launches earlier (u_j, u*, v, grad m, v~) are
     // loaded before waiting on the preceding column kernel; only G depends on it.
-    // u_j == nullptr stands for u_j = 0 (the incremental state at t = 0).  For
-    // the longest rows the operands are read after the FFT instead, which keeps
-    // the register count low enough for two CTAs per SM.
-    constexpr bool PRE = RowBlocks<LOGL>::value == 1;
+    // u_j == nullptr stands for u_j = 0 (the incremental state at t = 0).  With
+    // PRE = false the operands are read after the FFT instead, which keeps the
+    // register count low enough for two CTAs per SM.
     float pv1[8], pv2[8], puj[8], pus[8], psrc[8];
     auto load_ops = [&](int k) {
         const size_t idx = rowbase + t + k * T;
@@ -277,7 +280,8 @@ __global__ void __launch_bounds__(512, RowBlocks<LOGL>::value) k_row_adv(AdvArgs
         pus[k] = (a.stage == 2) ? a.us[idx] : 0.f;
         psrc[k] = a.gm ? -(a.vt[idx] * a.gm[idx] + a.vt[N + idx] * a.gm[N + idx]) : 0.f;
     };
-    if (PRE) {
+    const bool early = PRE && !a.late;
+    if (early) {
 #pragma unroll
         for (int k = 0; k < 8; ++k) load_ops(k);
     }
@@ -303,7 +307,7 @@ __global__ void __launch_bounds__(512, RowBlocks<LOGL>::value) k_row_adv(AdvArgs
     float out[8];
 #pragma unroll
     for (int k = 0; k < 8; ++k) {
-        if (!PRE) load_ops(k);
+        if (!early) load_ops(k);
         const size_t idx = rowbase + t + k * T;
         const float d1 = x[k].x, d2 = x[k].y;
         if (a.grad_out) {
@@ -365,8 +369,8 @@ __device__ __forceinline__ void flux_fft_store(float2 (&x)[8], int q, int t, int
     }
 }
 
-template <int LOGL>
-__global__ void __launch_bounds__(512, RowBlocks<LOGL>::value) k_row_adj(AdjArgs a, int N, int R,
+template <int LOGL, bool PRE>
+__global__ void __launch_bounds__(512, RowBlocks<PRE>::value) k_row_adj(AdjArgs a, int N, int R,
                                                                            const float2* __restrict__ tw) {
     extern __shared__ __align__(16) float2 sm[];
     constexpr int L = 1 << LOGL, T = L >> 3, W = L >> 1;
@@ -377,8 +381,7 @@ __global__ void __launch_bounds__(512, RowBlocks<LOGL>::value) k_row_adj(AdjArgs
     const size_t rowbase = (size_t)(row0 + q) * L;
     // Operands written at least two launches earlier (lam_j, lam*, v, b, grad m)
     // are loaded before waiting on the preceding column kernel, which writes D
-    // (after the FFT for the longest rows, as in k_row_adv).
-    constexpr bool PRE = RowBlocks<LOGL>::value == 1;
+    // (after the FFT with PRE = false, as in k_row_adv).
     float plj[8], pls[8], pv1[8], pv2[8], pb1[8], pb2[8], pg1[8], pg2[8];
     auto load_ops = [&](int k) {
         const size_t idx = rowbase + t + k * T;
@@ -520,6 +523,36 @@ __device__ __forceinline__ void spec_apply(const SpecParams& P, float k1o, float
         proj_sym(P, P.pmode, k1o, k2o, kk, K11, K12, K22);
         y[0] = cscale(cadd(cscale(x[0], K11), cscale(x[1], K12)), s);
         y[1] = cscale(cadd(cscale(x[0], K12), cscale(x[1], K22)), s);
+    } else if (OP == OP_QINV || OP == OP_QMUL) {
+        const float a = (kk == 0.f) ? 1.f : reg_sym(P.regnorm, kk);
+        const float q = sqrtf(P.beta_v * a);
+        const float c = (OP == OP_QINV) ? s / q : s * q;
+        y[0] = cscale(x[0], c);
+        y[1] = cscale(x[1], c);
+    } else if (OP == OP_ASSEMBLE_Y) {
+        float K11, K12, K22;
+        proj_sym(P, P.pmode, k1o, k2o, kk, K11, K12, K22);
+        const float a = (kk == 0.f) ? 1.f : reg_sym(P.regnorm, kk);
+        const float qi = s / sqrtf(P.beta_v * a);
+        const float c0 = (kk == 0.f) ? 0.f : s;
+        y[0] = cadd(cscale(x[0], c0), cscale(cadd(cscale(x[2], K11), cscale(x[3], K12)), qi));
+        y[1] = cadd(cscale(x[1], c0), cscale(cadd(cscale(x[2], K12), cscale(x[3], K22)), qi));
+    } else if (OP == OP_QNORM) {
+        const double a = (kk == 0.f) ? 1.0 : (double)reg_sym(P.regnorm, kk);
+        eacc += ew * (double)P.beta_v * a *
+                ((double)x[0].x * x[0].x + (double)x[0].y * x[0].y + (double)x[1].x * x[1].x + (double)x[1].y * x[1].y);
+    } else if (OP == OP_ENERGY_Y) {
+        // (beta_v / 2) <A v, v> = |Pi0 y|^2 / 2 ; mass-source term (beta_w / 2) (1 + |k|^2) |k~ . v^|^2 with v^ = y^ / Q^
+        double e = (kk == 0.f) ? 0.0
+                               : 0.5 * ((double)x[0].x * x[0].x + (double)x[0].y * x[0].y + (double)x[1].x * x[1].x +
+                                        (double)x[1].y * x[1].y);
+        if (P.ebw != 0.0) {
+            const double a = (kk == 0.f) ? 1.0 : (double)reg_sym(P.regnorm, kk);
+            const double dr = (double)k1o * x[0].x + (double)k2o * x[1].x;
+            const double di = (double)k1o * x[0].y + (double)k2o * x[1].y;
+            e += P.ebw * (1.0 + kk) * (dr * dr + di * di) / ((double)P.beta_v * a);
+        }
+        eacc += ew * e;
     } else if (OP == OP_SMOOTH_PROJ) {
         float K11, K12, K22;
         proj_sym(P, PROJ_LERAY, k1o, k2o, kk, K11, K12, K22);
@@ -633,7 +666,7 @@ __global__ void __launch_bounds__(256) k_col(ColArgs a, const float2* __restrict
 #pragma unroll
         for (int o = 0; o < NOUT; ++o) y[o][k] = yv[o];
     }
-    if (OP == OP_ENERGY) {
+    if (OP == OP_ENERGY || OP == OP_QNORM || OP == OP_ENERGY_Y) {
         const double s = block_reduce<0>(eacc);
         if (threadIdx.x == 0) a.part[blockIdx.x] = s * a.P.escale;
         return;
@@ -670,7 +703,8 @@ __global__ void __launch_bounds__(256) k_col(ColArgs a, const float2* __restrict
 // Default tile choices.  R rows per row CTA: a multiple of 4 with at least 64
 // threads (T = L/8 per row); C spectrum columns per column CTA: at least 2
 // (64-byte segments) and 64 threads.  reg_autotune may replace both per grid.
-void default_tiles(int n1, int n2, int* R_out, int* C_out) {
+void default_tiles(int n1, int n2, int* R_out, int* C_out, int* P_out) {
+    if (P_out) *P_out = n2 <= 512 ? 1 : 0;
     int R = 4;
     while (R * (n2 / 8) < 64 && R * 2 <= n1) R *= 2;
     const int W = n2 / 2;
@@ -683,8 +717,9 @@ void default_tiles(int n1, int n2, int* R_out, int* C_out) {
 // Launch limits of the row kernels (32 to 512 threads; 2 CTAs per SM for
 // 1024-point rows) and the column kernel (32 to 256 threads), and 227 KB of
 // shared memory (3 complex buffers of R rows or C columns).
-bool tiles_valid(int n1, int n2, int R, int C) {
+bool tiles_valid(int n1, int n2, int R, int C, int P) {
     const size_t smax = 227 * 1024;
+    if (P != 0 && (P != 1 || n2 > 512)) return false;
     const int W = n2 / 2;
     if (R < 4 || (R & 3) || R > n1 || (n1 % R)) return false;
     if (R * (n2 / 8) < 32 || R * (n2 / 8) > 512 || 3 * (size_t)R * n2 * sizeof(float2) > smax) return false;
@@ -694,15 +729,21 @@ bool tiles_valid(int n1, int n2, int R, int C) {
 }
 
 static int rows_per_cta(const reg_ctx* ctx) {
-    int R, C;
-    default_tiles(ctx->n1, ctx->n2, &R, &C);
+    int R, C, P;
+    default_tiles(ctx->n1, ctx->n2, &R, &C, &P);
     return ctx->tileR > 0 ? ctx->tileR : R;
 }
 
 static int cols_per_cta(const reg_ctx* ctx) {
-    int R, C;
-    default_tiles(ctx->n1, ctx->n2, &R, &C);
+    int R, C, P;
+    default_tiles(ctx->n1, ctx->n2, &R, &C, &P);
     return ctx->tileC > 0 ? ctx->tileC : C;
+}
+
+static bool prefetch_rows(const reg_ctx* ctx) {
+    int R, C, P;
+    default_tiles(ctx->n1, ctx->n2, &R, &C, &P);
+    return (ctx->tileR > 0 ? ctx->tileP : P) != 0;
 }
 
 // Opt in to more than 48 KB of dynamic shared memory once per kernel instantiation and size
@@ -731,11 +772,12 @@ static void set_smem(K kern, size_t bytes) {
         default: break;                               \
     }
 
-struct RowCfg { int R, threads; size_t smem; int grid; };
+struct RowCfg { int R, threads; size_t smem; int grid; bool pre; };
 static RowCfg row_cfg(reg_ctx* ctx) {
     RowCfg c;
     const int L = ctx->n2;
     c.R = rows_per_cta(ctx);
+    c.pre = prefetch_rows(ctx);
     c.threads = c.R * (L / 8);
     c.smem = 3 * (size_t)c.R * L * sizeof(float2);
     c.grid = ctx->n1 / c.R;
@@ -794,7 +836,7 @@ void launch_row_adv(reg_ctx* ctx, const AdvArgs& a) {
                 (a.S_out ? 1 : 0);
     ktimer_begin(ctx, KC_ROWSTAGE, 4.0 * fl * ctx->N);
     DISPATCH_LOG(ctx->log2, {
-        auto kern = k_row_adv<LG>;
+        auto kern = (g.pre && LG <= 9) ? k_row_adv<LG, (LG <= 9)> : k_row_adv<LG, false>;
         set_smem(kern, g.smem);
         launch_k(ctx, kern, g.grid, g.threads, g.smem, a, ctx->N, g.R, ctx->tw);
     });
@@ -807,7 +849,7 @@ void launch_row_adj(reg_ctx* ctx, const AdjArgs& a) {
     double fl = 1 + 1 + 2 + 1 + (a.stage == 2 ? 1 : 0) + (a.b ? 6 : 0) + (a.F1 ? 2 : 0);
     ktimer_begin(ctx, KC_ROWSTAGE, 4.0 * fl * ctx->N);
     DISPATCH_LOG(ctx->log2, {
-        auto kern = k_row_adj<LG>;
+        auto kern = (g.pre && LG <= 9) ? k_row_adj<LG, (LG <= 9)> : k_row_adj<LG, false>;
         set_smem(kern, g.smem);
         launch_k(ctx, kern, g.grid, g.threads, g.smem, a, ctx->N, g.R, ctx->tw);
     });
@@ -872,6 +914,11 @@ void launch_col(reg_ctx* ctx, int op, const float2* const* in, float2* const* ou
         case OP_GRAD1: launch_col_t<1, 1, OP_GRAD1>(ctx, in, out, P, part); break;
         case OP_DIV1: launch_col_t<1, 1, OP_DIV1>(ctx, in, out, P, part); break;
         case OP_SMOOTH_PROJ: launch_col_t<2, 2, OP_SMOOTH_PROJ>(ctx, in, out, P, part); break;
+        case OP_QINV: launch_col_t<2, 2, OP_QINV>(ctx, in, out, P, part); break;
+        case OP_QMUL: launch_col_t<2, 2, OP_QMUL>(ctx, in, out, P, part); break;
+        case OP_ASSEMBLE_Y: launch_col_t<4, 2, OP_ASSEMBLE_Y>(ctx, in, out, P, part); break;
+        case OP_QNORM: launch_col_t<2, 0, OP_QNORM>(ctx, in, out, P, part); break;
+        case OP_ENERGY_Y: launch_col_t<2, 0, OP_ENERGY_Y>(ctx, in, out, P, part); break;
         default: break;
     }
 }

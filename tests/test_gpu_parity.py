@@ -300,3 +300,75 @@ def test_warm_start_solve_matches_oracle():
     assert st["n_newton"] == st_ref["n_newton"] and st["n_mv"] == st_ref["n_mv"]
     assert rel_l2(to_np(v), v_ref) < 1e-3
     ctx.close()
+
+
+@pytest.mark.parametrize("seed,gamma", [(4000, math.inf), (4013, math.inf), (4010, 0.0)])
+def test_h2_solve_in_preconditioned_coordinates_matches_oracle(seed, gamma):
+    """H2 solves iterate on y = (beta_v A')^(1/2) v (reg_solve): 128^2 mixed-batch pairs
+    (nt=16, beta_v=1e-2) that stalled at the FP32 floor of the H2 gradient when iterating
+    on v reach the tolerance with the FP64 oracle's Newton count and velocity."""
+    import torch
+    n, nt = 128, 16
+    mT, mR, _ = synth.ellipses_pair(n, seed, vmax=0.196, kmax=16)
+    P = Registration(mT, mR, nt, regnorm=2, beta_v=1e-2, beta_w=gamma)
+    v_ref, st_ref = P.solve(tol=1e-2)
+    assert st_ref["status"] == 0
+    ctx = make_ctx(n, n, nt, regnorm=2, beta=1e-2, gamma=gamma)
+    ctx.set_images(to_gpu(mT), to_gpu(mR))
+    v = torch.zeros(2, n, n, device="cuda")
+    st = ctx.solve(v)
+    assert st["status"] == 0 and st["gnorm_rel"] <= 1e-2
+    assert st["n_newton"] == st_ref["n_newton"]
+    assert rel_l2(to_np(v), v_ref) < 1e-3
+    assert abs(st["rnorm_rel_sq"] - st_ref["rnorm_rel_sq"]) < 1e-3 * st_ref["rnorm_rel_sq"]
+    ctx.close()
+
+
+@pytest.mark.parametrize("n,beta,gamma", [(256, 1e-3, 1e-3), (512, 1e-2, math.inf), (512, 1e-3, 0.0)])
+def test_h2_solves_converge_at_full_size(n, beta, gamma):
+    """Property at the 256^2 / 512^2 sizes (no oracle run): H2 solves of the mixed batch's
+    settings reach ||g|| <= 1e-2 ||g(0)|| with a monotone objective and div v = 0 (w = 0)."""
+    import torch
+    from oracle import spectral as S
+    nt = 16
+    mT, mR, _ = synth.ellipses_pair(n, 4100 + n, vmax=0.049 * 512 / n, kmax=16)
+    ctx = make_ctx(n, n, nt, regnorm=2, beta=beta, gamma=gamma)
+    ctx.set_images(to_gpu(mT), to_gpu(mR))
+    v = torch.zeros(2, n, n, device="cuda")
+    st = ctx.solve(v)
+    assert st["status"] == 0 and st["gnorm_rel"] <= 1e-2
+    assert st["J"] < st["J0"]
+    if math.isinf(gamma):
+        vn = to_np(v).astype(np.float64)
+        assert np.abs(S.div(vn)).max() < 1e-4 * max(np.abs(vn).max(), 1e-30) * n
+    ctx.close()
+
+
+@pytest.mark.parametrize("n1,n2,regnorm,beta", [(64, 128, 2, 1e-2), (128, 64, 1, 1e-3), (32, 32, 2, 1e-3)])
+def test_precond_sqrt(n1, n2, regnorm, beta):
+    """Q^{+-1} x with Q^ = (beta_v A'^)^(1/2), A'(0) = 1, against the oracle's symbols; Q Q^-1 = I;
+    Q^2 = the preconditioner's inverse (Q^-1 Q^-1 x = P^-1 x)."""
+    import torch
+    rng = np.random.default_rng(n1 + n2 + regnorm)
+    x = np.stack([synth.gaussian_smooth(rng.standard_normal((n1, n2)), 0.05) for _ in range(2)])
+    A = S.reg_symbol(n1, n2, regnorm).copy()
+    A[0, 0] = 1.0
+    Qs = np.sqrt(beta * A)
+    ref = lambda m: np.stack([np.real(np.fft.ifft2(m * np.fft.fft2(x[c]))) for c in range(2)])
+    ctx = make_ctx(n1, n2, 4, regnorm=regnorm, beta=beta)
+    xg = to_gpu(x)
+    out = torch.empty_like(xg)
+    for inv, mult in ((False, Qs), (True, 1.0 / Qs)):
+        ctx.apply_precond_sqrt(xg, out, inverse=inv)
+        assert rel_l2(to_np(out), ref(mult)) < 1e-5
+    back = torch.empty_like(xg)
+    ctx.apply_precond_sqrt(xg, out, inverse=True)
+    ctx.apply_precond_sqrt(out, back, inverse=False)
+    # Q re-amplifies the FP32 rounding of Q^-1 x by up to max Q / min Q
+    assert rel_l2(to_np(back), x) < 1e-5 + 2.0 ** -24 * Qs.max() / Qs.min()
+    z = torch.empty_like(xg)
+    ctx.apply_precond(xg, z)
+    ctx.apply_precond_sqrt(xg, out, inverse=True)
+    ctx.apply_precond_sqrt(out, back, inverse=True)
+    assert rel_l2(to_np(back), to_np(z)) < 1e-5
+    ctx.close()

@@ -1,8 +1,8 @@
 """FFT tile choices and their autotuner (row a15): every valid (rows per row
-CTA, spectrum columns per column CTA) gives the same gradient and Hessian
-matvec bit for bit (each row and column transform is the same code whatever
-the CTA holds; only FP64 reduction order may change J in the last bits), and
-reg_autotune picks a valid pair that later contexts use."""
+CTA, spectrum columns per column CTA, operand prefetch) gives the same
+gradient and Hessian matvec bit for bit (each row and column transform is the
+same code whatever the CTA holds; only FP64 reduction order may change J in
+the last bits), and reg_autotune picks a valid choice that later contexts use."""
 import math
 
 import numpy as np
@@ -21,7 +21,7 @@ def _cuda():
 
 
 def valid_tiles(n1, n2):
-    """The launch limits stated for reg_autotune, restated."""
+    """The launch limits stated for reg_autotune, restated: [(R, C, P)]."""
     out = []
     R = 4
     while R <= n1:
@@ -30,7 +30,8 @@ def valid_tiles(n1, n2):
             ok = (n1 % R == 0 and 32 <= R * n2 // 8 <= 512 and 3 * R * n2 * 8 <= 227 * 1024 and
                   (n2 // 2) % C == 0 and 32 <= C * n1 // 8 <= 256 and 3 * C * n1 * 8 <= 227 * 1024)
             if ok:
-                out.append((R, C))
+                for P in ((0, 1) if n2 <= 512 else (0,)):
+                    out.append((R, C, P))
             C *= 2
         R *= 2
     return out
@@ -52,21 +53,21 @@ def test_every_tile_choice_gives_identical_results(n1, n2):
     g0, h0 = torch.empty(2, n1, n2, device="cuda"), torch.empty(2, n1, n2, device="cuda")
     torch.cuda.synchronize()
     ctx.set_images(mTd, mRd)
-    ctx.set_tiles(0, 0)
+    ctx.set_tiles(0, 0, 0)
     J0 = ctx.gradient(vd, g0)
     ctx.hessian_matvec(vtd, h0)
     cands = valid_tiles(n1, n2)
     assert len(cands) >= 2
-    for R, C in cands:
-        ctx.set_tiles(R, C)
-        assert ctx.tile_config() == (R, C)
+    for R, C, P in cands:
+        ctx.set_tiles(R, C, P)
+        assert ctx.tile_config() == (R, C, P)
         g, h = torch.empty_like(g0), torch.empty_like(h0)
         torch.cuda.synchronize()
         J = ctx.gradient(vd, g)
         ctx.hessian_matvec(vtd, h)
         stream.synchronize()
-        assert torch.equal(g, g0), (R, C)
-        assert torch.equal(h, h0), (R, C)
+        assert torch.equal(g, g0), (R, C, P)
+        assert torch.equal(h, h0), (R, C, P)
         assert abs(J - J0) <= 1e-12 * abs(J0)
     ctx.close()
 
@@ -74,19 +75,25 @@ def test_every_tile_choice_gives_identical_results(n1, n2):
 def test_invalid_tiles_rejected():
     from paper_1503_00757_gb300.binding import Context, RegError
     ctx = Context(128, 128, 4)
-    for R, C in [(6, 4), (256, 4), (4, 3), (4, 128), (2, 4)]:
+    for R, C, P in [(6, 4, 0), (256, 4, 0), (4, 3, 0), (4, 128, 0), (2, 4, 0), (4, 4, 2)]:
         with pytest.raises(RegError):
-            ctx.set_tiles(R, C)
+            ctx.set_tiles(R, C, P)
+    ctx.close()
+    big = Context(64, 1024, 4)
+    with pytest.raises(RegError):
+        big.set_tiles(4, 4, 1)  # no prefetch variant for 1024-point rows
+    big.close()
     ctx.close()
 
 
 def test_autotune_picks_a_valid_pair_used_by_later_contexts():
     from paper_1503_00757_gb300.binding import Context, autotune
-    R, C, ms = autotune(128, 256, nt=4, force=True)
-    assert (R, C) in valid_tiles(128, 256)
-    assert ms > 0.0
-    ctx = Context(128, 256, 4)
-    assert ctx.tile_config() == (R, C)
-    ctx.close()
-    R2, C2, ms2 = autotune(128, 256, nt=4)
-    assert (R2, C2) == (R, C) and ms2 < 0.0  # cached
+    for conc in (1, 3):
+        R, C, P, ms = autotune(128, 256, nt=4, concurrency=conc, force=True)
+        assert (R, C, P) in valid_tiles(128, 256)
+        assert ms > 0.0
+        ctx = Context(128, 256, 4)
+        assert ctx.tile_config() == (R, C, P)
+        ctx.close()
+        R2, C2, P2, ms2 = autotune(128, 256, nt=4)
+        assert (R2, C2, P2) == (R, C, P) and ms2 < 0.0  # cached
