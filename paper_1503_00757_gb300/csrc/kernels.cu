@@ -148,6 +148,11 @@ __device__ double block_reduce(double v) {
 // threads per SM).  PRE = false loads them after the FFT and is compiled for
 // two CTAs of 512 threads per SM (64 registers), which is what concurrent
 // solves and 1024-point rows want.  The autotuner chooses per grid.
+// Elements per batch of late operand loads in the RK2 row kernels: the largest
+// batch that stays within 64 registers without spills (advection 8, adjoint 4).
+constexpr int ADV_LOAD_BATCH = 8;
+constexpr int ADJ_LOAD_BATCH = 4;
+
 template <bool PRE>
 struct RowBlocks {
     static constexpr int value = PRE ? 1 : 2;
@@ -304,19 +309,28 @@ __global__ void __launch_bounds__(512, RowBlocks<PRE>::value) k_row_adv(AdvArgs 
 #pragma unroll
         for (int k = 0; k < 8; ++k) x[k] = make_float2(0.f, 0.f);
     }
+    // Late operands are loaded a batch of elements at a time before any of those
+    // elements' results is stored, so that the loads of a batch are in flight together
+    // (the compiler cannot move a load above a store to a pointer that may alias it).
     float out[8];
 #pragma unroll
-    for (int k = 0; k < 8; ++k) {
-        if (!early) load_ops(k);
-        const size_t idx = rowbase + t + k * T;
-        const float d1 = x[k].x, d2 = x[k].y;
-        if (a.grad_out) {
-            a.grad_out[idx] = d1;
-            a.grad_out[N + idx] = d2;
+    for (int k0 = 0; k0 < 8; k0 += ADV_LOAD_BATCH) {
+        if (!early) {
+#pragma unroll
+            for (int k = k0; k < k0 + ADV_LOAD_BATCH; ++k) load_ops(k);
         }
-        const float kk = psrc[k] - (pv1[k] * d1 + pv2[k] * d2);
-        out[k] = (a.stage == 1) ? fmaf(a.h, kk, puj[k]) : 0.5f * (puj[k] + pus[k] + a.h * kk);
-        a.u_out[idx] = out[k];
+#pragma unroll
+        for (int k = k0; k < k0 + ADV_LOAD_BATCH; ++k) {
+            const size_t idx = rowbase + t + k * T;
+            const float d1 = x[k].x, d2 = x[k].y;
+            if (a.grad_out) {
+                a.grad_out[idx] = d1;
+                a.grad_out[N + idx] = d2;
+            }
+            const float kk = psrc[k] - (pv1[k] * d1 + pv2[k] * d2);
+            out[k] = (a.stage == 1) ? fmaf(a.h, kk, puj[k]) : 0.5f * (puj[k] + pus[k] + a.h * kk);
+            a.u_out[idx] = out[k];
+        }
     }
     if (!a.S_out) return;
     float* O = reinterpret_cast<float*>(A);
@@ -420,19 +434,25 @@ __global__ void __launch_bounds__(512, RowBlocks<PRE>::value) k_row_adj(AdjArgs 
     }
     __syncthreads();
 #pragma unroll
-    for (int k = 0; k < 8; ++k) {
-        if (!PRE) load_ops(k);
-        const int j = t + k * T;
-        const size_t idx = rowbase + j;
-        const float dv = O[q * L + j];
-        const float out = (a.stage == 1) ? fmaf(a.h, dv, plj[k]) : 0.5f * (plj[k] + pls[k] + a.h * dv);
-        a.l_out[idx] = out;
-        if (a.b) {
-            const float wl = a.w * out;
-            a.b[idx] = fmaf(wl, pg1[k], pb1[k]);
-            a.b[N + idx] = fmaf(wl, pg2[k], pb2[k]);
+    for (int k0 = 0; k0 < 8; k0 += ADJ_LOAD_BATCH) {
+        if (!PRE) {
+#pragma unroll
+            for (int k = k0; k < k0 + ADJ_LOAD_BATCH; ++k) load_ops(k);  // batched, as in k_row_adv
         }
-        x[k] = make_float2(out * pv1[k], out * pv2[k]);
+#pragma unroll
+        for (int k = k0; k < k0 + ADJ_LOAD_BATCH; ++k) {
+            const int j = t + k * T;
+            const size_t idx = rowbase + j;
+            const float dv = O[q * L + j];
+            const float out = (a.stage == 1) ? fmaf(a.h, dv, plj[k]) : 0.5f * (plj[k] + pls[k] + a.h * dv);
+            a.l_out[idx] = out;
+            if (a.b) {
+                const float wl = a.w * out;
+                a.b[idx] = fmaf(wl, pg1[k], pb1[k]);
+                a.b[N + idx] = fmaf(wl, pg2[k], pb2[k]);
+            }
+            x[k] = make_float2(out * pv1[k], out * pv2[k]);
+        }
     }
     if (!a.F1) return;
     flux_fft_store<LOGL>(x, q, t, R, row0, A, X, a.F1, a.F2, tw);
@@ -605,6 +625,7 @@ __global__ void __launch_bounds__(256) k_col(ColArgs a, const float2* __restrict
     const int W = a.n2 >> 1;
     float2* A = sm;
     float2* X = sm + C * L;
+    float2* B2 = sm + 3 * C * L;  // OP_DIV1: the untransformed second input, staged with the first
     const int c = threadIdx.x / T, t = threadIdx.x - c * T;
     const int e0 = blockIdx.x * C;
     const int e = e0 + c;
@@ -616,7 +637,9 @@ __global__ void __launch_bounds__(256) k_col(ColArgs a, const float2* __restrict
             const int g = idx / (4 * C);
             const int rem = idx - g * 4 * C;
             const int cc = rem >> 2, rr = rem & 3;
-            A[cc * L + 4 * g + rr] = src[((size_t)g * W + e0 + cc) * 4 + rr];
+            const size_t gi = ((size_t)g * W + e0 + cc) * 4 + rr;
+            A[cc * L + 4 * g + rr] = src[gi];
+            if (OP == OP_DIV1 && f == 0) B2[cc * L + 4 * g + rr] = a.in[1][gi];
         }
         __syncthreads();
 #pragma unroll
@@ -688,7 +711,7 @@ __global__ void __launch_bounds__(256) k_col(ColArgs a, const float2* __restrict
             float2 val = A[cc * L + 4 * g + rr];
             if (OP == OP_DIV1) {
                 // + (i k2~ / n2) F2, diagonal in the row spectra; k2~ = 0 in the packed column 0
-                const float2 f2 = a.in[1][gi];
+                const float2 f2 = B2[cc * L + 4 * g + rr];
                 const float ce = cd2 * (float)(e0 + cc);
                 val = make_float2(val.x - ce * f2.y, val.y + ce * f2.x);
             }
@@ -716,7 +739,7 @@ void default_tiles(int n1, int n2, int* R_out, int* C_out, int* P_out) {
 
 // Launch limits of the row kernels (32 to 512 threads; 2 CTAs per SM for
 // 1024-point rows) and the column kernel (32 to 256 threads), and 227 KB of
-// shared memory (3 complex buffers of R rows or C columns).
+// shared memory (3 complex buffers of R rows, up to 4 of C columns).
 bool tiles_valid(int n1, int n2, int R, int C, int P) {
     const size_t smax = 227 * 1024;
     if (P != 0 && (P != 1 || n2 > 512)) return false;
@@ -724,7 +747,7 @@ bool tiles_valid(int n1, int n2, int R, int C, int P) {
     if (R < 4 || (R & 3) || R > n1 || (n1 % R)) return false;
     if (R * (n2 / 8) < 32 || R * (n2 / 8) > 512 || 3 * (size_t)R * n2 * sizeof(float2) > smax) return false;
     if (C < 2 || (C & (C - 1)) || C > W || (W % C)) return false;
-    if (C * (n1 / 8) < 32 || C * (n1 / 8) > 256 || 3 * (size_t)C * n1 * sizeof(float2) > smax) return false;
+    if (C * (n1 / 8) < 32 || C * (n1 / 8) > 256 || 4 * (size_t)C * n1 * sizeof(float2) > smax) return false;
     return true;
 }
 
@@ -877,7 +900,7 @@ static void launch_col_t(reg_ctx* ctx, const float2* const* in, float2* const* o
                          double* part) {
     const int L = ctx->n1, W = ctx->n2 / 2;
     const int cpb = cols_per_cta(ctx);
-    const size_t smem = 3 * (size_t)cpb * L * sizeof(float2);
+    const size_t smem = (OP == OP_DIV1 ? 4 : 3) * (size_t)cpb * L * sizeof(float2);
     ColArgs a;
     for (int f = 0; f < 5; ++f) a.in[f] = (f < NIN) ? in[f] : nullptr;
     if (OP == OP_DIV1) a.in[1] = in[1];  // read untransformed in the store phase

@@ -28,7 +28,7 @@ def valid_tiles(n1, n2):
         C = 2
         while C <= n2 // 2:
             ok = (n1 % R == 0 and 32 <= R * n2 // 8 <= 512 and 3 * R * n2 * 8 <= 227 * 1024 and
-                  (n2 // 2) % C == 0 and 32 <= C * n1 // 8 <= 256 and 3 * C * n1 * 8 <= 227 * 1024)
+                  (n2 // 2) % C == 0 and 32 <= C * n1 // 8 <= 256 and 4 * C * n1 * 8 <= 227 * 1024)
             if ok:
                 for P in ((0, 1) if n2 <= 512 else (0,)):
                     out.append((R, C, P))
