@@ -268,9 +268,12 @@ int reg_detgrad(reg_ctx* ctx, const float* v, float* detF, double* stats);
 /* ---- row a16: learned warm start (the paper has no learned component) ---- */
 
 /* An 8-layer 3x3 convolutional network with circular padding (channel
- * widths 2 -> 32 (x7) -> 2, ReLU between layers) mapping an image pair to a
- * velocity, Leray-projected (Eq. (e:project-body-force) with w = 0) so that
- * it satisfies div v = 0.  BF16 activations and weights on the tensor cores
+ * widths 2 -> 32 (x7) -> 2, ReLU between layers, layer l dilated by
+ * min(d_l, H/8, W/32) with d = 1, 2, 4, 8, 8, 4, 2, 1) mapping an image pair
+ * to a velocity.  Its output map is a Gaussian low-pass (symbol
+ * exp(-sigma^2 |k|^2 / 2), sigma = 2 * 2 pi / max(H, W)) followed by the Leray
+ * projection (Eq. (e:project-body-force) with w = 0), so that the prediction
+ * satisfies div v = 0 and has no grid-scale noise.  BF16 activations and weights on the tensor cores
  * with FP32 accumulation; FP32 master weights; Adam (0.9, 0.999, 1e-8).
  * Parameters are a flat FP32 array: for each layer W (Cout, Cin, 3, 3), with
  * W[o, c, dy+1, dx+1] multiplying the input at (y+dy, x+dx), then b (Cout).
@@ -285,9 +288,13 @@ int reg_net_set_stream(reg_net* net, void* stream);
 /* Copy parameters in (device, num_params floats; resets the Adam state) / out. */
 int reg_net_set_params(reg_net* net, const float* params);
 int reg_net_get_params(reg_net* net, float* params);
-/* Leray-projected prediction v_out. */
+/* Prediction v_out = s P G net(x), s the output scale (default 1). */
 int reg_net_forward(reg_net* net, const float* images, int B, float* v_out);
-/* loss = sum((P net(x) - t)^2) / (2 M) (M = 2 B H W, host double) and, if grads
+/* Output scale s of reg_net_forward (0 < s <= 4; training and the loss use
+ * s = 1): a warm start of s times the prediction; the warm-start pipeline
+ * calibrates s on validation pairs. */
+int reg_net_set_output_scale(reg_net* net, float scale);
+/* loss = sum((P G net(x) - t)^2) / (2 M) (M = 2 B H W, host double) and, if grads
  * is not NULL, its gradient w.r.t. the flat parameters (device).  Synchronous. */
 int reg_net_loss_grad(reg_net* net, const float* images, const float* targets, int B, double* loss, float* grads);
 /* One Adam step with learning rate lr on that loss.  Synchronous (loss is read back). */

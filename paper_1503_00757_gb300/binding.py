@@ -90,6 +90,7 @@ _SIGS = {
     "reg_net_set_params": ([_P, _P], _I),
     "reg_net_get_params": ([_P, _P], _I),
     "reg_net_forward": ([_P, _P, _I, _P], _I),
+    "reg_net_set_output_scale": ([_P, ctypes.c_float], _I),
     "reg_net_loss_grad": ([_P, _P, _P, _I, ctypes.POINTER(_D), _P], _I),
     "reg_net_train_step": ([_P, _P, _P, _I, ctypes.c_float, ctypes.POINTER(_D)], _I),
 }
@@ -267,6 +268,10 @@ class Net:
         B = images.shape[0]
         n = B * 2 * self.H * self.W
         _check(lib().reg_net_forward(self.h, _ptr(images, n, "images"), B, _ptr(v_out, n, "v_out")))
+
+    def set_output_scale(self, scale):
+        """reg_net_forward returns scale times the projected prediction (warm-start damping)."""
+        _check(lib().reg_net_set_output_scale(self.h, float(scale)))
 
     def loss_grad(self, images, targets, grads=None):
         B = images.shape[0]

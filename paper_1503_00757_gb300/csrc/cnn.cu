@@ -426,6 +426,7 @@ struct reg_net {
     int nwg;                   // wgrad CTAs
     double *d_part, *h_part;
     int adam_t;
+    float out_scale;           // reg_net_forward multiplies its prediction by this
 };
 
 static size_t conv_smem(int cin, int cout) {
@@ -462,7 +463,7 @@ extern "C" int reg_net_create(int H, int W, int max_batch, reg_net** out) {
         return reg_fail(REG_ERR_ARG, "H and W must be powers of two in [32, 1024]");
     if (max_batch < 1 || max_batch > 256) return reg_fail(REG_ERR_ARG, "max_batch must be in [1, 256]");
     reg_net* n = new reg_net();
-    n->H = H; n->W = W; n->maxB = max_batch; n->stream = 0; n->adam_t = 0;
+    n->H = H; n->W = W; n->maxB = max_batch; n->stream = 0; n->adam_t = 0; n->out_scale = 1.f;
     long long off = 0, gwo = 0, gbo = 0, wfo = 0;
     for (int l = 0; l < NLAYER; ++l) {
         LayerDesc d;
@@ -607,9 +608,22 @@ extern "C" int reg_net_forward(reg_net* n, const float* images, int B, float* v_
     if (B < 1 || B > n->maxB) return reg_fail(REG_ERR_ARG, "batch out of range");
     const int st = net_forward(n, images, B);
     if (st != REG_OK) return st;
-    const cudaError_t e = cudaMemcpyAsync(v_out, n->pred, sizeof(float) * 2 * B * n->H * n->W,
-                                          cudaMemcpyDeviceToDevice, n->stream);
+    cudaError_t e;
+    if (n->out_scale != 1.f) {
+        launch_axpby(n->proj, 2LL * B * n->H * n->W, n->out_scale, n->pred, 0.f, n->pred, -1, -1, v_out);
+        e = cudaGetLastError();
+    } else {
+        e = cudaMemcpyAsync(v_out, n->pred, sizeof(float) * 2 * B * n->H * n->W, cudaMemcpyDeviceToDevice,
+                            n->stream);
+    }
     return e == cudaSuccess ? REG_OK : reg_fail(REG_ERR_CUDA, cudaGetErrorString(e));
+}
+
+extern "C" int reg_net_set_output_scale(reg_net* n, float scale) {
+    if (!n) return reg_fail(REG_ERR_ARG, "net is NULL");
+    if (!(scale > 0.f && scale <= 4.f)) return reg_fail(REG_ERR_ARG, "output scale must be in (0, 4]");
+    n->out_scale = scale;
+    return REG_OK;
 }
 
 // forward, loss, backward into n->gW / n->gb

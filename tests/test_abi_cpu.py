@@ -81,3 +81,4 @@ def test_new_entry_points_reject_invalid_arguments_without_gpu(lib):
     assert lib.reg_autotune(reg_grid(64, 64), 4, 17, 0, None, None, None, None) == 1
     assert lib.reg_tile_config(None, ctypes.byref(R), ctypes.byref(C), ctypes.byref(P)) == 1
     assert lib.reg_set_tiles(None, 4, 2, 0) == 1
+    assert lib.reg_net_set_output_scale(None, ctypes.c_float(1.0)) == 1

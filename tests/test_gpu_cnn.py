@@ -105,3 +105,26 @@ def test_training_reduces_loss_and_output_is_divergence_free():
     for i in range(B):
         assert np.abs(S.div(vn[i])).max() < 1e-3 * np.abs(vn[i]).max()
     net.close()
+
+
+def test_output_scale_multiplies_the_prediction():
+    import torch
+    from paper_1503_00757_gb300.binding import Net, flatten_params
+    n, B = 64, 2
+    x, _ = _data(n, B, 5200)
+    net = Net(n, n, B)
+    net.set_params(torch.tensor(flatten_params(cnn.init_params(14)), dtype=torch.float32, device="cuda"))
+    xg = torch.tensor(x, dtype=torch.float32, device="cuda").contiguous()
+    v1, vs = torch.empty(B, 2, n, n, device="cuda"), torch.empty(B, 2, n, n, device="cuda")
+    net.forward(xg, v1)
+    net.set_output_scale(0.75)
+    net.forward(xg, vs)
+    torch.cuda.synchronize()
+    assert torch.equal(vs, 0.75 * v1)
+    net.set_output_scale(1.0)
+    net.forward(xg, vs)
+    torch.cuda.synchronize()
+    assert torch.equal(vs, v1)
+    with pytest.raises(Exception):
+        net.set_output_scale(0.0)
+    net.close()
