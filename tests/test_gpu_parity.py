@@ -372,3 +372,49 @@ def test_precond_sqrt(n1, n2, regnorm, beta):
     ctx.apply_precond_sqrt(out, back, inverse=True)
     assert rel_l2(to_np(back), to_np(z)) < 1e-5
     ctx.close()
+
+
+def test_precision_config_full_size():
+    """The precision workload at its full size: 256^2 smoothed noisy 4-label images, v* with
+    |k| <= 8 and a 30 % gradient part (max|v*| = 0.8), H2, beta_v = beta_w = 1e-3 (mass source).
+    Operator parity against the FP64 oracle at v = v*/2 with nt adapted to CFL 0.25 (66 steps);
+    then the GPU solve with the CFL policy reaches the tolerance within 100 Newton iterations
+    (property, no oracle solve)."""
+    import torch
+    from paper_1503_00757_gb300.binding import default_opts
+    n = 256
+    mT, mR, vs = synth.labels_pair(n, 2000)
+    v = 0.5 * vs
+    vmax = np.sqrt(v[0] ** 2 + v[1] ** 2).max()
+    nt = int(math.ceil(vmax * n / (2 * math.pi * 0.25)))
+    assert 60 <= nt <= 70
+    vt = synth.velocity(n, n, 8, 0.3, np.random.default_rng(9), grad_fraction=0.3)
+    P = Registration(mT, mR, nt, regnorm=2, beta_v=1e-3, beta_w=1e-3)
+    ctx = make_ctx(n, n, nt, regnorm=2, beta=1e-3, gamma=1e-3)
+    ctx.set_images(to_gpu(mT), to_gpu(mR))
+    g = torch.empty(2, n, n, device="cuda")
+    J = ctx.gradient(to_gpu(v), g)
+    g_ref, J_ref = P.gradient(v)
+    assert abs(J - J_ref) < OP_TOL * abs(J_ref)
+    b = torch.empty(2, n, n, device="cuda")
+    ctx.body_force(b)
+    assert rel_l2(to_np(b), P.b) < OP_TOL
+    assert rel_l2(to_np(g), g_ref) < op_tol(1e-3, 2, n, n, v, g_ref, P.b)
+    Hv = torch.empty(2, n, n, device="cuda")
+    ctx.hessian_matvec(to_gpu(vt), Hv)
+    Hv_ref = P.matvec(vt)
+    ctx.body_force(b)
+    # the intermediate b~ carries the FP32 rounding of 2 nt RK2 stages (incremental state and
+    # adjoint): its bound grows with nt beyond the 32 steps of the other cases
+    assert rel_l2(to_np(b), P.bt) < OP_TOL * max(1.0, nt / 32)
+    assert rel_l2(to_np(Hv), Hv_ref) < op_tol(1e-3, 2, n, n, vt, Hv_ref, P.bt)
+    ctx.close()
+    ctx = make_ctx(n, n, 16, regnorm=2, beta=1e-3, gamma=1e-3)
+    ctx.set_images(to_gpu(mT), to_gpu(mR))
+    vsol = torch.zeros(2, n, n, device="cuda")
+    # a hard problem (H2, beta_v = 1e-3, displacements up to 0.8): on one GB300 it takes 67
+    # Newton iterations and ~6200 matvecs, most PCG solves at their 100-iteration cap
+    st = ctx.solve(vsol, default_opts(tol=1e-2, nt_policy=1, cfl_max=0.25, maxit_newton=100))
+    assert st["status"] == 0 and st["gnorm_rel"] <= 1e-2 and st["J"] < st["J0"]
+    assert st["cfl"] <= 0.25 + 1e-9 and st["nt_used"] >= 16
+    ctx.close()
