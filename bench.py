@@ -78,6 +78,10 @@ def images(seed=SEED):
     return mT.astype(np.float32), mR.astype(np.float32)
 
 
+# DRAM bytes (read + write) per launch of the RK2 row-stage kernel at 512^2, nt=32: the mean over
+# 8 incremental-state launches of one ncu capture (cold L2), profiles/traffic_row_stage_512_nt32.md.
+ROW_STAGE_TRAFFIC_512 = 9.99e6
+
 C4_SIZES = (128, 256, 512)
 C4_COUNTS = (147, 73, 36)  # 4 : 2 : 1 over 256 pairs
 C4_VMAX = {128: 0.196, 256: 0.098, 512: 0.049}  # CFL 0.25 at nt = 16
@@ -551,7 +555,8 @@ def main():
                     "d2h_bytes_per_step": PAIRS * 2 * 4 * N_GRID * N_GRID},
             "gpu_launches": launches,
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                         "frac": achieved / peak, "traffic": None, "kernel": names[dom],
+                         "frac": achieved / peak,
+                         "traffic": ROW_STAGE_TRAFFIC_512 if dom == 1 else None, "kernel": names[dom],
                          "launches": n_dom, "ms": ms_dom, "peak_kind": peak_kind},
             "matvec_1024": ({"ms_per_matvec": big["ms_per_matvec"], "matvec_per_s": 1e3 / big["ms_per_matvec"],
                              "roofline": {"bound": "hbm", "kernel": big["roofline"]["kernel"],
