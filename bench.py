@@ -113,8 +113,8 @@ def run_batched_mixed(dev, stream, opts, nworkers=16):
     gen_s = time.perf_counter() - t0
     tiles = {}
     for n in C4_SIZES:
-        R, C, P, ms = autotune(n, n, nt=4, concurrency=8)
-        tiles[str(n)] = {"rows_per_cta": R, "cols_per_cta": C, "prefetch": P}
+        R, C, P, D, ms = autotune(n, n, nt=8, concurrency=8)
+        tiles[str(n)] = {"rows_per_cta": R, "cols_per_cta": C, "prefetch": P, "pdl": D}
     pairs = []
     for s, (a, b) in zip(specs, imgs):
         n = s["n"]
@@ -291,8 +291,8 @@ def main():
 
     # FFT tiles of the workload's grid, picked once by the autotuner before any context exists
     # (with --profile-grid: the tiles of that grid instead)
-    tR, tC, tP, _ = autotune(args.profile_grid or N_GRID, args.profile_grid or N_GRID, nt=4,
-                             concurrency=1 if args.profile_grid else PAIRS)
+    tR, tC, tP, tD, _ = autotune(args.profile_grid or N_GRID, args.profile_grid or N_GRID, nt=8,
+                                 concurrency=1 if args.profile_grid else PAIRS)
 
     # the step's batch: PAIRS independent registrations of this rank (seeds differ per rank)
     pairs_np = [images(s) for s in rank_seeds(rank)]
@@ -540,7 +540,7 @@ def main():
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": WORKLOAD, "grid": [N_GRID, N_GRID], "nt": NT, "pairs_per_step": PAIRS,
-                       "tiles": {"rows_per_cta": tR, "cols_per_cta": tC, "prefetch": tP,
+                       "tiles": {"rows_per_cta": tR, "cols_per_cta": tC, "prefetch": tP, "pdl": tD,
                                  "tuned_for": f"{PAIRS} concurrent solves"},
                        "l2": "flushed between steps", "parallelism": f"replicas x{world}, {PAIRS} concurrent streams",
                        "start": "zero (plain); warm start reported in warm_start_vs_plain"},

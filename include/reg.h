@@ -234,7 +234,8 @@ void reg_executor_destroy(reg_executor* ex);
  * throughput of that many, as in the batch executor), for every valid tile
  * choice (R rows per row-kernel CTA, C spectrum columns per column-kernel
  * CTA, P = 1 if the RK2 row kernels prefetch their operands before waiting on
- * the preceding kernel), on the current device with zero images and velocity
+ * the preceding kernel) with programmatic dependent launch on and off
+ * (D, see reg_set_pdl), on the current device with zero images and velocity
  * and private streams, and records the fastest in a process-wide table;
  * contexts created afterwards on this device and grid use it (existing
  * contexts keep theirs).  Valid: R a multiple of 4 dividing n1,
@@ -246,17 +247,24 @@ void reg_executor_destroy(reg_executor* ex);
  * REG_ERR_ARG for a grid outside powers of two in [16, 1024], nt outside
  * [1, 4096] or concurrency outside [1, 16]. */
 int reg_autotune(reg_grid grid, int nt, int concurrency, int force, int* rows_per_cta, int* cols_per_cta,
-                 int* prefetch, double* ms_per_matvec);
+                 int* prefetch, int* pdl, double* ms_per_matvec);
 
-/* The tiles a context launches with (tuned, else the default rule: the
- * smallest R, C with at least 64 threads, P = 1 for n2 <= 512). */
-int reg_tile_config(reg_ctx* ctx, int* rows_per_cta, int* cols_per_cta, int* prefetch);
+/* The tiles and launch mode a context launches with (tuned, else the default
+ * rule: the smallest R, C with at least 64 threads, P = 1 for n2 <= 512,
+ * D = 1). */
+int reg_tile_config(reg_ctx* ctx, int* rows_per_cta, int* cols_per_cta, int* prefetch, int* pdl);
 
 /* Sets a context's tiles (validity as for reg_autotune; R = C = 0 restores
  * the default rule).  Results do not depend on the tiles except for the
  * summation order of FP64 reductions (objective, norms).  REG_ERR_ARG for
  * invalid tiles. */
 int reg_set_tiles(reg_ctx* ctx, int rows_per_cta, int cols_per_cta, int prefetch);
+
+/* Programmatic dependent launch (default on): each kernel may start while its
+ * predecessor finishes and waits on it in-kernel, which hides launch latency
+ * for one solve; enable = 0 launches every kernel after its predecessor has
+ * completed.  Results are identical either way. */
+int reg_set_pdl(reg_ctx* ctx, int enable);
 
 /* ---- row a14: deformation gradient (Eq. (e:def-grad)) ---- */
 

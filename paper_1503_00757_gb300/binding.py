@@ -80,9 +80,10 @@ _SIGS = {
     "reg_executor_solve": ([_P, ctypes.POINTER(reg_batch_item), _I, ctypes.POINTER(reg_solve_opts)], _I),
     "reg_executor_destroy": ([_P], None),
     "reg_autotune": ([reg_grid, _I, _I, _I, ctypes.POINTER(_I), ctypes.POINTER(_I), ctypes.POINTER(_I),
-                      ctypes.POINTER(_D)], _I),
-    "reg_tile_config": ([_P, ctypes.POINTER(_I), ctypes.POINTER(_I), ctypes.POINTER(_I)], _I),
+                      ctypes.POINTER(_I), ctypes.POINTER(_D)], _I),
+    "reg_tile_config": ([_P, ctypes.POINTER(_I), ctypes.POINTER(_I), ctypes.POINTER(_I), ctypes.POINTER(_I)], _I),
     "reg_set_tiles": ([_P, _I, _I, _I], _I),
+    "reg_set_pdl": ([_P, _I], _I),
     "reg_net_create": ([_I, _I, _I, ctypes.POINTER(_P)], _I),
     "reg_net_destroy": ([_P], None),
     "reg_net_num_params": ([_P], ctypes.c_longlong),
@@ -156,13 +157,13 @@ def spectral_grad_static(f, grad_f, stream=None):
 
 
 def autotune(n1, n2, nt=4, concurrency=1, force=False):
-    """FFT tiles for an n1 x n2 grid (reg_autotune) timed with `concurrency` solves at once:
-    (rows per row CTA, columns per column CTA, prefetch flag, ms per matvec of the winner,
-    or -1 if the grid was already tuned)."""
-    R, C, P, ms = ctypes.c_int(), ctypes.c_int(), ctypes.c_int(), ctypes.c_double()
+    """FFT tiles and launch mode for an n1 x n2 grid (reg_autotune) timed with `concurrency`
+    solves at once: (rows per row CTA, columns per column CTA, prefetch flag, PDL flag,
+    ms per matvec of the winner, or -1 if the grid was already tuned)."""
+    R, C, P, D, ms = ctypes.c_int(), ctypes.c_int(), ctypes.c_int(), ctypes.c_int(), ctypes.c_double()
     _check(lib().reg_autotune(reg_grid(n1, n2), nt, concurrency, 1 if force else 0, ctypes.byref(R), ctypes.byref(C),
-                              ctypes.byref(P), ctypes.byref(ms)))
-    return R.value, C.value, P.value, ms.value
+                              ctypes.byref(P), ctypes.byref(D), ctypes.byref(ms)))
+    return R.value, C.value, P.value, D.value, ms.value
 
 
 def _batch_items(pairs):
@@ -435,10 +436,15 @@ class Context:
         return lib().reg_launch_count(self.h)
 
     def tile_config(self):
-        """(rows per row-kernel CTA, spectrum columns per column-kernel CTA, prefetch flag) of this context."""
-        R, C, P = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
-        _check(lib().reg_tile_config(self.h, ctypes.byref(R), ctypes.byref(C), ctypes.byref(P)))
-        return R.value, C.value, P.value
+        """(rows per row-kernel CTA, spectrum columns per column-kernel CTA, prefetch flag, PDL flag)
+        of this context."""
+        R, C, P, D = ctypes.c_int(), ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+        _check(lib().reg_tile_config(self.h, ctypes.byref(R), ctypes.byref(C), ctypes.byref(P), ctypes.byref(D)))
+        return R.value, C.value, P.value, D.value
+
+    def set_pdl(self, enable):
+        """Programmatic dependent launch on (default) or off for this context's kernels."""
+        _check(lib().reg_set_pdl(self.h, 1 if enable else 0))
 
     def set_tiles(self, R, C, P=0):
         """Launch with R rows per row-kernel CTA, C spectrum columns per column-kernel CTA and

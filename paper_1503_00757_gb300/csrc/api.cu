@@ -150,15 +150,16 @@ extern "C" int reg_create(reg_grid grid, int nt, int regnorm, double beta, doubl
     c->stream = 0;
     c->launches = 0;
     c->tileR = c->tileC = c->tileP = 0;
+    c->pdl = true;
     {
-        int dev = 0, R, C, P;
-        if (cudaGetDevice(&dev) == cudaSuccess && tuned_tiles(dev, c->n1, c->n2, &R, &C, &P)) {
+        int dev = 0, R, C, P, D;
+        if (cudaGetDevice(&dev) == cudaSuccess && tuned_tiles(dev, c->n1, c->n2, &R, &C, &P, &D)) {
             c->tileR = R;
             c->tileC = C;
             c->tileP = P;
+            c->pdl = D != 0;
         }
     }
-    c->pdl = true;
     c->use_graphs = true;
     c->timing = false;
     for (int k = 0; k < KC_COUNT; ++k) { c->tcount[k] = 0; c->tms[k] = 0.0; c->tbytes[k] = 0.0; }
@@ -224,6 +225,14 @@ extern "C" int reg_set_tiles(reg_ctx* c, int rows_per_cta, int cols_per_cta, int
     c->tileR = rows_per_cta;
     c->tileC = cols_per_cta;
     c->tileP = prefetch;
+    return REG_OK;
+}
+
+extern "C" int reg_set_pdl(reg_ctx* c, int enable) {
+    if (!c) return reg_fail(REG_ERR_ARG, "ctx is NULL");
+    const bool on = enable != 0;
+    if (on != c->pdl) clear_graphs(c);  // captures bake in the launch attribute
+    c->pdl = on;
     return REG_OK;
 }
 

@@ -68,8 +68,8 @@ extern "C" int reg_executor_solve(reg_executor* ex, reg_batch_item* items, int c
         std::map<std::pair<int, int>, int> sizes;
         for (int i = 0; i < count; ++i) sizes[std::make_pair(items[i].grid.n1, items[i].grid.n2)] = 1;
         for (const auto& kv : sizes) {
-            const int st = reg_autotune(reg_grid{kv.first.first, kv.first.second}, 4, std::min(nworkers, 8), 0,
-                                        nullptr, nullptr, nullptr, nullptr);
+            const int st = reg_autotune(reg_grid{kv.first.first, kv.first.second}, 8, std::min(nworkers, 8), 0,
+                                        nullptr, nullptr, nullptr, nullptr, nullptr);
             if (st != REG_OK) return st;
         }
     }

@@ -127,8 +127,8 @@ struct reg_ctx {
 // ---- FFT tile choices (kernels.cu: defaults and limits; tune.cu: autotuner table) ----
 void default_tiles(int n1, int n2, int* R, int* C, int* P);
 bool tiles_valid(int n1, int n2, int R, int C, int P);
-// tuned (R, C, P) for this device and grid, if reg_autotune has measured it
-bool tuned_tiles(int dev, int n1, int n2, int* R, int* C, int* P);
+// tuned (R, C, P, D) for this device and grid, if reg_autotune has measured it (D: launch with PDL)
+bool tuned_tiles(int dev, int n1, int n2, int* R, int* C, int* P, int* D);
 
 // ---- launchers (kernels.cu); all asynchronous on ctx->stream ----
 cudaError_t k_init_twiddles(reg_ctx* ctx);

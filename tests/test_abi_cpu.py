@@ -75,10 +75,11 @@ def test_new_entry_points_reject_invalid_arguments_without_gpu(lib):
     assert lib.reg_spectral_grad_static(reg_grid(12, 16), None, None, None) == 1
     # autotuner: grid and nt checked before any CUDA call
     R, C, P, ms = ctypes.c_int(), ctypes.c_int(), ctypes.c_int(), ctypes.c_double()
-    assert lib.reg_autotune(reg_grid(96, 64), 4, 1, 0, ctypes.byref(R), ctypes.byref(C), ctypes.byref(P),
+    assert lib.reg_autotune(reg_grid(96, 64), 4, 1, 0, ctypes.byref(R), ctypes.byref(C), ctypes.byref(P), None,
                             ctypes.byref(ms)) == 1
-    assert lib.reg_autotune(reg_grid(64, 64), 0, 1, 0, None, None, None, None) == 1
-    assert lib.reg_autotune(reg_grid(64, 64), 4, 17, 0, None, None, None, None) == 1
-    assert lib.reg_tile_config(None, ctypes.byref(R), ctypes.byref(C), ctypes.byref(P)) == 1
+    assert lib.reg_autotune(reg_grid(64, 64), 0, 1, 0, None, None, None, None, None) == 1
+    assert lib.reg_autotune(reg_grid(64, 64), 4, 17, 0, None, None, None, None, None) == 1
+    assert lib.reg_tile_config(None, ctypes.byref(R), ctypes.byref(C), ctypes.byref(P), None) == 1
     assert lib.reg_set_tiles(None, 4, 2, 0) == 1
     assert lib.reg_net_set_output_scale(None, ctypes.c_float(1.0)) == 1
+    assert lib.reg_set_pdl(None, 1) == 1

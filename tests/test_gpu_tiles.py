@@ -60,7 +60,8 @@ def test_every_tile_choice_gives_identical_results(n1, n2):
     assert len(cands) >= 2
     for R, C, P in cands:
         ctx.set_tiles(R, C, P)
-        assert ctx.tile_config() == (R, C, P)
+        assert ctx.tile_config()[:3] == (R, C, P)
+        ctx.set_pdl(R % 8 == 0)  # both launch modes give the same results too
         g, h = torch.empty_like(g0), torch.empty_like(h0)
         torch.cuda.synchronize()
         J = ctx.gradient(vd, g)
@@ -89,11 +90,11 @@ def test_invalid_tiles_rejected():
 def test_autotune_picks_a_valid_pair_used_by_later_contexts():
     from paper_1503_00757_gb300.binding import Context, autotune
     for conc in (1, 3):
-        R, C, P, ms = autotune(128, 256, nt=4, concurrency=conc, force=True)
-        assert (R, C, P) in valid_tiles(128, 256)
+        R, C, P, D, ms = autotune(128, 256, nt=4, concurrency=conc, force=True)
+        assert (R, C, P) in valid_tiles(128, 256) and D in (0, 1)
         assert ms > 0.0
         ctx = Context(128, 256, 4)
-        assert ctx.tile_config() == (R, C, P)
+        assert ctx.tile_config() == (R, C, P, D)
         ctx.close()
-        R2, C2, P2, ms2 = autotune(128, 256, nt=4)
-        assert (R2, C2, P2) == (R, C, P) and ms2 < 0.0  # cached
+        R2, C2, P2, D2, ms2 = autotune(128, 256, nt=4)
+        assert (R2, C2, P2, D2) == (R, C, P, D) and ms2 < 0.0  # cached
