@@ -113,7 +113,7 @@ def run_batched_mixed(dev, stream, opts, nworkers=16):
     gen_s = time.perf_counter() - t0
     tiles = {}
     for n in C4_SIZES:
-        R, C, P, D, ms = autotune(n, n, nt=8, concurrency=8)
+        R, C, P, D, ms = autotune(n, n, nt=8, concurrency=8, force=True)
         tiles[str(n)] = {"rows_per_cta": R, "cols_per_cta": C, "prefetch": P, "pdl": D}
     pairs = []
     for s, (a, b) in zip(specs, imgs):
@@ -384,6 +384,11 @@ def main():
         ms_step = aggregate_ms(total_ms / args.steps, world, dist if world > 1 else None, dev)
         value = throughput(ms_step, world)
 
+        # single-stream measurements (one registration alone, matvecs/s) with the tiles and launch mode
+        # tuned for one solve at a time
+        sR, sC, sP, sD, _ = autotune(N_GRID, N_GRID, nt=8, concurrency=1, force=True)
+        ctx.set_tiles(sR, sC, sP)
+        ctx.set_pdl(sD)
         # single-registration latency (one pair alone on one stream)
         for _ in range(2):
             stats, det = single()
@@ -462,6 +467,7 @@ def main():
             nb = 1024
             from paper_1503_00757_gb300 import synth
             bT, bR, bv = synth.ellipses_pair(nb, SEED, vmax=0.049)
+            autotune(nb, nb, nt=8, concurrency=1)
             ctxb = Context(nb, nb, NT, regnorm=1, beta=BETA, gamma=math.inf, shear=0.0, stream=stream)
             ctxb.set_images(torch.from_numpy(bT.astype(np.float32)).to(dev), torch.from_numpy(bR.astype(np.float32)).to(dev))
             vb = torch.from_numpy((0.5 * bv).astype(np.float32)).to(dev).contiguous()
@@ -542,6 +548,8 @@ def main():
             "config": {"workload": WORKLOAD, "grid": [N_GRID, N_GRID], "nt": NT, "pairs_per_step": PAIRS,
                        "tiles": {"rows_per_cta": tR, "cols_per_cta": tC, "prefetch": tP, "pdl": tD,
                                  "tuned_for": f"{PAIRS} concurrent solves"},
+                       "tiles_single_stream": {"rows_per_cta": sR, "cols_per_cta": sC, "prefetch": sP, "pdl": sD,
+                                               "used_for": "latency_ms_single_registration, matvec_per_s"},
                        "l2": "flushed between steps", "parallelism": f"replicas x{world}, {PAIRS} concurrent streams",
                        "start": "zero (plain); warm start reported in warm_start_vs_plain"},
             "latency_ms_single_registration": lat,
