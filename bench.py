@@ -260,6 +260,8 @@ def main():
                     help="skip the warm-start comparison")
     ap.add_argument("--no-big", dest="big", action="store_false",
                     help="skip the 1024^2 matvec measurement")
+    ap.add_argument("--no-shear", dest="shear", action="store_false",
+                    help="skip the shear-control (nonlinear Stokes) solves")
     ap.add_argument("--no-batched", dest="batched", action="store_false",
                     help="skip the mixed-size batch (256 pairs) against the sequential loop")
     ap.add_argument("--profile", action="store_true",
@@ -526,6 +528,35 @@ def main():
                     "speedup": w_["registrations_per_s"] / z["registrations_per_s"]}
             netw.close()
             exw.close()
+        # shear-control model (nonlinear Stokes, s = -1/2: shear thickening, +1/2: shear thinning) on the
+        # C3 pair: a full solve and Hessian matvecs/s at its solution (one context, single-stream tiles)
+        shear = {}
+        if args.shear:
+            for s_ in (-0.5, 0.5):
+                cs = Context(N_GRID, N_GRID, NT, regnorm=1, beta=BETA, gamma=math.inf, shear=s_, stream=stream)
+                cs.set_images(mT, mR)
+                vsh = torch.zeros(2, N_GRID, N_GRID, device=dev)
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                sts = cs.solve(vsh, opts, check=False)
+                torch.cuda.synchronize()
+                tsol = time.perf_counter() - t0
+                gs, Hs_, vts = torch.empty_like(vsh), torch.empty_like(vsh), torch.randn_like(vsh)
+                cs.gradient(vsh, gs)
+                for _ in range(3):
+                    cs.hessian_matvec(vts, Hs_)
+                torch.cuda.synchronize()
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                for _ in range(50):
+                    cs.hessian_matvec(vts, Hs_)
+                e1.record(stream)
+                e1.synchronize()
+                shear[str(s_)] = {"nu": (1 + s_) / (1 - s_), "solve_ms": 1e3 * tsol,
+                                  "solve": {k: sts[k] for k in ("rc", "n_newton", "n_mv", "gnorm_rel", "rnorm_rel_sq")},
+                                  "matvec_per_s": 1e3 * 50 / e0.elapsed_time(e1)}
+                cs.close()
         batched_mixed = run_batched_mixed(dev, stream, opts) if (args.batched and rank == 0) else None
     dom = max(classes, key=lambda k: classes[k][1])
     n_dom, ms_dom, bytes_dom = classes[dom]
@@ -555,6 +586,7 @@ def main():
             "latency_ms_single_registration": lat,
             "warm_start_vs_plain": warm,
             "batched_mixed_vs_sequential": batched_mixed,
+            "shear_control_512": shear or None,
             "matvec_per_s": 1e3 / mv_ms, "ms_per_matvec": mv_ms,
             "solve": {k: stats[k] for k in ("n_newton", "n_mv", "n_pde", "n_ls", "gnorm_rel", "rnorm_rel_sq", "status")},
             "solve_batch": [{k: b[k] for k in ("n_newton", "n_mv", "gnorm_rel", "rc")} for b in bstats],
