@@ -506,6 +506,7 @@ struct ColArgs {
     SpecParams P;
     double* part;
     int cpb;
+    int lcpb;       // log2(cpb): cpb is a power of two (reg_set_tiles / reg_autotune limits)
     int n2;
 };
 
@@ -622,6 +623,7 @@ __global__ void __launch_bounds__(256) k_col(ColArgs a, const float2* __restrict
     extern __shared__ __align__(16) float2 sm[];
     constexpr int L = 1 << LOGL, T = L >> 3, H = L >> 1;
     const int C = a.cpb;
+    const int g_shift = a.lcpb + 2, g_mask = 4 * C - 1;  // idx -> (4-row group, column in CTA, row in group)
     const int W = a.n2 >> 1;
     float2* A = sm;
     float2* X = sm + C * L;
@@ -634,8 +636,8 @@ __global__ void __launch_bounds__(256) k_col(ColArgs a, const float2* __restrict
     for (int f = 0; f < NIN; ++f) {
         const float2* src = a.in[f];
         for (int idx = threadIdx.x; idx < C * L; idx += blockDim.x) {
-            const int g = idx / (4 * C);
-            const int rem = idx - g * 4 * C;
+            const int g = idx >> g_shift;
+            const int rem = idx & g_mask;
             const int cc = rem >> 2, rr = rem & 3;
             const size_t gi = ((size_t)g * W + e0 + cc) * 4 + rr;
             A[cc * L + 4 * g + rr] = src[gi];
@@ -704,8 +706,8 @@ __global__ void __launch_bounds__(256) k_col(ColArgs a, const float2* __restrict
         float2* dst = a.out[o];
         const float cd2 = 1.0f / (float)a.n2;
         for (int idx = threadIdx.x; idx < C * L; idx += blockDim.x) {
-            const int g = idx / (4 * C);
-            const int rem = idx - g * 4 * C;
+            const int g = idx >> g_shift;
+            const int rem = idx & g_mask;
             const int cc = rem >> 2, rr = rem & 3;
             const size_t gi = ((size_t)g * W + e0 + cc) * 4 + rr;
             float2 val = A[cc * L + 4 * g + rr];
@@ -908,6 +910,8 @@ static void launch_col_t(reg_ctx* ctx, const float2* const* in, float2* const* o
     a.P = P;
     a.part = part;
     a.cpb = cpb;
+    a.lcpb = 0;
+    while ((1 << a.lcpb) < cpb) ++a.lcpb;
     a.n2 = ctx->n2;
     ktimer_begin(ctx, KC_COL, 4.0 * (NIN + NOUT + (OP == OP_DIV1 ? 1 : 0)) * ctx->N);
     DISPATCH_LOG(ctx->log1, {
