@@ -167,10 +167,10 @@ def run_batched_mixed(dev, stream, opts, nworkers=16):
 class Clocks:
     """Samples nvidia-smi clocks and throttle reasons during the timed region."""
 
-    def __init__(self, index):
+    def __init__(self, index, directory):
         self.index = index
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{index}.csv")
+        self.path = os.path.join(directory, f"clocks_rank{index}.csv")
 
     def start(self):
         try:
@@ -255,6 +255,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--clocks-dir", default=None,
+                    help="where the nvidia-smi clock samples of the timed region are written (default: a temp dir)")
     ap.add_argument("--matvecs", type=int, default=200)
     ap.add_argument("--no-warm", dest="warm", action="store_false",
                     help="skip the warm-start comparison")
@@ -363,7 +365,8 @@ def main():
         torch.cuda.synchronize()
         barrier()
         torch.cuda.synchronize()
-        clocks = Clocks(local)
+        import tempfile
+        clocks = Clocks(local, args.clocks_dir or tempfile.gettempdir())
         clocks.start()
         total_ms = 0.0
         wall = 0.0

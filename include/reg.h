@@ -123,7 +123,7 @@ int reg_set_stream(reg_ctx* ctx, void* stream);
  * context (Eq. (e:objective), (e:init-transport-eq)). */
 int reg_set_images(reg_ctx* ctx, const float* mT, const float* mR);
 
-/* ---- rows a1-a4: spectral operators (Sec. 4, pseudospectral discretization) ---- */
+/* ---- spectral operators (Sec. 4, pseudospectral discretization) ---- */
 
 /* grad f (2*n1*n2 out) of a scalar field f; odd symbol i k with the Nyquist
  * wavenumber set to 0. */
@@ -146,7 +146,7 @@ int reg_apply_precond(reg_ctx* ctx, const float* r, float* out);
  * y = Q v for the H2 seminorm. */
 int reg_apply_precond_sqrt(reg_ctx* ctx, const float* x, float* out, int inverse);
 
-/* ---- rows a5-a7: state solve, objective, adjoint, reduced gradient ---- */
+/* ---- state solve, objective, adjoint, reduced gradient ---- */
 
 /* Forward state solve (Eq. (e:state-eq-elim)) and objective J[v]
  * (Eq. (e:objective)).  m1 (nullable) receives m(t = 1); J (nullable, host). */
@@ -156,7 +156,7 @@ int reg_objective(reg_ctx* ctx, const float* v, float* m1, double* J);
  * Fixes the linearization point for reg_hessian_matvec. */
 int reg_gradient(reg_ctx* ctx, const float* v, float* g, double* J);
 
-/* ---- rows a8-a10: Gauss-Newton Hessian matvec ---- */
+/* ---- Gauss-Newton Hessian matvec ---- */
 
 /* H v~ = beta_v B[v~] + L[b~] (Eq. (e:inc-control-eq-elim)) with the
  * Gauss-Newton approximation (lambda terms dropped, Sec. 4), at the v of the
@@ -169,7 +169,7 @@ int reg_hessian_matvec(reg_ctx* ctx, const float* vt, float* Hvt);
  * b_out (device, 2*n1*n2).  REG_ERR_STATE if neither has run. */
 int reg_body_force(reg_ctx* ctx, float* b_out);
 
-/* ---- rows a12-a13: Newton-Krylov solve (Algorithms 1 and 2) ---- */
+/* ---- Newton-Krylov solve (Algorithms 1 and 2) ---- */
 
 /* v_inout (device, 2*n1*n2): initial guess if opts->warm_start, else ignored
  * (v_0 = 0); receives the final velocity.  opts NULL = defaults.  stats
@@ -183,7 +183,7 @@ int reg_solve(reg_ctx* ctx, float* v_inout, const reg_solve_opts* opts, reg_solv
 int reg_register_host(reg_ctx* ctx, const float* mT_host, const float* mR_host, float* v_host,
                       const reg_solve_opts* opts, reg_solve_stats* stats);
 
-/* ---- row a15: batched registration of many independent pairs ---- */
+/* ---- batched registration of many independent pairs ---- */
 
 /* One pair of a batch.  Inputs: grid, nt, regnorm, beta, gamma, shear (as in
  * reg_create), mT and mR (device, n1*n2 floats each), want_detgrad (1: also
@@ -226,7 +226,7 @@ int reg_executor_create(int nworkers, reg_executor** out);
 int reg_executor_solve(reg_executor* ex, reg_batch_item* items, int count, const reg_solve_opts* opts);
 void reg_executor_destroy(reg_executor* ex);
 
-/* ---- row a15: autotuner of the FFT tiles ---- */
+/* ---- autotuner of the FFT tiles and launch mode ---- */
 
 /* Times the Gauss-Newton Hessian matvec (Algorithm 2's product with H, two
  * transport solves of nt steps) on an n1 x n2 grid with `concurrency` solves
@@ -266,14 +266,14 @@ int reg_set_tiles(reg_ctx* ctx, int rows_per_cta, int cols_per_cta, int prefetch
  * completed.  Results are identical either way. */
 int reg_set_pdl(reg_ctx* ctx, int enable);
 
-/* ---- row a14: deformation gradient (Eq. (e:def-grad)) ---- */
+/* ---- deformation gradient (Eq. (e:def-grad)) ---- */
 
 /* Transports F (F(0) = I) with v; detF (nullable, device n1*n2) receives
  * det F1; stats (host, 5 doubles) receives min, mean, max of det F1 and max,
  * mean of D = ||F1 - I||_F (Appendix F). */
 int reg_detgrad(reg_ctx* ctx, const float* v, float* detF, double* stats);
 
-/* ---- row a16: learned warm start (the paper has no learned component) ---- */
+/* ---- learned warm start (the paper has no learned component) ---- */
 
 /* An 8-layer 3x3 convolutional network with circular padding (channel
  * widths 2 -> 32 (x7) -> 2, ReLU between layers, layer l dilated by

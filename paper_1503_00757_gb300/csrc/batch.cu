@@ -1,4 +1,4 @@
-// Batched registration of many independent image pairs (row a15): a native
+// Batched registration of many independent image pairs: a native
 // host-side executor.  Pairs are independent (one registration each), so the
 // GB300 is filled by running several Newton-Krylov solves at once, each on
 // its own stream, instead of one solve at a time.

@@ -1,4 +1,4 @@
-// Learned warm start (row a16): an 8-layer 3x3 convolutional network with
+// Learned warm start: an 8-layer 3x3 convolutional network with
 // circular padding (channel widths 2 -> 32 x 7 -> 2, ReLU between layers)
 // that predicts the velocity of a registration from the image pair
 // (m_T, m_R).  The middle layers are dilated (layer l samples its taps

@@ -1,4 +1,4 @@
-// Autotuner of the FFT tile choices (row a15).  The row kernels process R
+// Autotuner of the FFT tile choices.  The row kernels process R
 // grid rows per CTA and the column kernels C spectrum columns per CTA, and the
 // RK2 row kernels either prefetch their operands before waiting on the
 // preceding kernel (P = 1, more registers) or load them after the FFT (P = 0,

@@ -1,4 +1,4 @@
-"""Learned warm start for the Newton-Krylov registration (row a16).
+"""Learned warm start for the Newton-Krylov registration.
 
 Pipeline (all compute on the GPU through the C ABI):
   1. seeded synthetic pairs (``synth.ellipses_pair``) at n x n;
@@ -144,8 +144,8 @@ def main():
     ap.add_argument("--scales", default="0.5,0.6,0.7,0.8,0.9,1.0")
     ap.add_argument("--init", default=None, help="initial parameters (.npy, flat FP32); default: He initialisation")
     ap.add_argument("--eval-only", action="store_true", help="no training: calibrate and evaluate --init")
-    ap.add_argument("--out", default="gpurun_out/warmstart.json")
-    ap.add_argument("--weights", default="gpurun_out/warmstart_weights.npy")
+    ap.add_argument("--out", default="warmstart.json")
+    ap.add_argument("--weights", default="warmstart_weights.npy")
     args = ap.parse_args()
     log = lambda m: print(m, flush=True)
     n = args.n

@@ -1,4 +1,4 @@
-"""Batched registration (reg_solve_batch, row a15): every pair of a mixed-size,
+"""Batched registration (reg_solve_batch): every pair of a mixed-size,
 mixed-setting batch solved concurrently must equal its standalone reg_solve
 bit for bit (same kernels, same order, per-pair streams)."""
 import math

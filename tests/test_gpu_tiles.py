@@ -1,4 +1,4 @@
-"""FFT tile choices and their autotuner (row a15): every valid (rows per row
+"""FFT tile choices and their autotuner: every valid (rows per row
 CTA, spectrum columns per column CTA, operand prefetch) gives the same
 gradient and Hessian matvec bit for bit (each row and column transform is the
 same code whatever the CTA holds; only FP64 reduction order may change J in
