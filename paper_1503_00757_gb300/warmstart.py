@@ -109,6 +109,17 @@ def summarize(stats, seconds):
             "seconds": seconds, "registrations_per_s": len(stats) / seconds}
 
 
+CHANNELS = (2, 32, 32, 32, 32, 32, 32, 32, 2)
+
+
+def he_init(seed, channels=CHANNELS):
+    """Initial network parameters: W ~ N(0, 2 / (9 Cin)) per layer (He), b = 0, as a list of
+    (W (Cout, Cin, 3, 3), b (Cout,)) in the layout reg_net_set_params flattens."""
+    rng = np.random.default_rng(seed)
+    return [(rng.standard_normal((cout, cin, 3, 3)) * np.sqrt(2.0 / (9.0 * cin)), np.zeros(cout))
+            for cin, cout in zip(channels[:-1], channels[1:])]
+
+
 def calibrate_scale(net, images, executor, scales, batch, log=None):
     """Output scale s of the warm start s P G net(x) with the fewest mean Hessian matvecs on
     the given (validation) pairs; ties go to the larger s.  Returns (s, table)."""
@@ -129,7 +140,6 @@ def calibrate_scale(net, images, executor, scales, batch, log=None):
 
 def main():
     import torch
-    from oracle import cnn as oracle_cnn  # initial parameters only (He initialisation)
     from .binding import Executor, Net, default_opts, flatten_params
 
     ap = argparse.ArgumentParser()
@@ -159,7 +169,7 @@ def main():
     if args.init:
         p0 = torch.from_numpy(np.load(args.init).astype(np.float32)).cuda()
     else:
-        p0 = torch.tensor(flatten_params(oracle_cnn.init_params(1)), dtype=torch.float32, device="cuda")
+        p0 = torch.tensor(flatten_params(he_init(1)), dtype=torch.float32, device="cuda")
     net.set_params(p0)
     res = {"n": n, "nt": NT, "beta_v": BETA, "test_pairs": args.test, "val_pairs": args.val}
     if not args.eval_only:
