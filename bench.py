@@ -268,11 +268,26 @@ def main():
                     help="skip the mixed-size batch (256 pairs) against the sequential loop")
     ap.add_argument("--profile", action="store_true",
                     help="run --warmup registrations then one registration and exit (for ncu launch lists)")
+    ap.add_argument("--profile-net", action="store_true",
+                    help="run 4 training steps of the warm-start network (256^2, batch 8) and exit (for ncu)")
     ap.add_argument("--profile-grid", type=int, default=0,
                     help="with --profile: instead run a gradient and 3 GN matvecs on this grid (nt=32)")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
+        return
+    if args.profile_net:
+        import torch
+        from paper_1503_00757_gb300 import warmstart as ws
+        from paper_1503_00757_gb300.binding import Net, flatten_params
+        x = torch.from_numpy(ws.make_images(256, range(ws.TRAIN_SEED, ws.TRAIN_SEED + 8))).cuda().contiguous()
+        t = torch.zeros(8, 2, 256, 256, device="cuda")
+        net = Net(256, 256, 8)
+        net.set_params(torch.tensor(flatten_params(ws.he_init(1)), dtype=torch.float32, device="cuda"))
+        losses = [net.train_step(x, t, 1e-3) for _ in range(4)]
+        torch.cuda.synchronize()
+        print(json.dumps({"profile_net": True, "losses": losses}))
+        net.close()
         return
 
     import torch
