@@ -174,7 +174,12 @@ int reg_body_force(reg_ctx* ctx, float* b_out);
 /* v_inout (device, 2*n1*n2): initial guess if opts->warm_start, else ignored
  * (v_0 = 0); receives the final velocity.  opts NULL = defaults.  stats
  * (nullable, host).  Returns REG_OK, REG_ERR_LINESEARCH, REG_ERR_MAXIT,
- * REG_ERR_NAN or an argument/CUDA error. */
+ * REG_ERR_NAN or an argument/CUDA error.  With the H2 seminorm (and no shear
+ * term) the iteration runs on y = Q v, Q = (beta_v A')^(1/2) (see
+ * reg_apply_precond_sqrt): the same Algorithms 1 and 2, with PCG on v
+ * becoming unpreconditioned CG on y and every test taken on v-space norms,
+ * so that the FP32 rounding of v is not amplified by beta_v |k|^4 in the
+ * gradient. */
 int reg_solve(reg_ctx* ctx, float* v_inout, const reg_solve_opts* opts, reg_solve_stats* stats);
 
 /* Same solve with HOST buffers: copies m_T, m_R (host, n1*n2 floats) to the
