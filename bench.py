@@ -72,6 +72,30 @@ def peaks():
     return 6800.0, "fallback"
 
 
+def matvec_models(n1, n2, nt, ms, hbm_gbs, fp32_tflops):
+    """One Gauss-Newton Hessian matvec taking `ms` milliseconds on an n1 x n2 grid with nt
+    time steps, against two byte models and an FFT flop model (N = n1 n2 nodes, FP32):
+      streaming  (24 nt + 40) N bytes: a time step fully on chip, so that each of the two
+                 sweeps reads the state history once and round-trips one state per step;
+      fft_pass   280 nt N bytes: every 2-D FFT pass (about 15 real 2-D transforms per step,
+                 16 N bytes each) and the pointwise work (about 40 N) through memory;
+      flops      the transforms of the 4 nt RK2 stages (incremental state and adjoint, two
+                 stages per step), 5 n log2 n flop per complex transform of length n: per
+                 stage one column transform pair over n2/2 spectrum columns (5 N log2 n1)
+                 and 1.5 row transforms' worth over the n1 rows (7.5 N log2 n2).
+    Returns bytes or flops, the achieved rate and its fraction of the given ceiling."""
+    N = n1 * n2
+    sec = ms * 1e-3
+    out = {"ms_per_matvec": ms}
+    for name, byt in (("streaming", (24 * nt + 40) * N), ("fft_pass", 280 * nt * N)):
+        gbs = byt / sec / 1e9
+        out[name] = {"bytes": byt, "GB/s": gbs, "frac_hbm": gbs / hbm_gbs}
+    fl = 4 * nt * (5 * math.log2(n1) + 7.5 * math.log2(n2)) * N
+    tf = fl / sec / 1e12
+    out["flops"] = {"flop": fl, "TFLOP/s": tf, "frac_fp32": (tf / fp32_tflops) if fp32_tflops else None}
+    return out
+
+
 def images(seed=SEED):
     from paper_1503_00757_gb300 import synth
     mT, mR, _ = synth.ellipses_pair(N_GRID, seed, vmax=VMAX)
@@ -576,6 +600,8 @@ def main():
                                   "matvec_per_s": 1e3 * 50 / e0.elapsed_time(e1)}
                 cs.close()
         batched_mixed = run_batched_mixed(dev, stream, opts) if (args.batched and rank == 0) else None
+    from paper_1503_00757_gb300.binding import fp32_peak
+    fp32_tf, _ = fp32_peak()
     dom = max(classes, key=lambda k: classes[k][1])
     n_dom, ms_dom, bytes_dom = classes[dom]
     peak, peak_kind = peaks()
@@ -621,6 +647,10 @@ def main():
                                           "achieved": big["roofline"]["achieved"], "peak": peak,
                                           "frac": big["roofline"]["achieved"] / peak, "unit": "GB/s"},
                              "kernel_classes": big["kernel_classes"]} if big else None),
+            "ceilings": {"fp32_tflops_measured": fp32_tf, "hbm_gbs": peak,
+                         "matvec_512": matvec_models(N_GRID, N_GRID, NT, mv_ms, peak, fp32_tf),
+                         "matvec_1024": (matvec_models(1024, 1024, NT, big["ms_per_matvec"], peak, fp32_tf)
+                                         if big else None)},
             "kernel_classes": {names[k]: {"launches": classes[k][0], "ms": classes[k][1],
                                           "GB": classes[k][2] / 1e9} for k in classes},
             "clocks": clk,

@@ -271,6 +271,22 @@ int reg_set_tiles(reg_ctx* ctx, int rows_per_cta, int cols_per_cta, int prefetch
  * completed.  Results are identical either way. */
 int reg_set_pdl(reg_ctx* ctx, int enable);
 
+/* ---- arithmetic ceiling ---- */
+
+/* FP32 FMA throughput of the current device, measured.  Not an operation of
+ * the method: it is the arithmetic ceiling of the transform and RK2 kernels
+ * (the pseudospectral FFTs and transport updates of Sec. 4 run in FP32 on the
+ * CUDA cores), against which a matvec's FFT flop count is compared.  One wave
+ * of 256-thread CTAs (SM count x CTAs resident per SM); each thread runs 16
+ * independent FMA recurrences of 2048 steps.  After two warm-up launches,
+ * three windows of five launches are timed with CUDA events; *tflops
+ * (host, required) = 2 x FMAs per launch / the best window's time per launch,
+ * in TFLOP/s; *ms_per_launch (host, nullable) = that time.  Runs on a stream
+ * of its own, which it synchronizes; allocates 4 bytes of device memory for
+ * the duration of the call.  REG_ERR_ARG if tflops is NULL, REG_ERR_NOMEM or
+ * REG_ERR_CUDA if a CUDA call fails. */
+int reg_fp32_peak(double* tflops, double* ms_per_launch);
+
 /* ---- deformation gradient (Eq. (e:def-grad)) ---- */
 
 /* Transports F (F(0) = I) with v; detF (nullable, device n1*n2) receives

@@ -84,6 +84,7 @@ _SIGS = {
     "reg_tile_config": ([_P, ctypes.POINTER(_I), ctypes.POINTER(_I), ctypes.POINTER(_I), ctypes.POINTER(_I)], _I),
     "reg_set_tiles": ([_P, _I, _I, _I], _I),
     "reg_set_pdl": ([_P, _I], _I),
+    "reg_fp32_peak": ([ctypes.POINTER(_D), ctypes.POINTER(_D)], _I),
     "reg_net_create": ([_I, _I, _I, ctypes.POINTER(_P)], _I),
     "reg_net_destroy": ([_P], None),
     "reg_net_num_params": ([_P], ctypes.c_longlong),
@@ -164,6 +165,14 @@ def autotune(n1, n2, nt=4, concurrency=1, force=False):
     _check(lib().reg_autotune(reg_grid(n1, n2), nt, concurrency, 1 if force else 0, ctypes.byref(R), ctypes.byref(C),
                               ctypes.byref(P), ctypes.byref(D), ctypes.byref(ms)))
     return R.value, C.value, P.value, D.value, ms.value
+
+
+def fp32_peak():
+    """Measured FP32 FMA throughput of the current device (reg_fp32_peak):
+    (TFLOP/s, ms per launch of the FMA kernel)."""
+    tf, ms = ctypes.c_double(), ctypes.c_double()
+    _check(lib().reg_fp32_peak(ctypes.byref(tf), ctypes.byref(ms)))
+    return tf.value, ms.value
 
 
 def _batch_items(pairs):

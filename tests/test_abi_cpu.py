@@ -78,6 +78,8 @@ def test_new_entry_points_reject_invalid_arguments_without_gpu(lib):
     assert lib.reg_autotune(reg_grid(96, 64), 4, 1, 0, ctypes.byref(R), ctypes.byref(C), ctypes.byref(P), None,
                             ctypes.byref(ms)) == 1
     assert lib.reg_autotune(reg_grid(64, 64), 0, 1, 0, None, None, None, None, None) == 1
+    # FP32 peak: the output pointer is checked before any CUDA call
+    assert lib.reg_fp32_peak(None, None) == 1
     assert lib.reg_autotune(reg_grid(64, 64), 4, 17, 0, None, None, None, None, None) == 1
     assert lib.reg_tile_config(None, ctypes.byref(R), ctypes.byref(C), ctypes.byref(P), None) == 1
     assert lib.reg_set_tiles(None, 4, 2, 0) == 1
