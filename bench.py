@@ -30,9 +30,9 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "registrations/sec and Hessian matvecs/sec at 512² nt=32; warm-start vs plain"
-PAIRS = 5  # independent C3 pairs per step (seeds 3000..3004), solved concurrently
+PAIRS = 5  # independent 512^2 pairs per step (seeds 3000..3004), solved concurrently
 N_GRID, NT, BETA, SEED, VMAX = 512, 32, 1e-3, 3000, 0.098
-WORKLOAD = ("C3 synthetic brain-like ellipses 512x512, nt=32, H1, beta_v=1e-3, incompressible, "
+WORKLOAD = ("synthetic brain-like ellipses 512x512, nt=32, H1, beta_v=1e-3, incompressible, "
             "shear s=0, zero start, tol 1e-2; step = 5 independent pairs solved concurrently + det F1 each")
 # PDE solves of one zero-start registration of this workload as counted by
 # reg_solve on the GPU (stats n_pde: 5 Newton iterations, 38 matvecs, 5
@@ -125,7 +125,7 @@ def c4_specs():
 
 
 def run_batched_mixed(dev, stream, opts, nworkers=16):
-    """C4: the mixed batch through the executor (autotuned tiles, concurrent streams) against a
+    """The mixed-size batch through the executor (autotuned tiles, concurrent streams) against a
     sequential per-pair loop of the same library (one context per grid size, one pair at a time)."""
     import torch
     from paper_1503_00757_gb300 import synth
@@ -180,7 +180,7 @@ def run_batched_mixed(dev, stream, opts, nworkers=16):
     ex.close()
     ok_b = sum(1 for s in st_b if s["rc"] == 0)
     ok_s = sum(1 for s in st_s if s["rc"] == 0)
-    return {"workload": "C4 mixed batch: 256 pairs, 128^2:256^2:512^2 = 147:73:36, nt=16, seeded random "
+    return {"workload": "mixed batch: 256 pairs, 128^2:256^2:512^2 = 147:73:36, nt=16, seeded random "
                         "H1/H2, beta_v in {1e-2,1e-3}, beta_w in {0,1e-3,inf}, zero start, tol 1e-2",
             "batched": {"pairs_per_s": len(pairs) / sec_b, "seconds": sec_b, "converged": ok_b, "workers": nworkers},
             "sequential": {"pairs_per_s": len(pairs) / sec_s, "seconds": sec_s, "converged": ok_s},
@@ -544,7 +544,7 @@ def main():
                                           "pointwise/reduction"][bd], "achieved": ach, "launches": bcls[bd][0]}
             big["kernel_classes"] = {str(k): {"launches": bcls[k][0], "ms": bcls[k][1], "GB": bcls[k][2] / 1e9}
                                      for k in bcls}
-        # learned warm start vs plain zero start (C5 workload, 256^2, nt=16) with the committed weights
+        # learned warm start vs plain zero start (256^2, nt=16, held-out pairs) with the committed weights
         warm = None
         wpath = os.path.join(ROOT, "paper_1503_00757_gb300", "weights", "warmstart_n256.npy")
         if args.warm and os.path.exists(wpath):
@@ -564,14 +564,14 @@ def main():
             sp = time.perf_counter() - t0
             _, st1, s1 = ws.solve_all(xw, exw, default_opts(tol=1e-2, warm_start=1), v0=vp)
             z, w_ = ws.summarize(st0, s0), ws.summarize(st1, s1 + sp)
-            warm = {"workload": "C5 256x256, nt=16, H1, beta_v=1e-3, incompressible, 16 held-out pairs, tol 1e-2",
+            warm = {"workload": "learned warm start 256x256, nt=16, H1, beta_v=1e-3, incompressible, 16 held-out pairs, tol 1e-2",
                     "output_scale": wscale,
                     "plain": z, "warm": w_, "matvec_reduction": 1.0 - w_["matvec_mean"] / z["matvec_mean"],
                     "speedup": w_["registrations_per_s"] / z["registrations_per_s"]}
             netw.close()
             exw.close()
         # shear-control model (nonlinear Stokes, s = -1/2: shear thickening, +1/2: shear thinning) on the
-        # C3 pair: a full solve and Hessian matvecs/s at its solution (one context, single-stream tiles)
+        # first 512^2 pair: a full solve and Hessian matvecs/s at its solution (one context, single-stream tiles)
         shear = {}
         if args.shear:
             for s_ in (-0.5, 0.5):
