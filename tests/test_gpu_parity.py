@@ -418,3 +418,85 @@ def test_precision_config_full_size():
     assert st["status"] == 0 and st["gnorm_rel"] <= 1e-2 and st["J"] < st["J0"]
     assert st["cfl"] <= 0.25 + 1e-9 and st["nt_used"] >= 16
     ctx.close()
+
+
+def test_registration_workload_at_full_size():
+    """The benchmark's registration workload at its full size, in the launch configuration the
+    benchmark times. Workload: 512^2, nt = 32, H1, incompressible, beta_v = 1e-3, its first
+    seeded image pair. Launch configuration: 4 rows per row CTA, 2 columns per column CTA,
+    operand prefetch, programmatic dependent launch, CUDA graphs on a non-default stream.
+
+    Element by element against the FP64 oracle: the state solve (m_1 and J).
+
+    Properties that hold at any size:
+    * the reduced gradient against central differences of J, in the L2 inner product of the
+      grid (weight h1 h2);
+    * the Gauss-Newton matvec against central differences of the gradient at a zero-residual
+      point (m_R := m_1(v)), where Gauss-Newton equals the full Hessian;
+    * linearity of the matvec: exact for a factor 2, to FP32 rounding for a sum.
+
+    Tolerances. The oracle's own mismatch of the two difference checks at this size is
+    1.5e-4 (gradient) and 8.5e-5 (matvec): the O(h_t^2) consistency of the
+    optimize-then-discretize derivatives. FP32 rounding adds about 1e-5 to the differences."""
+    import torch
+    from paper_1503_00757_gb300.binding import Context
+    n, nt, beta = 512, 32, 1e-3
+    mT, mR, vs = synth.ellipses_pair(n, 3000, vmax=0.098)
+    v = 0.5 * vs
+    vt = synth.velocity(n, n, 16, 0.3, np.random.default_rng(7))
+    w = synth.velocity(n, n, 8, 0.2, np.random.default_rng(8), grad_fraction=0.5)
+    J_ref, m_ref = Registration(mT, mR, nt, regnorm=1, beta_v=beta, beta_w=math.inf).objective(v)
+
+    stream = torch.cuda.Stream()
+    ctx = Context(n, n, nt, regnorm=1, beta=beta, gamma=math.inf, stream=stream)
+    ctx.set_tiles(4, 2, 1)
+    ctx.set_pdl(True)
+    mTd, mRd, vd, vtd, wd = to_gpu(mT), to_gpu(mR), to_gpu(v), to_gpu(vt), to_gpu(w)
+    m1 = torch.empty(n, n, device="cuda")
+    g = torch.empty(2, n, n, device="cuda")
+    torch.cuda.synchronize()
+    ctx.set_images(mTd, mRd)
+    J = ctx.objective(vd, m1)
+    stream.synchronize()
+    assert rel_l2(to_np(m1), m_ref[-1]) < OP_TOL
+    assert abs(J - J_ref) < OP_TOL * abs(J_ref)
+
+    # gradient vs central differences of J along d = g / |g|. Every device input is made on
+    # the default stream and synchronized before the context's stream reads it.
+    h2 = (2 * math.pi / n) ** 2
+    ctx.gradient(vd, g)
+    stream.synchronize()
+    gn = to_np(g)
+    d = gn / np.linalg.norm(gn)
+    eps = 1e-2 * np.linalg.norm(v)
+    vp, vm = to_gpu(v + eps * d), to_gpu(v - eps * d)
+    torch.cuda.synchronize()
+    Jp = ctx.objective(vp)
+    Jm = ctx.objective(vm)
+    fd = (Jp - Jm) / (2 * eps)
+    gd = h2 * float(np.sum(gn * d))
+    assert abs(fd - gd) < 2e-3 * abs(gd), (fd, gd)
+
+    # zero residual: m_R := m_1(v); matvecs at v, then central differences of the gradient
+    e = 1e-2 * np.linalg.norm(v) / np.linalg.norm(vt)
+    mR0 = m1.clone()
+    vt2, vtw = 2.0 * vtd, vtd + wd
+    vep, vem = to_gpu(v + e * vt), to_gpu(v - e * vt)
+    Hv, H2v, Hw, Hvw = (torch.empty(2, n, n, device="cuda") for _ in range(4))
+    gp, gm = torch.empty_like(g), torch.empty_like(g)
+    torch.cuda.synchronize()
+    ctx.set_images(mTd, mR0)
+    ctx.gradient(vd, g)
+    ctx.hessian_matvec(vtd, Hv)
+    ctx.hessian_matvec(vt2, H2v)
+    ctx.hessian_matvec(wd, Hw)
+    ctx.hessian_matvec(vtw, Hvw)
+    stream.synchronize()
+    assert torch.equal(H2v, 2.0 * Hv)
+    assert rel_l2(to_np(Hvw), to_np(Hv) + to_np(Hw)) < OP_TOL
+    ctx.gradient(vep, gp)
+    ctx.gradient(vem, gm)
+    stream.synchronize()
+    fdH = (to_np(gp) - to_np(gm)) / (2 * e)
+    assert rel_l2(fdH, to_np(Hv)) < 1e-3
+    ctx.close()
