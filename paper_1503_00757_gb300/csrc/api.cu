@@ -860,7 +860,7 @@ extern "C" int reg_solve(reg_ctx* c, float* v, const reg_solve_opts* opts, reg_s
     const long long n2N = 2 * (long long)c->N;
     const size_t vb = sizeof(float) * n2N;
     int n_pde = 0;
-    double gref;
+    double gref = 0.0;
     if (!o.warm_start) launch_fill(c, n2N, v, 0.f);
     // Quadratic H2 regularization iterates on y = Q v (Q^2 = beta_v A' is the
     // preconditioner): the FP32 rounding of v, amplified by beta_v |k|^4 in the

@@ -922,10 +922,7 @@ static void launch_col_t(reg_ctx* ctx, const float2* const* in, float2* const* o
     ktimer_end(ctx);
 }
 
-int col_blocks(reg_ctx* ctx) {
-    const int L = ctx->n1, W = ctx->n2 / 2;
-    return W / cols_per_cta(ctx);
-}
+int col_blocks(reg_ctx* ctx) { return (ctx->n2 / 2) / cols_per_cta(ctx); }
 
 void launch_col(reg_ctx* ctx, int op, const float2* const* in, float2* const* out, const SpecParams& P,
                 double* part) {
