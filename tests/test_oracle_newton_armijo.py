@@ -12,7 +12,11 @@ backtracked from 1 by halving:
 * s = 4: rejected at 1 and 1/2, exact at 1/4;
 * s = 1/2 (half step): accepted at a = 1, and ||g|| halves every iteration;
 * s = -1 (ascent direction): replaced by -P^-1 g, which is exact here;
-* c1 > 1: no step can satisfy the rule."""
+* c1 > 1: no step can satisfy the rule.
+
+Algorithm 2's PCG runs on a diagonal operator with k distinct eigenvalues. There CG must
+terminate after exactly k iterations, since the Krylov space is then exhausted. With the exact
+inverse as preconditioner it must terminate after one."""
 import math
 
 import numpy as np
@@ -105,3 +109,41 @@ def test_warm_start_keeps_the_zero_start_reference():
     assert abs(st["gnorm_rel"] - 2.0 ** -7) < 1e-12
     # the forcing term is relative to the gradient at the warm start
     assert P.etas[0] == 0.5 and abs(P.etas[2] - 0.5) < 1e-12 and abs(P.etas[3] - math.sqrt(0.125)) < 1e-12
+
+
+class Diagonal(Registration):
+    """A Registration whose Hessian is a diagonal operator with a chosen set of eigenvalues
+    and whose preconditioner is chosen per test; Algorithm 2's loop is the oracle's own."""
+
+    def __init__(self, eigs, n=16, precond_exact=False, seed=1):
+        rng = np.random.default_rng(seed)
+        self.lam = rng.choice(np.asarray(eigs, dtype=np.float64), size=(2, n, n))
+        self.lam.flat[: len(eigs)] = eigs  # every eigenvalue present
+        self.exact = precond_exact
+        self.n_pde = 0
+
+    def matvec(self, vt):
+        return self.lam * vt
+
+    def precond(self, r):
+        return r / self.lam if self.exact else r
+
+
+@pytest.mark.parametrize("eigs", [[2.0], [1.0, 3.0], [0.5, 2.0, 7.0], [1.0, 2.0, 4.0, 8.0, 16.0]])
+def test_pcg_terminates_after_as_many_iterations_as_distinct_eigenvalues(eigs):
+    # the Krylov space of a matrix with k distinct eigenvalues is exhausted after k steps
+    P = Diagonal(eigs)
+    g = np.random.default_rng(2).standard_normal(P.lam.shape)
+    vt, it, relres, hit = P.pcg(g, 1e-10, 50)
+    assert it == len(eigs) and not hit and relres < 1e-10
+    assert np.abs(vt + g / P.lam).max() < 1e-9 * np.abs(g / P.lam).max()
+
+
+def test_pcg_with_the_exact_preconditioner_takes_one_iteration_and_caps():
+    P = Diagonal([0.5, 2.0, 7.0, 11.0], precond_exact=True)
+    g = np.random.default_rng(3).standard_normal(P.lam.shape)
+    vt, it, relres, hit = P.pcg(g, 1e-10, 50)
+    assert it == 1 and not hit and np.abs(vt + g / P.lam).max() < 1e-12
+    P = Diagonal([0.5, 2.0, 7.0, 11.0])
+    vt, it, relres, hit = P.pcg(g, 1e-10, 2)
+    assert it == 2 and hit and relres > 1e-6
