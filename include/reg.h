@@ -246,9 +246,11 @@ void reg_executor_destroy(reg_executor* ex);
  * contexts keep theirs).  Valid: R a multiple of 4 dividing n1,
  * 32 <= R n2 / 8 <= 512 threads; C a power of two >= 2 dividing n2 / 2,
  * 32 <= C n1 / 8 <= 256 threads; at most 227 KB of shared memory; P = 1 only
- * for n2 <= 512.  A grid already in the table is not re-measured unless
- * force != 0 (then *ms_per_matvec < 0); *ms_per_matvec is per matvec of the
- * whole group.  Outputs are host pointers, each nullable.  Synchronous.
+ * for n2 <= 512.  Every candidate is timed in two passes and keeps its faster
+ * one.  A grid already in the table is not re-measured unless force != 0; a
+ * cached answer sets *ms_per_matvec < 0, a measured one the winner's time per
+ * matvec of the whole group.  Outputs are host pointers, each nullable.
+ * Synchronous.
  * REG_ERR_ARG for a grid outside powers of two in [16, 1024], nt outside
  * [1, 4096] or concurrency outside [1, 16]. */
 int reg_autotune(reg_grid grid, int nt, int concurrency, int force, int* rows_per_cta, int* cols_per_cta,
