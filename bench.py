@@ -255,7 +255,7 @@ def run_reference(args):
     mT, mR = images()
     pde_per_reg = PDE_PER_REG
     for _ in range(args.warmup):
-        pass  # the oracle has no warm-up effects worth paying 15 s for
+        cpu_oracle_pde_time(mT, mR)  # untimed warm-up steps
     times = [cpu_oracle_pde_time(mT, mR) for _ in range(args.steps)]
     t = float(np.mean(times))
     value = 1.0 / (t * pde_per_reg)
