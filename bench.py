@@ -4,16 +4,22 @@ Workload: synthetic "brain-like" nested smoothed ellipses (5 labels, random
 contrasts), reference = template displaced by a divergence-free velocity with
 modes |k| <= 16 (max |v| = 0.098, CFL 0.25 at nt = 32); H1 seminorm,
 incompressible (div v = 0), beta_v = 1e-3, zero start, relative gradient 1e-2.
-One step = one full Newton-Krylov registration (reg_solve: state, adjoint,
-gradient, PCG with GN matvecs, Armijo, Newton) plus det F1 (reg_detgrad).
+One step = PAIRS independent full Newton-Krylov registrations (reg_solve:
+state, adjoint, gradient, PCG with GN matvecs, Armijo, Newton) plus det F1
+(reg_detgrad) of each, solved concurrently through the batch executor.
 
 Arms:
-  default            the CUDA library through the C ABI (device-resident inputs);
-                     also e2e through reg_register_host with host buffers,
-                     a matvec throughput loop, per-kernel-class timing for the
-                     roofline and the FP64 oracle CPU baseline.
-  --impl reference   the FP64 oracle on the host cores (bounded sample).
-Multi-GPU (torchrun): independent replicas, one registration per rank
+  default            the CUDA library through the C ABI.  `value`: device-resident
+                     inputs.  `e2e`: one reg_register_host call per pair from
+                     pinned host buffers (images in, velocity out inside the call)
+                     on PAIRS host threads, each pair's context on its own stream,
+                     then det F1 from the velocity copied back in.  Also: matvec
+                     throughput (one context, and PAIRS contexts at once), the
+                     roofline of the matvec against the streaming byte model, and
+                     the FP64 oracle timed on the host cores (cpu_baseline).
+  --impl reference   the FP64 oracle on the host cores: every step, one 512^2
+                     Gauss-Newton matvec per core (a process pool).
+Multi-GPU (torchrun): independent replicas, PAIRS registrations per rank
 (pairs are independent), value = all ranks' registrations / max time.
 """
 import argparse
@@ -34,10 +40,11 @@ PAIRS = 5  # independent 512^2 pairs per step (seeds 3000..3004), solved concurr
 N_GRID, NT, BETA, SEED, VMAX = 512, 32, 1e-3, 3000, 0.098
 WORKLOAD = ("synthetic brain-like ellipses 512x512, nt=32, H1, beta_v=1e-3, incompressible, "
             "shear s=0, zero start, tol 1e-2; step = 5 independent pairs solved concurrently + det F1 each")
-# PDE solves of one zero-start registration of this workload as counted by
-# reg_solve on the GPU (stats n_pde: 5 Newton iterations, 38 matvecs, 5
-# line-search evaluations); scales the oracle's per-PDE-solve time to a
-# registration in the reference arm, which runs without a GPU.
+# PDE solves of one zero-start registration of this workload's first pair as
+# counted by reg_solve on the GPU (stats n_pde: 5 Newton iterations, 38 matvecs,
+# 5 line-search evaluations): the matvec equivalents (n_pde / 2) that turn the
+# oracle's measured matvecs/s into registrations/s in the reference arm, which
+# runs without a GPU.
 PDE_PER_REG = 93
 
 
@@ -96,15 +103,87 @@ def matvec_models(n1, n2, nt, ms, hbm_gbs, fp32_tflops):
     return out
 
 
+def stream_bytes(n1, n2, nt):
+    """Algorithmic bytes of one Gauss-Newton matvec, the minimal streaming model (FP32): the
+    two transport sweeps each read the state history once (2 (nt+1) fields), round-trip one
+    state per step (2 nt x 2 fields), and v, v~ are read and H v~ written (about 10 fields):
+    about (24 nt + 40) N bytes, N = n1 n2."""
+    return (24 * nt + 40) * n1 * n2
+
+
+# DRAM bytes (read + write) per Gauss-Newton matvec at 512^2, nt = 32, summed over its kernels
+# from an ncu capture of the current kernels (dram__bytes_read.sum + dram__bytes_write.sum); None
+# until a capture of the current kernels has been taken.
+MATVEC_TRAFFIC_512 = None
+
+
+def roofline(bytes_per_matvec, conc, ms_single, peak, peak_kind):
+    """The matvec against the HBM roofline: algorithmic bytes (streaming model) per matvec
+    times the matvecs completed, over the CUDA-event time of the window, with PAIRS contexts
+    issuing matvecs at once (the concurrency of the registration step); the same for one
+    context alone."""
+    ach = bytes_per_matvec * conc["matvec_per_s"] / 1e9
+    ach1 = bytes_per_matvec / ms_single / 1e6
+    return {"bound": "hbm", "unit": "GB/s", "kernel": "Gauss-Newton matvec (all its kernels)",
+            "bytes_per_matvec": bytes_per_matvec, "achieved": ach, "peak": peak, "peak_kind": peak_kind,
+            "frac": ach / peak, "mode": f"{conc['contexts']} contexts issuing matvecs concurrently",
+            "single_context": {"achieved": ach1, "frac": ach1 / peak, "ms_per_matvec": ms_single},
+            "traffic": MATVEC_TRAFFIC_512}
+
+
+def matvec_concurrent(dev, pairs, opts, nmv):
+    """Gauss-Newton matvecs/s with one context per pair (each linearized at its pair's current
+    velocity, a random direction), all issuing matvecs on their own streams at once; timed
+    with CUDA events between a fork and a join on the current stream."""
+    import torch
+    from paper_1503_00757_gb300.binding import Context
+    torch.cuda.synchronize()
+    K = len(pairs)
+    streams = [torch.cuda.Stream(device=dev) for _ in range(K)]
+    gen = torch.Generator(device=dev)
+    gen.manual_seed(11)
+    ctxs, vts, Hs = [], [], []
+    for p, s in zip(pairs, streams):
+        c = Context(N_GRID, N_GRID, NT, regnorm=1, beta=BETA, gamma=math.inf, shear=0.0, stream=s)
+        vt = torch.randn(2, N_GRID, N_GRID, device=dev, generator=gen)
+        H = torch.empty_like(vt)
+        g = torch.empty_like(vt)
+        torch.cuda.synchronize()
+        c.set_images(p["mT"], p["mR"])
+        c.gradient(p["v"], g)
+        for _ in range(3):
+            c.hessian_matvec(vt, H)
+        ctxs.append(c)
+        vts.append(vt)
+        Hs.append(H)
+    torch.cuda.synchronize()
+    cur = torch.cuda.current_stream(dev)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(cur)
+    for s in streams:
+        s.wait_event(e0)
+    for _ in range(nmv):
+        for c, vt, H in zip(ctxs, vts, Hs):
+            c.hessian_matvec(vt, H)
+    for s in streams:
+        e = torch.cuda.Event()
+        e.record(s)
+        cur.wait_event(e)
+    e1.record(cur)
+    e1.synchronize()
+    ms = e0.elapsed_time(e1)
+    for c in ctxs:
+        c.close()
+    return {"contexts": K, "matvecs": K * nmv, "ms": ms, "matvec_per_s": K * nmv * 1e3 / ms,
+            "ms_per_matvec": ms / (K * nmv)}
+
+
 def images(seed=SEED):
     from paper_1503_00757_gb300 import synth
     mT, mR, _ = synth.ellipses_pair(N_GRID, seed, vmax=VMAX)
     return mT.astype(np.float32), mR.astype(np.float32)
 
-
-# DRAM bytes (read + write) per launch of the RK2 row-stage kernel at 512^2, nt=32: the mean over
-# 8 incremental-state launches of one ncu capture (cold L2), profiles/traffic_row_stage_512_nt32.md.
-ROW_STAGE_TRAFFIC_512 = 9.99e6
 
 C4_SIZES = (128, 256, 512)
 C4_COUNTS = (147, 73, 36)  # 4 : 2 : 1 over 256 pairs
@@ -182,6 +261,7 @@ def run_batched_mixed(dev, stream, opts, nworkers=16):
     ok_s = sum(1 for s in st_s if s["rc"] == 0)
     return {"workload": "mixed batch: 256 pairs, 128^2:256^2:512^2 = 147:73:36, nt=16, seeded random "
                         "H1/H2, beta_v in {1e-2,1e-3}, beta_w in {0,1e-3,inf}, zero start, tol 1e-2",
+            "design": "multi-stream executor (host worker threads, one stream each), not a persistent launch",
             "batched": {"pairs_per_s": len(pairs) / sec_b, "seconds": sec_b, "converged": ok_b, "workers": nworkers},
             "sequential": {"pairs_per_s": len(pairs) / sec_s, "seconds": sec_s, "converged": ok_s},
             "speedup": sec_s / sec_b, "tiles": tiles, "image_generation_s": gen_s,
@@ -238,35 +318,144 @@ class Clocks:
                 "samples": len(sm)}
 
 
-def cpu_oracle_pde_time(mT, mR):
-    """Time one FP64 oracle state solve (one PDE solve) of this workload."""
-    from oracle.transport import state_solve
+# ---------------------------------------------------------------------------
+# FP64 oracle timed on the host cores (cpu_baseline and the reference arm).
+# Worker processes are started with "spawn" (a fork after the first CUDA call
+# can hang) and run one thread each (BLAS / OpenMP pools pinned to 1).
+# ---------------------------------------------------------------------------
+_ORACLE = {}
+
+
+def _oracle_init(seed):
+    """Worker set-up (untimed): the 512^2 workload's pair `seed`, its linearization point
+    v = v*/2 (the oracle's gradient: state solve, adjoint, grad m history) and a
+    band-limited direction v~."""
+    from oracle.registration import Registration
     from paper_1503_00757_gb300 import synth
-    v = 0.5 * synth.velocity(N_GRID, N_GRID, 16, VMAX, np.random.default_rng(SEED + 7))
+    mT, mR, vs = synth.ellipses_pair(N_GRID, seed, vmax=VMAX)
+    P = Registration(mT, mR, NT, regnorm=1, beta_v=BETA, beta_w=math.inf)
+    P.gradient(0.5 * vs)
+    _ORACLE["P"] = P
+    _ORACLE["vt"] = synth.velocity(N_GRID, N_GRID, 16, 0.3, np.random.default_rng(seed + 7))
+
+
+def _oracle_matvec(_):
+    """One FP64 Gauss-Newton matvec (incremental state and adjoint solves, b~, K); seconds."""
     t0 = time.perf_counter()
-    state_solve(mT.astype(np.float64), v, NT)
+    _ORACLE["P"].matvec(_ORACLE["vt"])
     return time.perf_counter() - t0
+
+
+def _oracle_register(spec):
+    """One full FP64 registration (Algorithm 1: gradient, PCG, Armijo, Newton) from zero;
+    returns (seconds, Newton iterations, matvecs, status)."""
+    from oracle.registration import Registration
+    from paper_1503_00757_gb300 import synth
+    kind, n, nt, seed, regnorm, beta, gamma, vmax = spec
+    if kind == "blobs":
+        mT, mR, _ = synth.blobs_pair(n, seed)
+    else:
+        mT, mR, _ = synth.ellipses_pair(n, seed, vmax=vmax)
+    t0 = time.perf_counter()
+    _, st = Registration(mT, mR, nt, regnorm=regnorm, beta_v=beta, beta_w=gamma).solve(tol=1e-2)
+    return time.perf_counter() - t0, st["n_newton"], st["n_mv"], st["status"]
+
+
+def _oracle_pool(workers, init_seed=None):
+    import multiprocessing as mp
+    saved = {k: os.environ.get(k) for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS")}
+    for k in saved:
+        os.environ[k] = "1"
+    try:
+        ctx = mp.get_context("spawn")
+        if init_seed is None:
+            return ctx.Pool(workers)
+        return ctx.Pool(workers, initializer=_oracle_init, initargs=(init_seed,))
+    finally:
+        for k, val in saved.items():
+            if val is None:
+                os.environ.pop(k, None)
+            else:
+                os.environ[k] = val
+
+
+def c1_specs(count):
+    """C1 plain FP64 problems: 64^2 Gaussian blobs, nt = 4, H1, div v = 0, beta_v = 1e-2 (seeds 1000+)."""
+    return [("blobs", 64, 4, 1000 + i, 1, 1e-2, math.inf, None) for i in range(count)]
+
+
+def c4_subset_specs(count):
+    """The first `count` 128^2 pairs of the mixed batch (nt = 16, their seeded settings)."""
+    out = []
+    for s in c4_specs():
+        if s["n"] == 128 and len(out) < count:
+            out.append(("ellipses", 128, C4_NT, s["seed"], s["regnorm"], s["beta"], s["gamma"], C4_VMAX[128]))
+    return out
+
+
+def cpu_oracle_baseline(pde_per_reg):
+    """The FP64 oracle as it stands, timed on this host's cores (a bounded sample, ~1 min):
+    full C1 registrations (1 core, all cores), 512^2 nt=32 Gauss-Newton matvecs (1 core:
+    3 matvecs; all cores: one per core), 16 full 128^2 registrations of the mixed batch
+    (all cores).  512^2 registrations/s = matvecs/s on all cores / (pde_per_reg / 2), the
+    matvec equivalents of one registration of the workload (a matvec is two PDE solves)."""
+    nproc = os.cpu_count() or 1
+    res = {"nproc": nproc}
+    with _oracle_pool(1) as pool:
+        ts = pool.map(_oracle_register, c1_specs(3))
+    res["c1_64_registrations_per_s_1core"] = len(ts) / sum(t[0] for t in ts)
+    with _oracle_pool(nproc) as pool:
+        t0 = time.perf_counter()
+        ts = pool.map(_oracle_register, c1_specs(2 * nproc), chunksize=1)
+        res["c1_64_registrations_per_s_allcores"] = len(ts) / (time.perf_counter() - t0)
+        t0 = time.perf_counter()
+        ts = pool.map(_oracle_register, c4_subset_specs(16), chunksize=1)
+        res["c4_128_subset_pairs_per_s_allcores"] = len(ts) / (time.perf_counter() - t0)
+        res["c4_128_subset_converged"] = sum(1 for t in ts if t[3] == 0)
+    with _oracle_pool(1, SEED) as pool:
+        ts = pool.map(_oracle_matvec, range(3))
+    res["matvec_512_per_s_1core"] = len(ts) / sum(ts)
+    with _oracle_pool(nproc, SEED) as pool:
+        pool.map(_oracle_matvec, range(nproc), chunksize=1)  # every worker has finished its set-up
+        t0 = time.perf_counter()
+        pool.map(_oracle_matvec, range(nproc), chunksize=1)
+        res["matvec_512_per_s_allcores"] = nproc / (time.perf_counter() - t0)
+    value = res["matvec_512_per_s_allcores"] / (pde_per_reg / 2.0)
+    return {"value": value, "unit": "registrations/s", "cores": nproc, "kind": "oracle",
+            "sample": (f"FP64 oracle on {nproc} host cores: {nproc} Gauss-Newton matvecs at 512^2 nt=32 (one per "
+                       f"core) timed, registrations/s = matvecs/s / {pde_per_reg / 2:g} matvec equivalents per "
+                       f"registration of this workload; also timed: full 64^2 (C1) registrations on 1 and "
+                       f"{nproc} cores, 3 matvecs on 1 core, 16 full 128^2 mixed-batch registrations"),
+            "measured": res}
 
 
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
-    mT, mR = images()
-    pde_per_reg = PDE_PER_REG
-    for _ in range(args.warmup):
-        cpu_oracle_pde_time(mT, mR)  # untimed warm-up steps
-    times = [cpu_oracle_pde_time(mT, mR) for _ in range(args.steps)]
+    nproc = os.cpu_count() or 1
+    with _oracle_pool(nproc, SEED) as pool:
+        for _ in range(max(1, args.warmup)):  # untimed: the first one also waits for every worker's set-up
+            pool.map(_oracle_matvec, range(nproc), chunksize=1)
+        times = []
+        for _ in range(args.steps):
+            t0 = time.perf_counter()
+            pool.map(_oracle_matvec, range(nproc), chunksize=1)
+            times.append(time.perf_counter() - t0)
     t = float(np.mean(times))
-    value = 1.0 / (t * pde_per_reg)
+    mv_per_s = nproc / t
+    value = mv_per_s / (PDE_PER_REG / 2.0)
+    sample = (f"per step {nproc} FP64 oracle Gauss-Newton matvecs at 512^2 nt=32, one per host core (process "
+              f"pool); registrations/s = matvecs/s / {PDE_PER_REG / 2:g} matvec equivalents per registration "
+              f"({PDE_PER_REG} PDE solves, counted by the GPU solve of this workload)")
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": "registrations/s",
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": t * 1e3, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f64", "data": "synthetic", "config": {"workload": WORKLOAD},
-        "cpu_baseline": {"value": value, "unit": "registrations/s", "cores": 1, "kind": "oracle",
-                         "sample": f"one FP64 oracle state solve (512^2, nt=32) per step, scaled by "
-                                   f"{pde_per_reg} PDE solves per registration"},
+        "matvec_per_s": mv_per_s,
+        "cpu_baseline": {"value": value, "unit": "registrations/s", "cores": nproc, "kind": "oracle",
+                         "sample": sample},
         "e2e": {"value": value, "unit": "registrations/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line))
@@ -453,30 +642,48 @@ def main():
         launches = launches_single * PAIRS
         lat /= nlat
 
-        # e2e: the same batch from pinned host buffers (H2D of images, D2H of velocities and stats inside)
+        # e2e through the public host-buffer call: per pair one reg_register_host (H2D of the
+        # pinned images, the solve, D2H of the velocity inside the call) on its own host thread,
+        # context and stream, then det F1 of the velocity copied back to the device
+        import threading
+        hstreams = [torch.cuda.Stream(device=dev) for _ in range(PAIRS)]
+        hctx = [Context(N_GRID, N_GRID, NT, regnorm=1, beta=BETA, gamma=math.inf, shear=0.0, stream=hs)
+                for hs in hstreams]
         hpairs = [(torch.from_numpy(a).pin_memory(), torch.from_numpy(b).pin_memory()) for a, b in pairs_np]
         hv = [torch.empty(2, N_GRID, N_GRID, dtype=torch.float32).pin_memory() for _ in range(PAIRS)]
+        vdev = [torch.empty(2, N_GRID, N_GRID, device=dev) for _ in range(PAIRS)]
+        e2e_stats = [None] * PAIRS
+
+        def e2e_pair(i):
+            c, hs = hctx[i], hstreams[i]
+            st = c.register_host(hpairs[i][0], hpairs[i][1], hv[i], opts)
+            with torch.cuda.stream(hs):
+                vdev[i].copy_(hv[i], non_blocking=True)
+            e2e_stats[i] = (st, c.detgrad(vdev[i]))  # reads the statistics back: synchronizes hs
+
+        def e2e_step():
+            ths = [threading.Thread(target=e2e_pair, args=(i,)) for i in range(PAIRS)]
+            for t in ths:
+                t.start()
+            for t in ths:
+                t.join()
+
+        e2e_step()  # warm-up: captured launch sequences of the new contexts
         torch.cuda.synchronize()
         e2e_ms = 0.0
         for _ in range(args.steps):
             flush.fill_(1.0)
             torch.cuda.synchronize()
-            e0 = torch.cuda.Event(enable_timing=True)
-            e1 = torch.cuda.Event(enable_timing=True)
-            e0.record(stream)
-            for p, (a, b) in zip(pairs, hpairs):
-                p["mT"].copy_(a, non_blocking=True)
-                p["mR"].copy_(b, non_blocking=True)
-            stream.synchronize()
-            step()
-            for p, h in zip(pairs, hv):
-                h.copy_(p["v"], non_blocking=True)
-            e1.record(stream)
-            e1.synchronize()
-            e2e_ms += e0.elapsed_time(e1)
+            t0 = time.perf_counter()
+            e2e_step()
+            e2e_ms += 1e3 * (time.perf_counter() - t0)
+        for c in hctx:
+            c.close()
         e2e_value = throughput(aggregate_ms(e2e_ms / args.steps, world, dist if world > 1 else None, dev), world)
+        e2e_ok = all(st["rc"] == 0 for st, _ in e2e_stats)
 
-        # Hessian matvec throughput at a fixed linearization point (the converged v)
+        # Hessian matvec throughput at a fixed linearization point (the converged v): one
+        # context alone, and PAIRS contexts (one per pair, each at its own solution) at once
         g = torch.empty_like(v)
         ctx.gradient(v, g)
         vt = torch.randn_like(v)
@@ -492,7 +699,7 @@ def main():
         e1.record(stream)
         e1.synchronize()
         mv_ms = e0.elapsed_time(e1) / args.matvecs
-
+        mv_conc = matvec_concurrent(dev, pairs, opts, args.matvecs // 4)
         # roofline: per-kernel-class CUDA-event timing over one more registration
         ctx.kernel_timing(True)
         ctx.set_images(mT, mR)
@@ -538,10 +745,6 @@ def main():
             bcls = {kc: ctxb.kernel_time(kc) for kc in range(4)}
             ctxb.kernel_timing(False)
             ctxb.close()
-            bd = max(bcls, key=lambda k: bcls[k][1])
-            ach = bcls[bd][2] / (bcls[bd][1] * 1e-3) / 1e9 if bcls[bd][1] > 0 else 0.0
-            big["roofline"] = {"kernel": ["column FFT + multiplier", "row FFT + RK2 stage", "row FFT (other)",
-                                          "pointwise/reduction"][bd], "achieved": ach, "launches": bcls[bd][0]}
             big["kernel_classes"] = {str(k): {"launches": bcls[k][0], "ms": bcls[k][1], "GB": bcls[k][2] / 1e9}
                                      for k in bcls}
         # learned warm start vs plain zero start (256^2, nt=16, held-out pairs) with the committed weights
@@ -602,20 +805,15 @@ def main():
         batched_mixed = run_batched_mixed(dev, stream, opts) if (args.batched and rank == 0) else None
     from paper_1503_00757_gb300.binding import fp32_peak
     fp32_tf, _ = fp32_peak()
-    dom = max(classes, key=lambda k: classes[k][1])
-    n_dom, ms_dom, bytes_dom = classes[dom]
     peak, peak_kind = peaks()
-    achieved = (bytes_dom / (ms_dom * 1e-3)) / 1e9 if ms_dom > 0 else 0.0
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
-        t_pde = cpu_oracle_pde_time(mT_np, mR_np)
-        n_pde = stats.get("n_pde", PDE_PER_REG)
-        cpu = {"value": 1.0 / (t_pde * n_pde), "unit": "registrations/s", "cores": 1, "kind": "oracle",
-               "sample": f"one FP64 oracle state solve (512^2, nt=32) = {t_pde:.1f} s, scaled by the "
-                         f"{n_pde} PDE solves of the GPU registration"}
+        cpu = cpu_oracle_baseline(stats.get("n_pde", PDE_PER_REG))
 
     if rank == 0:
+        names = ["column FFT + multiplier", "row FFT + RK2 stage", "row FFT (other)", "pointwise/reduction"]
+        sb512 = stream_bytes(N_GRID, N_GRID, NT)
         line = {
             "metric": METRIC, "value": value, "unit": "registrations/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
@@ -632,27 +830,31 @@ def main():
             "batched_mixed_vs_sequential": batched_mixed,
             "shear_control_512": shear or None,
             "matvec_per_s": 1e3 / mv_ms, "ms_per_matvec": mv_ms,
+            "matvec_concurrent": mv_conc,
             "solve": {k: stats[k] for k in ("n_newton", "n_mv", "n_pde", "n_ls", "gnorm_rel", "rnorm_rel_sq", "status")},
             "solve_batch": [{k: b[k] for k in ("n_newton", "n_mv", "gnorm_rel", "rc")} for b in bstats],
             "detF": {"min": det[0], "mean": det[1], "max": det[2], "maxD": det[3]},
-            "e2e": {"value": e2e_value, "unit": "registrations/s", "h2d_bytes_per_step": PAIRS * 2 * 4 * N_GRID * N_GRID,
-                    "d2h_bytes_per_step": PAIRS * 2 * 4 * N_GRID * N_GRID},
+            "e2e": {"value": e2e_value, "unit": "registrations/s", "all_converged": e2e_ok,
+                    "call": "reg_register_host per pair (pinned host buffers) + reg_detgrad, one host thread per pair",
+                    "h2d_bytes_per_step": PAIRS * (1 + 1 + 2) * 4 * N_GRID * N_GRID,
+                    "d2h_bytes_per_step": PAIRS * (2 * 4 * N_GRID * N_GRID + 5 * 8)},
             "gpu_launches": launches,
-            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                         "frac": achieved / peak,
-                         "traffic": ROW_STAGE_TRAFFIC_512 if dom == 1 else None, "kernel": names[dom],
-                         "launches": n_dom, "ms": ms_dom, "peak_kind": peak_kind},
+            "roofline": roofline(sb512, mv_conc, mv_ms, peak, peak_kind),
             "matvec_1024": ({"ms_per_matvec": big["ms_per_matvec"], "matvec_per_s": 1e3 / big["ms_per_matvec"],
-                             "roofline": {"bound": "hbm", "kernel": big["roofline"]["kernel"],
-                                          "achieved": big["roofline"]["achieved"], "peak": peak,
-                                          "frac": big["roofline"]["achieved"] / peak, "unit": "GB/s"},
+                             "roofline_single_context": {
+                                 "bound": "hbm", "unit": "GB/s", "bytes_per_matvec": stream_bytes(1024, 1024, NT),
+                                 "achieved": stream_bytes(1024, 1024, NT) / big["ms_per_matvec"] / 1e6,
+                                 "peak": peak,
+                                 "frac": stream_bytes(1024, 1024, NT) / big["ms_per_matvec"] / 1e6 / peak},
                              "kernel_classes": big["kernel_classes"]} if big else None),
             "ceilings": {"fp32_tflops_measured": fp32_tf, "hbm_gbs": peak,
                          "matvec_512": matvec_models(N_GRID, N_GRID, NT, mv_ms, peak, fp32_tf),
+                         "matvec_512_concurrent": matvec_models(N_GRID, N_GRID, NT, mv_conc["ms_per_matvec"], peak,
+                                                                fp32_tf),
                          "matvec_1024": (matvec_models(1024, 1024, NT, big["ms_per_matvec"], peak, fp32_tf)
                                          if big else None)},
             "kernel_classes": {names[k]: {"launches": classes[k][0], "ms": classes[k][1],
-                                          "GB": classes[k][2] / 1e9} for k in classes},
+                                          "GB_library_tally": classes[k][2] / 1e9} for k in classes},
             "clocks": clk,
             "cpu_baseline": cpu,
         }

@@ -240,8 +240,10 @@ void reg_executor_destroy(reg_executor* ex);
  * choice (R rows per row-kernel CTA, C spectrum columns per column-kernel
  * CTA, P = 1 if the RK2 row kernels prefetch their operands before waiting on
  * the preceding kernel) with programmatic dependent launch on and off
- * (D, see reg_set_pdl), on the current device with zero images and velocity
- * and private streams, and records the fastest in a process-wide table;
+ * (D, see reg_set_pdl), and, on grids where it runs, the cluster-resident
+ * transport kernel (see reg_set_transport), on the current device with zero
+ * images and velocity and private streams, and records the fastest in a
+ * process-wide table;
  * contexts created afterwards on this device and grid use it (existing
  * contexts keep theirs).  Valid: R a multiple of 4 dividing n1,
  * 32 <= R n2 / 8 <= 512 threads; C a power of two >= 2 dividing n2 / 2,
@@ -266,6 +268,32 @@ int reg_tile_config(reg_ctx* ctx, int* rows_per_cta, int* cols_per_cta, int* pre
  * summation order of FP64 reductions (objective, norms).  REG_ERR_ARG for
  * invalid tiles. */
 int reg_set_tiles(reg_ctx* ctx, int rows_per_cta, int cols_per_cta, int prefetch);
+
+/* ---- transport kernels ---- */
+
+/* Selects how the transport solves (state, adjoint, and the incremental state and
+ * adjoint of a Gauss-Newton matvec; Eqs. (e:state-eq-elim)-(e:inc-adj-eq-elim),
+ * Heun steps of Sec. 4) run on this context:
+ *   cluster != 0: one launch per solve (both sweeps of a matvec in one launch),
+ *     resident in a thread-block cluster of max(1, n^2 / 16384) CTAs that keep
+ *     the row spectra of the transported field in shared memory and exchange
+ *     column slabs through distributed shared memory (square grids n x n,
+ *     16 <= n <= 512, on devices with thread-block clusters);
+ *   cluster == 0: a row kernel and a column kernel per Heun stage, the spectra
+ *     passing through global memory (every grid).
+ * Default: the two-kernel path, unless reg_autotune measured the cluster path
+ * faster for this device and grid before the context was created.  Results
+ * agree to FP32 rounding (the transforms are the same; the order of a few
+ * additions differs).  REG_ERR_ARG if cluster != 0 and this grid or device
+ * cannot run it. */
+int reg_set_transport(reg_ctx* ctx, int cluster);
+
+/* The transport path of a context: *cluster = 1 for the cluster-resident
+ * kernel; *ctas_per_cluster = its cluster size on this grid (0 if it cannot
+ * run); *max_active_clusters = how many such clusters fit on the device at
+ * once (cudaOccupancyMaxActiveClusters; independent solves on separate
+ * streams run concurrently up to that number).  Host pointers, each nullable. */
+int reg_transport_config(reg_ctx* ctx, int* cluster, int* ctas_per_cluster, int* max_active_clusters);
 
 /* Programmatic dependent launch (default on): each kernel may start while its
  * predecessor finishes and waits on it in-kernel, which hides launch latency
@@ -346,9 +374,10 @@ int reg_net_train_step(reg_net* net, const float* images, const float* targets, 
  *   grad_f    device, 2*n1*n2 floats (output: d1 f then d2 f);
  *   stream    cudaStream_t the work is issued on (NULL = legacy default).
  * The first call on each device does that device's set-up (looks up the
- * arrays' device addresses and copies the twiddle table with a synchronous
- * cudaMemcpyToSymbol), so make the first call on a device before any stream
- * capture begins.  All calls share the one scratch array and it keeps the
+ * arrays' device addresses, copies the twiddle table with cudaMemcpyToSymbol
+ * and waits with cudaDeviceSynchronize until it has arrived, so that the
+ * first call's kernels may run on any stream, non-blocking ones included),
+ * so make the first call on a device before any stream capture begins.  All calls share the one scratch array and it keeps the
  * last call's contents; nothing in it has to start at zero because every
  * entry is written before it is read.  Calls that overlap on the GPU (other
  * streams, other host threads) race on the scratch: serialize them.
@@ -364,7 +393,8 @@ int reg_spectral_grad_static(reg_grid grid, const float* f, float* grad_f, void*
  * every output written once) since the last enable (host pointers, each
  * nullable).  Classes: 0 column FFT + multiplier kernels, 1 row FFT + RK2
  * stage kernels (advection / adjoint), 2 other row FFT kernels,
- * 3 pointwise / reduction kernels. */
+ * 3 pointwise / reduction kernels, 4 cluster-resident transport kernels (one
+ * launch per transport solve, or per matvec for both of its solves). */
 int reg_kernel_timing(reg_ctx* ctx, int enable);
 int reg_kernel_time(reg_ctx* ctx, int kclass, long long* launches, double* ms, double* bytes);
 /* Number of kernels this context has launched since creation. */

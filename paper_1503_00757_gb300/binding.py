@@ -84,6 +84,8 @@ _SIGS = {
     "reg_tile_config": ([_P, ctypes.POINTER(_I), ctypes.POINTER(_I), ctypes.POINTER(_I), ctypes.POINTER(_I)], _I),
     "reg_set_tiles": ([_P, _I, _I, _I], _I),
     "reg_set_pdl": ([_P, _I], _I),
+    "reg_set_transport": ([_P, _I], _I),
+    "reg_transport_config": ([_P, ctypes.POINTER(_I), ctypes.POINTER(_I), ctypes.POINTER(_I)], _I),
     "reg_fp32_peak": ([ctypes.POINTER(_D), ctypes.POINTER(_D)], _I),
     "reg_net_create": ([_I, _I, _I, ctypes.POINTER(_P)], _I),
     "reg_net_destroy": ([_P], None),
@@ -459,3 +461,13 @@ class Context:
         """Launch with R rows per row-kernel CTA, C spectrum columns per column-kernel CTA and
         operand prefetch P in the RK2 row kernels (R = C = 0: default rule)."""
         _check(lib().reg_set_tiles(self.h, R, C, P))
+
+    def set_transport(self, cluster):
+        """Transport solves in the cluster-resident kernel (True) or the row/column kernel pairs (False)."""
+        _check(lib().reg_set_transport(self.h, 1 if cluster else 0))
+
+    def transport_config(self):
+        """(cluster path in use, CTAs per cluster, clusters that fit on the device at once)."""
+        a, b, c = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+        _check(lib().reg_transport_config(self.h, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)))
+        return a.value, b.value, c.value

@@ -151,13 +151,16 @@ extern "C" int reg_create(reg_grid grid, int nt, int regnorm, double beta, doubl
     c->launches = 0;
     c->tileR = c->tileC = c->tileP = 0;
     c->pdl = true;
+    c->tc_ok = tc_max_active_clusters(c->n1, c->n2) > 0;
+    c->use_tc = false;  // the row / column kernel pairs unless the autotuner measured the cluster kernel faster
     {
-        int dev = 0, R, C, P, D;
-        if (cudaGetDevice(&dev) == cudaSuccess && tuned_tiles(dev, c->n1, c->n2, &R, &C, &P, &D)) {
+        int dev = 0, R, C, P, D, T;
+        if (cudaGetDevice(&dev) == cudaSuccess && tuned_tiles(dev, c->n1, c->n2, &R, &C, &P, &D, &T)) {
             c->tileR = R;
             c->tileC = C;
             c->tileP = P;
             c->pdl = D != 0;
+            c->use_tc = T != 0 && c->tc_ok;
         }
     }
     c->use_graphs = true;
@@ -225,6 +228,24 @@ extern "C" int reg_set_tiles(reg_ctx* c, int rows_per_cta, int cols_per_cta, int
     c->tileR = rows_per_cta;
     c->tileC = cols_per_cta;
     c->tileP = prefetch;
+    return REG_OK;
+}
+
+extern "C" int reg_set_transport(reg_ctx* c, int cluster) {
+    if (!c) return reg_fail(REG_ERR_ARG, "ctx is NULL");
+    if (cluster && !c->tc_ok)
+        return reg_fail(REG_ERR_ARG, "the cluster-resident transport kernel does not run on this grid or device");
+    const bool on = cluster != 0;
+    if (on != c->use_tc) clear_graphs(c);  // captures bake in the kernels
+    c->use_tc = on;
+    return REG_OK;
+}
+
+extern "C" int reg_transport_config(reg_ctx* c, int* cluster, int* ctas_per_cluster, int* max_active_clusters) {
+    if (!c) return reg_fail(REG_ERR_ARG, "ctx is NULL");
+    if (cluster) *cluster = c->use_tc ? 1 : 0;
+    if (ctas_per_cluster) *ctas_per_cluster = c->tc_ok ? tc_cluster_size(c->n1) : 0;
+    if (max_active_clusters) *max_active_clusters = c->tc_ok ? tc_max_active_clusters(c->n1, c->n2) : 0;
     return REG_OK;
 }
 
@@ -442,6 +463,12 @@ static float* gmh(reg_ctx* c, int j) { return c->gm_hist + (size_t)j * 2 * c->N;
 // spectra and is formed by the row kernel from the stage's own spectrum S[0].
 static void state_solve(reg_ctx* c, const float* v, int nt) {
     const float h = 1.0f / (float)nt;
+    if (c->use_tc) {
+        TcArgs a = {};
+        a.nt = nt; a.h = h; a.v = v; a.mT = c->mT; a.m_hist = c->m_hist; a.gm_hist = c->gm_hist; a.us = c->w0;
+        launch_transport_cluster(c, TC_STATE, a);
+        return;
+    }
     cudaMemcpyAsync(mh(c, 0), c->mT, sizeof(float) * c->N, cudaMemcpyDeviceToDevice, c->stream);
     launch_r2c_scalar(c, mh(c, 0), c->S[0]);
     const float2* in[1] = {c->S[0]};
@@ -471,6 +498,13 @@ static void state_solve(reg_ctx* c, const float* v, int nt) {
 static void adjoint_solve(reg_ctx* c, const float* v, int nt, const float* a, float ca, const float* cf, float cb,
                           float* bout, double* part_jdata) {
     const float h = 1.0f / (float)nt;
+    if (c->use_tc && !part_jdata) {
+        TcArgs t = {};
+        t.nt = nt; t.h = h; t.v = v; t.gm_hist = c->gm_hist; t.lj = c->w1; t.ls = c->w2;
+        t.adj_a = a; t.adj_ca = ca; t.adj_c = cf; t.adj_cb = cb; t.b = bout;
+        launch_transport_cluster(c, TC_ADJOINT, t);
+        return;
+    }
     float* lam = c->w1;
     float* lst = c->w2;
     launch_adj_init(c, a, ca, cf, cb, v, lam, bout, gmh(c, nt), 0.5f * h, c->S[1], c->S[2], part_jdata);
@@ -595,19 +629,32 @@ static int gradient_dev_y(reg_ctx* c, const float* v, const float* y, float* gy,
     return REG_OK;
 }
 
+// Incremental state and Gauss-Newton incremental adjoint of a matvec (Algorithm 2's product):
+// m~(1) in c->w3, b~ in c->bvec.  The cluster path runs both sweeps in one launch.
+static void inc_solves(reg_ctx* c, const float* vt, int nt) {
+    if (c->use_tc) {
+        TcArgs a = {};
+        a.nt = nt; a.h = 1.0f / (float)nt; a.v = c->v_lin; a.vt = vt; a.gm_hist = c->gm_hist;
+        a.uj = c->w3; a.us = c->w0; a.lj = c->w1; a.ls = c->w2;
+        a.adj_a = nullptr; a.adj_ca = 0.f; a.adj_c = nullptr; a.adj_cb = -1.f; a.b = c->bvec;
+        launch_transport_cluster(c, TC_MATVEC, a);
+        return;
+    }
+    inc_state_solve(c, c->v_lin, vt, nt);
+    adjoint_solve(c, c->v_lin, nt, nullptr, 0.f, c->w3, -1.f, c->bvec, nullptr);
+}
+
 // Hessian product in preconditioned coordinates: H_y s = Q^-1 H_v Q^-1 s = Pi0 s + Q^-1 K b~(v~ = Q^-1 s)
 static void matvec_launches_y(reg_ctx* c, const float* s, float* Hs) {
     const int nt = c->nt_lin;
     sp_vec(c, OP_QINV, 0.f, s, c->vtil);
-    inc_state_solve(c, c->v_lin, c->vtil, nt);
-    adjoint_solve(c, c->v_lin, nt, nullptr, 0.f, c->w3, -1.f, c->bvec, nullptr);
+    inc_solves(c, c->vtil, nt);
     sp_assemble_y(c, s, c->bvec, Hs);
 }
 
 static void matvec_launches(reg_ctx* c, const float* vt, float* Hvt) {
     const int nt = c->nt_lin;
-    inc_state_solve(c, c->v_lin, vt, nt);
-    adjoint_solve(c, c->v_lin, nt, nullptr, 0.f, c->w3, -1.f, c->bvec, nullptr);
+    inc_solves(c, vt, nt);
     if (c->shear_model) {
         sp_grad_vec(c, vt, c->gtmp);
         launch_shear_second(c, c->gtmp, c->E_lin, c->eta_lin, (float)c->nu, c->T3);

@@ -44,7 +44,7 @@ struct SpecParams {
     double ebw;     // OP_ENERGY: beta_w / 2 (0 unless PROJ_MASS)
 };
 
-enum KClass { KC_COL = 0, KC_ROWSTAGE = 1, KC_ROW = 2, KC_POINT = 3, KC_COUNT = 4 };
+enum KClass { KC_COL = 0, KC_ROWSTAGE = 1, KC_ROW = 2, KC_POINT = 3, KC_TRANSPORT = 4, KC_COUNT = 5 };
 
 // Device-scalar slots (doubles) in reg_ctx::d_scal.
 enum Slot {
@@ -108,6 +108,8 @@ struct reg_ctx {
 
     float2* tw;      // twiddle table (REG_TW_N entries)
 
+    bool tc_ok;        // the cluster-resident transport kernel can run on this grid and device
+    bool use_tc;       // transport solves run in the cluster-resident kernel (else the two-pass kernels)
     int tileR, tileC;  // rows per row-kernel CTA, spectrum columns per column-kernel CTA (0: default)
     int tileP;         // 1: RK2 row kernels prefetch their operands (used when tileR > 0)
 
@@ -127,8 +129,9 @@ struct reg_ctx {
 // ---- FFT tile choices (kernels.cu: defaults and limits; tune.cu: autotuner table) ----
 void default_tiles(int n1, int n2, int* R, int* C, int* P);
 bool tiles_valid(int n1, int n2, int R, int C, int P);
-// tuned (R, C, P, D) for this device and grid, if reg_autotune has measured it (D: launch with PDL)
-bool tuned_tiles(int dev, int n1, int n2, int* R, int* C, int* P, int* D);
+// tuned (R, C, P, D, T) for this device and grid, if reg_autotune has measured it (D: launch with
+// PDL; T: transports in the cluster-resident kernel; T nullable)
+bool tuned_tiles(int dev, int n1, int n2, int* R, int* C, int* P, int* D, int* T);
 
 // ---- launchers (kernels.cu); all asynchronous on ctx->stream ----
 cudaError_t k_init_twiddles(reg_ctx* ctx);
@@ -214,3 +217,30 @@ int reg_fail(int status, const std::string& msg);
 // out = exp(-a |k|^2) P_L b on the context's grid (velocity fields, device):
 // the output map of the warm-start network (Gaussian low-pass, then Leray).
 int apply_smooth_proj(reg_ctx* ctx, float a, const float* b, float* out);
+
+// ---- cluster-resident transport solves (transport_cluster.cu) ----
+enum TcMode { TC_STATE = 0, TC_ADJOINT = 1, TC_MATVEC = 2 };
+struct TcArgs {
+    int nt;
+    float h;                 // 1 / nt
+    const float* v;          // velocity (2N)
+    const float* vt;         // incremental velocity (2N, TC_MATVEC)
+    const float* mT;         // template (TC_STATE)
+    float* m_hist;           // (nt+1) N: written by TC_STATE; m_nt read by TC_ADJOINT through adj_c
+    float* gm_hist;          // 2 (nt+1) N: written by TC_STATE, read by the others
+    float* uj;               // TC_MATVEC: m~_j (ends as m~_nt)
+    float* us;               // stage-2 input of the forward sweep (u*)
+    float* lj;               // adjoint lam_j
+    float* ls;               // adjoint lam*
+    const float* adj_a;      // lam_nt = adj_ca adj_a + adj_cb adj_c (adj_a nullable; TC_MATVEC uses uj for adj_c)
+    float adj_ca;
+    const float* adj_c;
+    float adj_cb;
+    float* b;                // body force (2N): written
+    const float2* tw;        // twiddle table (set by the launcher)
+};
+// CTAs per cluster for an n x n grid, and how many such clusters fit on the current device
+// at once (0: the cluster kernel cannot run on this grid or device)
+int tc_cluster_size(int n);
+int tc_max_active_clusters(int n1, int n2);
+void launch_transport_cluster(reg_ctx* ctx, int mode, const TcArgs& a);

@@ -771,18 +771,30 @@ static bool prefetch_rows(const reg_ctx* ctx) {
     return (ctx->tileR > 0 ? ctx->tileP : P) != 0;
 }
 
-// Opt in to more than 48 KB of dynamic shared memory once per kernel instantiation and size
-// (contexts on several host threads launch concurrently, hence the lock).
+// Opt in to more than 48 KB of dynamic shared memory once per (device, kernel instantiation)
+// and size: the attribute applies to the current device only (contexts on several host
+// threads launch concurrently, hence the lock).
+struct SmemKey {
+    int dev;
+    const void* kern;
+    bool operator==(const SmemKey& o) const { return dev == o.dev && kern == o.kern; }
+};
+struct SmemKeyHash {
+    size_t operator()(const SmemKey& k) const { return std::hash<const void*>()(k.kern) * 31u + (size_t)k.dev; }
+};
 template <typename K>
 static void set_smem(K kern, size_t bytes) {
     if (bytes <= 32 * 1024) return;  // static shared memory (reductions) also counts toward the 48 KB default
     static std::mutex mu;
-    static std::unordered_map<const void*, size_t> done;
+    static std::unordered_map<SmemKey, size_t, SmemKeyHash> done;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    const SmemKey key{dev, (const void*)kern};
     std::lock_guard<std::mutex> lock(mu);
-    auto it = done.find((const void*)kern);
+    auto it = done.find(key);
     if (it != done.end() && it->second >= bytes) return;
     cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
-    done[(const void*)kern] = bytes;
+    done[key] = bytes;
 }
 
 #define DISPATCH_LOG(LOG, ...)                        \

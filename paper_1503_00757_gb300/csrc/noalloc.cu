@@ -35,8 +35,8 @@ StaticDevice g_static[kMaxDevices];
 std::mutex g_static_mu;
 
 // Once per device, with that device current: resolve the device addresses of
-// the file-scope arrays (host code must not use their names as pointers) and
-// upload the twiddle table.
+// the file-scope arrays (host code must not use their names as pointers),
+// upload the twiddle table and wait for the upload to complete.
 int static_setup(int dev) {
     std::lock_guard<std::mutex> lock(g_static_mu);
     StaticDevice& s = g_static[dev];
@@ -52,6 +52,11 @@ int static_setup(int dev) {
     }
     e = cudaMemcpyToSymbol(g_static_twiddles, h, sizeof(h));
     if (e != cudaSuccess) return reg_fail(REG_ERR_CUDA, std::string("twiddle upload: ") + cudaGetErrorString(e));
+    // A copy from pageable host memory may return once the data is staged; the first
+    // call's kernels then run on the caller's stream, which need not be ordered after the
+    // legacy stream (cudaStreamNonBlocking).  Wait until the table is on the device.
+    e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) return reg_fail(REG_ERR_CUDA, std::string("twiddle upload (sync): ") + cudaGetErrorString(e));
     s.ready = true;
     return REG_OK;
 }

@@ -9,9 +9,11 @@
 // every valid (R, C, P) with a given number of solves running concurrently on
 // their own streams, each with and without programmatic dependent launch
 // (D): early launch hides one solve's launch latency but lets waiting CTAs
-// hold SM resources, and which wins depends on the concurrency.  Results live
-// in a process-wide table per (device, n1, n2); contexts created afterwards
-// on that device and grid use them.
+// hold SM resources, and which wins depends on the concurrency.  Where the
+// cluster-resident transport kernel runs (square grids up to 512^2) it is one
+// more candidate (T = 1; its transports do not use the row / column tiles).
+// Results live in a process-wide table per (device, n1, n2); contexts created
+// afterwards on that device and grid use them.
 #include <cmath>
 #include <map>
 #include <mutex>
@@ -23,7 +25,7 @@
 
 namespace {
 std::mutex g_tune_mu;
-std::map<std::tuple<int, int, int>, std::tuple<int, int, int, int>> g_tune;
+std::map<std::tuple<int, int, int>, std::tuple<int, int, int, int, int>> g_tune;
 
 bool pow2_grid(int n) { return n >= 16 && n <= 1024 && (n & (n - 1)) == 0; }
 
@@ -34,8 +36,8 @@ struct Lane {
 };
 
 // Milliseconds per Hessian matvec (throughput over `lanes.size()` concurrent
-// solves) with tiles (R, C, P) and launch mode D; < 0 on failure.
-double time_matvec(reg_grid grid, int nt, int R, int C, int P, int D, std::vector<Lane>& lanes, float* mT,
+// solves) with tiles (R, C, P), launch mode D and transport path T; < 0 on failure.
+double time_matvec(reg_grid grid, int nt, int R, int C, int P, int D, int T, std::vector<Lane>& lanes, float* mT,
                    float* mR, float* v, float* out, cudaStream_t root, cudaEvent_t e0, cudaEvent_t e1) {
     const size_t N2 = 2 * (size_t)grid.n1 * grid.n2;
     bool ok = true;
@@ -47,6 +49,7 @@ double time_matvec(reg_grid grid, int nt, int R, int C, int P, int D, std::vecto
         L.ctx->tileC = C;
         L.ctx->tileP = P;
         L.ctx->pdl = D != 0;
+        L.ctx->use_tc = T != 0 && L.ctx->tc_ok;
         float* o = out + i * N2;
         ok = reg_set_stream(L.ctx, L.st) == REG_OK && reg_set_images(L.ctx, mT, mR) == REG_OK &&
              reg_gradient(L.ctx, v, o, nullptr) == REG_OK;
@@ -75,7 +78,7 @@ double time_matvec(reg_grid grid, int nt, int R, int C, int P, int D, std::vecto
 }
 }  // namespace
 
-bool tuned_tiles(int dev, int n1, int n2, int* R, int* C, int* P, int* D) {
+bool tuned_tiles(int dev, int n1, int n2, int* R, int* C, int* P, int* D, int* T) {
     std::lock_guard<std::mutex> lock(g_tune_mu);
     auto it = g_tune.find(std::make_tuple(dev, n1, n2));
     if (it == g_tune.end()) return false;
@@ -83,6 +86,7 @@ bool tuned_tiles(int dev, int n1, int n2, int* R, int* C, int* P, int* D) {
     *C = std::get<1>(it->second);
     *P = std::get<2>(it->second);
     *D = std::get<3>(it->second);
+    if (T) *T = std::get<4>(it->second);
     return true;
 }
 
@@ -96,7 +100,7 @@ extern "C" int reg_autotune(reg_grid grid, int nt, int concurrency, int force, i
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return reg_fail(REG_ERR_CUDA, std::string("cudaGetDevice: ") + cudaGetErrorString(e));
     int R = 0, C = 0, P = 0, D = 1;
-    if (!force && tuned_tiles(dev, grid.n1, grid.n2, &R, &C, &P, &D)) {
+    if (!force && tuned_tiles(dev, grid.n1, grid.n2, &R, &C, &P, &D, nullptr)) {
         if (rows_per_cta) *rows_per_cta = R;
         if (cols_per_cta) *cols_per_cta = C;
         if (prefetch) *prefetch = P;
@@ -104,15 +108,16 @@ extern "C" int reg_autotune(reg_grid grid, int nt, int concurrency, int force, i
         if (ms_per_matvec) *ms_per_matvec = -1.0;
         return REG_OK;
     }
-    std::vector<std::tuple<int, int, int, int>> cands;
+    std::vector<std::tuple<int, int, int, int, int>> cands;
     for (int r = 4; r <= grid.n1; r *= 2)
         for (int c = 2; c <= grid.n2 / 2; c *= 2)
             for (int p = 0; p <= 1; ++p)
                 for (int d = 0; d <= 1; ++d)
-                    if (tiles_valid(grid.n1, grid.n2, r, c, p)) cands.emplace_back(r, c, p, d);
+                    if (tiles_valid(grid.n1, grid.n2, r, c, p)) cands.emplace_back(r, c, p, d, 0);
     int R0, C0, P0;
     default_tiles(grid.n1, grid.n2, &R0, &C0, &P0);
-    if (cands.empty()) cands.emplace_back(R0, C0, P0, 1);
+    if (cands.empty()) cands.emplace_back(R0, C0, P0, 1, 0);
+    if (tc_max_active_clusters(grid.n1, grid.n2) > 0) cands.emplace_back(R0, C0, P0, 1, 1);
 
     const size_t N = (size_t)grid.n1 * grid.n2;
     const int K = concurrency;
@@ -141,8 +146,8 @@ extern "C" int reg_autotune(reg_grid grid, int nt, int concurrency, int force, i
     for (int pass = 0; pass < 2 && status == REG_OK; ++pass) {
         for (size_t i = 0; status == REG_OK && i < cands.size(); ++i) {
             const int r = std::get<0>(cands[i]), c = std::get<1>(cands[i]), p = std::get<2>(cands[i]);
-            const int d = std::get<3>(cands[i]);
-            const double ms = time_matvec(grid, nt, r, c, p, d, lanes, mT, mR, v, out, root, e0, e1);
+            const int d = std::get<3>(cands[i]), tc = std::get<4>(cands[i]);
+            const double ms = time_matvec(grid, nt, r, c, p, d, tc, lanes, mT, mR, v, out, root, e0, e1);
             if (ms < 0.0) {
                 status = reg_fail(REG_ERR_CUDA, std::string("autotune candidate failed: ") + reg_last_error());
                 break;
@@ -151,10 +156,10 @@ extern "C" int reg_autotune(reg_grid grid, int nt, int concurrency, int force, i
         }
     }
     double best = -1.0;
-    int bR = R0, bC = C0, bP = P0, bD = 1;
+    int bR = R0, bC = C0, bP = P0, bD = 1, bT = 0;
     for (size_t i = 0; status == REG_OK && i < cands.size(); ++i) {
         const int r = std::get<0>(cands[i]), c = std::get<1>(cands[i]), p = std::get<2>(cands[i]);
-        const int d = std::get<3>(cands[i]);
+        const int d = std::get<3>(cands[i]), tc = std::get<4>(cands[i]);
         const double ms = tbest[i];
         if (best < 0.0 || ms < best) {
             best = ms;
@@ -162,6 +167,7 @@ extern "C" int reg_autotune(reg_grid grid, int nt, int concurrency, int force, i
             bC = c;
             bP = p;
             bD = d;
+            bT = tc;
         }
     }
     if (root) cudaStreamSynchronize(root);
@@ -177,7 +183,7 @@ extern "C" int reg_autotune(reg_grid grid, int nt, int concurrency, int force, i
     if (status != REG_OK) return status;
     {
         std::lock_guard<std::mutex> lock(g_tune_mu);
-        g_tune[std::make_tuple(dev, grid.n1, grid.n2)] = std::make_tuple(bR, bC, bP, bD);
+        g_tune[std::make_tuple(dev, grid.n1, grid.n2)] = std::make_tuple(bR, bC, bP, bD, bT);
     }
     if (rows_per_cta) *rows_per_cta = bR;
     if (cols_per_cta) *cols_per_cta = bC;

@@ -49,6 +49,7 @@ def test_every_tile_choice_gives_identical_results(n1, n2):
     dev = lambda a: torch.tensor(a, dtype=torch.float32, device="cuda").contiguous()
     stream = torch.cuda.Stream()  # a non-default stream: the captured-graph path
     ctx = Context(n1, n2, 8, regnorm=1, beta=1e-3, gamma=1e-3, stream=stream)
+    ctx.set_transport(False)  # the row / column kernel pairs, whose tiles are under test
     mTd, mRd, vd, vtd = dev(mT), dev(mR), dev(v), dev(vt)
     g0, h0 = torch.empty(2, n1, n2, device="cuda"), torch.empty(2, n1, n2, device="cuda")
     torch.cuda.synchronize()

@@ -1,0 +1,119 @@
+"""The cluster-resident transport kernel (one launch per transport solve, row spectra kept in
+shared memory, column slabs exchanged through distributed shared memory) against the FP64
+oracle element by element, and against the two-kernel path, on every square grid it serves
+below the benchmark's 512^2 (which test_gpu_parity_full covers): 16^2 .. 128^2 on one CTA,
+256^2 on a cluster of 4.  Quantities: m_1, J (state solve), b and g (adjoint solve, body
+force, reduced gradient), b~ and H v~ (incremental state and adjoint, Gauss-Newton matvec).
+Tolerances as in test_gpu_parity."""
+import math
+
+import numpy as np
+import pytest
+
+from oracle.registration import Registration
+from paper_1503_00757_gb300 import synth
+
+from .gpu_util import check, check_rel, to_gpu, to_np
+from .test_gpu_parity import OP_TOL, cfl_scaled, op_cond, op_tol
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1503_00757_gb300.binding import lib
+    lib()
+
+
+def _run(ctx, n, mT, mR, v, vt):
+    import torch
+    m1 = torch.empty(n, n, device="cuda")
+    g, b, Hv, bt = (torch.empty(2, n, n, device="cuda") for _ in range(4))
+    ctx.set_images(to_gpu(mT), to_gpu(mR))
+    J = ctx.objective(to_gpu(v), m1)
+    ctx.gradient(to_gpu(v), g)
+    ctx.body_force(b)
+    ctx.hessian_matvec(to_gpu(vt), Hv)
+    ctx.body_force(bt)
+    torch.cuda.synchronize()
+    return dict(J=J, m1=to_np(m1), g=to_np(g), b=to_np(b), Hv=to_np(Hv), bt=to_np(bt))
+
+
+CASES = [
+    # n, nt, regnorm, beta_v, beta_w
+    (16, 8, 1, 1e-2, math.inf),
+    (32, 4, 2, 1e-2, 0.0),
+    (64, 8, 1, 1e-3, 1e-3),
+    (128, 16, 1, 1e-3, math.inf),
+    (128, 8, 2, 1e-3, 1e-3),
+    (256, 8, 1, 1e-3, math.inf),
+    (256, 4, 2, 1e-2, 0.0),
+]
+
+
+@pytest.mark.parametrize("case", CASES)
+def test_cluster_transport_matches_oracle_and_two_kernel_path(case):
+    from paper_1503_00757_gb300.binding import Context
+    n, nt, regnorm, bv, bw = case
+    # smooth blob images below 128^2 (the ellipse images' edges are unresolved there), ellipses above
+    if n <= 64:
+        mT, mR, vs = synth.blobs_pair(n, 2200 + n, vmax=0.2, kmax=2)
+    else:
+        mT, mR, vs = synth.ellipses_pair(n, 2200 + n, vmax=0.2, kmax=max(2, n // 16))
+    v = 0.5 * cfl_scaled(vs, n, n, nt, cfl=0.25)  # half the displacement: lam = m_R - m_1 does not cancel
+    vt = synth.velocity(n, n, max(2, n // 8), 0.3, np.random.default_rng(n + 3), grad_fraction=0.5)
+    P = Registration(mT, mR, nt, regnorm=regnorm, beta_v=bv, beta_w=bw)
+    J_ref, m_ref = P.objective(v)
+    g_ref, _ = P.gradient(v)
+    b_ref = P.b.copy()
+    Hv_ref = P.matvec(vt)
+    bt_ref = P.bt.copy()
+
+    ctx = Context(n, n, nt, regnorm=regnorm, beta=bv, gamma=bw)
+    ctx.set_transport(True)
+    use, cs, active = ctx.transport_config()
+    assert use == 1 and cs == max(1, n * n // 16384) and active >= 1
+    out = _run(ctx, n, mT, mR, v, vt)
+    ctx.set_transport(False)
+    assert ctx.transport_config()[0] == 0
+    two = _run(ctx, n, mT, mR, v, vt)
+    ctx.close()
+
+    # the two transport paths agree to FP32 rounding
+    for k in ("m1", "b", "bt"):
+        check_rel(f"{k}: cluster vs two-kernel", out[k], two[k], OP_TOL)
+    for tag, res in ((" (two-kernel path)", two), ("", out)):
+        check_rel("m1" + tag, res["m1"], m_ref[-1], OP_TOL)
+        check("J" + tag, abs(res["J"] - J_ref) / abs(J_ref), OP_TOL)
+        check_rel("b" + tag, res["b"], b_ref, OP_TOL)
+        check_rel("g" + tag, res["g"], g_ref, op_tol(bv, regnorm, n, n, v, g_ref, b_ref),
+                  cond=op_cond(bv, regnorm, v, g_ref, b_ref))
+        check_rel("b~" + tag, res["bt"], bt_ref, OP_TOL)
+        check_rel("H v~" + tag, res["Hv"], Hv_ref, op_tol(bv, regnorm, n, n, vt, Hv_ref, bt_ref),
+                  cond=op_cond(bv, regnorm, vt, Hv_ref, bt_ref))
+
+
+def test_cluster_solve_matches_two_kernel_solve():
+    """A full registration (Algorithm 1) on the cluster path reaches the tolerance with the
+    Newton count of the two-kernel path and the same velocity to 1e-3 (the end-to-end bar)."""
+    import torch
+    from paper_1503_00757_gb300.binding import Context
+    n, nt = 128, 16
+    mT, mR, _ = synth.ellipses_pair(n, 3100, vmax=0.2)
+    res = []
+    for cluster in (True, False):
+        ctx = Context(n, n, nt, regnorm=1, beta=1e-3, gamma=math.inf)
+        ctx.set_transport(cluster)
+        ctx.set_images(to_gpu(mT), to_gpu(mR))
+        v = torch.zeros(2, n, n, device="cuda")
+        st = ctx.solve(v)
+        torch.cuda.synchronize()
+        res.append((st, to_np(v)))
+        ctx.close()
+    (s0, v0), (s1, v1) = res
+    assert s0["status"] == 0 and s0["gnorm_rel"] <= 1e-2
+    assert s0["n_newton"] == s1["n_newton"]
+    check_rel("solve v: cluster vs two-kernel", v0, v1, 1e-3)
