@@ -503,12 +503,18 @@ def main():
         net.close()
         return
 
-    import torch
-    import torch.distributed as dist
-
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
+    # the oracle on the host cores first, before this process touches the GPU (its worker
+    # processes are spawned; measured on an otherwise idle host)
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline and not (args.profile or args.profile_grid):
+        cpu = cpu_oracle_baseline(PDE_PER_REG)
+
+    import torch
+    import torch.distributed as dist
+
     if world > 1:
         dist.init_process_group("nccl", init_method="env://")
     torch.cuda.set_device(local)
@@ -806,10 +812,6 @@ def main():
     from paper_1503_00757_gb300.binding import fp32_peak
     fp32_tf, _ = fp32_peak()
     peak, peak_kind = peaks()
-
-    cpu = None
-    if rank == 0 and not args.no_cpu_baseline:
-        cpu = cpu_oracle_baseline(stats.get("n_pde", PDE_PER_REG))
 
     if rank == 0:
         names = ["column FFT + multiplier", "row FFT + RK2 stage", "row FFT (other)", "pointwise/reduction"]

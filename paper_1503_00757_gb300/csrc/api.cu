@@ -182,7 +182,7 @@ extern "C" int reg_create(reg_grid grid, int nt, int regnorm, double beta, doubl
     c->npart = 5 * 304 + 4096;
     if (ok && cudaMalloc(&c->d_scal, sizeof(double) * SL_COUNT) != cudaSuccess) ok = false;
     if (ok && cudaMalloc(&c->d_part, sizeof(double) * c->npart) != cudaSuccess) ok = false;
-    if (ok && cudaMalloc(&c->tw, sizeof(float2) * REG_TW_N) != cudaSuccess) ok = false;
+    if (ok && cudaMalloc(&c->tw, sizeof(float2) * REG_TW_TOTAL) != cudaSuccess) ok = false;
     if (ok && cudaMallocHost(&c->h_scal, sizeof(double) * SL_COUNT) != cudaSuccess) ok = false;
     if (!ok) {
         cudaGetLastError();

@@ -11,8 +11,10 @@
 // in both directions (the 1/(n1 n2) factor is applied with the Fourier
 // multiplier).
 //
-// Twiddles w^e = exp(-2 pi i e / 1024) come from a table filled once by the
-// host from FP64 sin/cos; length L reads entry e * (1024 / L).
+// Twiddles come from per-pass tables (fft.cuh) filled once by the host from FP64
+// sin/cos, laid out so that a warp reads consecutive entries.  The exchange
+// buffers are padded (fft_pad) so that a pass's stores are free of bank
+// conflicts.
 #pragma once
 #include <cuda_runtime.h>
 
@@ -49,15 +51,22 @@ __device__ __forceinline__ void dft8(float2 (&x)[8]) {
     x[3] = cadd(E3, t3); x[7] = csub(E3, t3);
 }
 
+// twiddle w^(p k s) of pass i (see fft.cuh), from the per-pass table of length 2^LOGL
 template <int LOGL, bool INV>
-__device__ __forceinline__ float2 twiddle(const float2* __restrict__ tw, int e) {
-    float2 w = __ldg(&tw[e << (REG_LOG_TW_N - LOGL)]);
+__device__ __forceinline__ float2 twiddle(const float2* __restrict__ tw, int i, int k, int p) {
+    float2 w = __ldg(&tw[twp_base(LOGL) + tw_off(LOGL, i) + (k - 1) * tw_groups(LOGL, i) + p]);
     if (INV) w.y = -w.y;
     return w;
 }
 
+// Exchange-buffer index with one padding slot every 8 entries: a radix-8 pass stores 8
+// consecutive entries per thread (stride 8 between threads), which without the padding puts
+// 16 threads of a warp on the same shared-memory banks.  A buffer holds fft_buf(L) entries.
+__host__ __device__ constexpr int fft_buf(int L) { return L + L / 8; }
+__device__ __forceinline__ int fft_pad(int i) { return i + (i >> 3); }
+
 // All threads of the CTA must call this together (it contains __syncthreads).
-// bA, bB: this FFT's two exchange buffers of L float2 each.  Threads with
+// bA, bB: this FFT's two exchange buffers of fft_buf(L) float2 each.  Threads with
 // active == false take part in the barriers only.
 template <int LOGL, bool INV>
 __device__ __forceinline__ void reg_fft(float2 (&x)[8], int t, bool active, float2* bA, float2* bB,
@@ -79,14 +88,14 @@ __device__ __forceinline__ void reg_fft(float2 (&x)[8], int t, bool active, floa
         if (active) {
             if (i > 0) {
 #pragma unroll
-                for (int k = 0; k < 8; ++k) x[k] = cur[q + s * (p + k * m)];
+                for (int k = 0; k < 8; ++k) x[k] = cur[fft_pad(q + s * (p + k * m))];
             }
             dft8<INV>(x);
             if (!last) {
 #pragma unroll
                 for (int k = 0; k < 8; ++k) {
-                    const float2 y = (k == 0) ? x[k] : cmul(x[k], twiddle<LOGL, INV>(tw, p * k * s));
-                    nxt[q + s * (8 * p + k)] = y;
+                    const float2 y = (k == 0) ? x[k] : cmul(x[k], twiddle<LOGL, INV>(tw, i, k, p));
+                    nxt[fft_pad(q + s * (8 * p + k))] = y;
                 }
             }
         }
@@ -100,7 +109,7 @@ __device__ __forceinline__ void reg_fft(float2 (&x)[8], int t, bool active, floa
         if (active) {
 #pragma unroll
             for (int j = 0; j < 4; ++j) {
-                const float2 a = cur[t + j * T], b = cur[t + j * T + 4 * T];
+                const float2 a = cur[fft_pad(t + j * T)], b = cur[fft_pad(t + j * T + 4 * T)];
                 x[j] = cadd(a, b);
                 x[j + 4] = csub(a, b);
             }
@@ -111,7 +120,8 @@ __device__ __forceinline__ void reg_fft(float2 (&x)[8], int t, bool active, floa
 #pragma unroll
             for (int j = 0; j < 2; ++j) {
                 const int q = t + j * T;
-                const float2 a0 = cur[q], a1 = cur[q + 2 * T], a2 = cur[q + 4 * T], a3 = cur[q + 6 * T];
+                const float2 a0 = cur[fft_pad(q)], a1 = cur[fft_pad(q + 2 * T)], a2 = cur[fft_pad(q + 4 * T)],
+                             a3 = cur[fft_pad(q + 6 * T)];
                 const float2 t0 = cadd(a0, a2), t1 = csub(a0, a2), t2 = cadd(a1, a3), t3 = mul_mi<INV>(csub(a1, a3));
                 x[j] = cadd(t0, t2);
                 x[j + 2] = cadd(t1, t3);

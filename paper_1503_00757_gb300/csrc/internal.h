@@ -106,7 +106,7 @@ struct reg_ctx {
     int npart;
     double* h_scal;  // pinned host mirror
 
-    float2* tw;      // twiddle table (REG_TW_N entries)
+    float2* tw;      // twiddle tables (REG_TW_TOTAL entries, fft.cuh layout)
 
     bool tc_ok;        // the cluster-resident transport kernel can run on this grid and device
     bool use_tc;       // transport solves run in the cluster-resident kernel (else the two-pass kernels)
@@ -135,6 +135,11 @@ bool tuned_tiles(int dev, int n1, int n2, int* R, int* C, int* P, int* D, int* T
 
 // ---- launchers (kernels.cu); all asynchronous on ctx->stream ----
 cudaError_t k_init_twiddles(reg_ctx* ctx);
+// host: fill the REG_TW_TOTAL twiddle entries (fft.cuh layout) from FP64 sin / cos
+void fill_twiddles(float2* h);
+// shared memory of a row kernel with R rows of length L, and of the column kernel with C columns
+size_t row_smem(int R, int L);
+size_t col_smem(int C, int L, bool div1);
 
 void launch_r2c_scalar(reg_ctx* ctx, const float* f, float2* S);
 void launch_r2c_vec(reg_ctx* ctx, const float* u1, const float* u2, float2* S1, float2* S2);

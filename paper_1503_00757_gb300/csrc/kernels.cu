@@ -89,13 +89,31 @@ void ktimer_end(reg_ctx* ctx) {
     ktimer_record(ctx, ctx->events.back().b);
 }
 
-cudaError_t k_init_twiddles(reg_ctx* ctx) {
-    std::vector<float2> h(REG_TW_N);
+void fill_twiddles(float2* h) {
+    // w^t = exp(-2 pi i t / 1024), t < 1024
     for (int t = 0; t < REG_TW_N; ++t) {
-        double a = -2.0 * M_PI * (double)t / (double)REG_TW_N;
+        const double a = -2.0 * M_PI * (double)t / (double)REG_TW_N;
         h[t] = make_float2((float)std::cos(a), (float)std::sin(a));
     }
-    return cudaMemcpy(ctx->tw, h.data(), sizeof(float2) * REG_TW_N, cudaMemcpyHostToDevice);
+    // per-pass tables of the lengths 2^4 .. 2^10 (layout in fft.cuh), from the exact angles
+    for (int logl = 4; logl <= 10; ++logl) {
+        const int L = 1 << logl;
+        for (int i = 0; i < tw_passes(logl); ++i) {
+            const int P = tw_groups(logl, i), s = 1 << (3 * i);
+            for (int k = 1; k <= 7; ++k)
+                for (int p = 0; p < P; ++p) {
+                    const double a = -2.0 * M_PI * (double)(p * k * s) / (double)L;
+                    h[twp_base(logl) + tw_off(logl, i) + (k - 1) * P + p] =
+                        make_float2((float)std::cos(a), (float)std::sin(a));
+                }
+        }
+    }
+}
+
+cudaError_t k_init_twiddles(reg_ctx* ctx) {
+    std::vector<float2> h(REG_TW_TOTAL);
+    fill_twiddles(h.data());
+    return cudaMemcpy(ctx->tw, h.data(), sizeof(float2) * REG_TW_TOTAL, cudaMemcpyHostToDevice);
 }
 
 // ---------------------------------------------------------------------------
@@ -191,7 +209,7 @@ __global__ void __launch_bounds__(512) k_r2c(const float* __restrict__ f1, const
             }
         }
     }
-    reg_fft<LOGL, false>(x, t, active, X + 2 * q * L, X + 2 * q * L + L, tw);
+    reg_fft<LOGL, false>(x, t, active, X + 2 * q * fft_buf(L), X + 2 * q * fft_buf(L) + fft_buf(L), tw);
     if (active) {
 #pragma unroll
         for (int k = 0; k < 8; ++k) A[q * L + t + k * T] = x[k];
@@ -234,7 +252,7 @@ __global__ void __launch_bounds__(512) k_c2r(const float2* __restrict__ S1, cons
             x[k] = VEC ? merged_entry<LOGL>(A, q, A + R * W, q, t + k * T)
                        : merged_entry<LOGL>(A, 2 * q, A, 2 * q + 1, t + k * T);
     }
-    reg_fft<LOGL, true>(x, t, active, X + 2 * q * L, X + 2 * q * L + L, tw);
+    reg_fft<LOGL, true>(x, t, active, X + 2 * q * fft_buf(L), X + 2 * q * fft_buf(L) + fft_buf(L), tw);
     if (active) {
 #pragma unroll
         for (int k = 0; k < 8; ++k) {
@@ -304,7 +322,7 @@ __global__ void __launch_bounds__(512, RowBlocks<PRE>::value) k_row_adv(AdvArgs 
 #pragma unroll
             for (int k = 0; k < 8; ++k) x[k] = merged_entry_d2<LOGL>(A, q, A + R * W, q, t + k * T, c);
         }
-        reg_fft<LOGL, true>(x, t, true, X + 2 * q * L, X + 2 * q * L + L, tw);
+        reg_fft<LOGL, true>(x, t, true, X + 2 * q * fft_buf(L), X + 2 * q * fft_buf(L) + fft_buf(L), tw);
     } else {
 #pragma unroll
         for (int k = 0; k < 8; ++k) x[k] = make_float2(0.f, 0.f);
@@ -345,7 +363,7 @@ __global__ void __launch_bounds__(512, RowBlocks<PRE>::value) k_row_adv(AdvArgs 
             x[k] = make_float2(O[2 * q * L + e], O[(2 * q + 1) * L + e]);
         }
     }
-    reg_fft<LOGL, false>(x, t, act2, X + 2 * q * L, X + 2 * q * L + L, tw);
+    reg_fft<LOGL, false>(x, t, act2, X + 2 * q * fft_buf(L), X + 2 * q * fft_buf(L) + fft_buf(L), tw);
     if (act2) {
 #pragma unroll
         for (int k = 0; k < 8; ++k) A[q * L + t + k * T] = x[k];
@@ -370,7 +388,7 @@ template <int LOGL>
 __device__ __forceinline__ void flux_fft_store(float2 (&x)[8], int q, int t, int R, int row0, float2* A, float2* X,
                                                float2* F1, float2* F2, const float2* __restrict__ tw) {
     constexpr int L = 1 << LOGL, T = L >> 3, W = L >> 1;
-    reg_fft<LOGL, false>(x, t, true, X + 2 * q * L, X + 2 * q * L + L, tw);
+    reg_fft<LOGL, false>(x, t, true, X + 2 * q * fft_buf(L), X + 2 * q * fft_buf(L) + fft_buf(L), tw);
 #pragma unroll
     for (int k = 0; k < 8; ++k) A[q * L + t + k * T] = x[k];
     __syncthreads();
@@ -423,7 +441,7 @@ __global__ void __launch_bounds__(512, RowBlocks<PRE>::value) k_row_adj(AdjArgs 
 #pragma unroll
         for (int k = 0; k < 8; ++k) x[k] = merged_entry<LOGL>(A, 2 * q, A, 2 * q + 1, t + k * T);
     }
-    reg_fft<LOGL, true>(x, t, act1, X + 2 * q * L, X + 2 * q * L + L, tw);
+    reg_fft<LOGL, true>(x, t, act1, X + 2 * q * fft_buf(L), X + 2 * q * fft_buf(L) + fft_buf(L), tw);
     float* O = reinterpret_cast<float*>(A);
     if (act1) {
 #pragma unroll
@@ -627,7 +645,7 @@ __global__ void __launch_bounds__(256) k_col(ColArgs a, const float2* __restrict
     const int W = a.n2 >> 1;
     float2* A = sm;
     float2* X = sm + C * L;
-    float2* B2 = sm + 3 * C * L;  // OP_DIV1: the untransformed second input, staged with the first
+    float2* B2 = X + 2 * C * fft_buf(L);  // OP_DIV1: the untransformed second input, staged with the first
     const int c = threadIdx.x / T, t = threadIdx.x - c * T;
     const int e0 = blockIdx.x * C;
     const int e = e0 + c;
@@ -646,13 +664,13 @@ __global__ void __launch_bounds__(256) k_col(ColArgs a, const float2* __restrict
         __syncthreads();
 #pragma unroll
         for (int k = 0; k < 8; ++k) xin[f][k] = A[c * L + t + k * T];
-        reg_fft<LOGL, false>(xin[f], t, true, X + 2 * c * L, X + 2 * c * L + L, tw);
+        reg_fft<LOGL, false>(xin[f], t, true, X + 2 * c * fft_buf(L), X + 2 * c * fft_buf(L) + fft_buf(L), tw);
     }
     float2 y[NOUT > 0 ? NOUT : 1][8];
     double eacc = 0.0;
     if (e0 == 0) {
         // packed column 0: stage every input's column-0 spectrum (natural order) for the -k1 partner
-        float2* Zs = sm;  // NIN * L <= 3 * C * L entries
+        float2* Zs = sm;  // NIN * L <= C * L + 2 * C * fft_buf(L) entries
         __syncthreads();
         if (c == 0) {
 #pragma unroll
@@ -699,7 +717,7 @@ __global__ void __launch_bounds__(256) k_col(ColArgs a, const float2* __restrict
 #pragma unroll
     for (int o = 0; o < NOUT; ++o) {
         __syncthreads();
-        reg_fft<LOGL, true>(y[o], t, true, X + 2 * c * L, X + 2 * c * L + L, tw);
+        reg_fft<LOGL, true>(y[o], t, true, X + 2 * c * fft_buf(L), X + 2 * c * fft_buf(L) + fft_buf(L), tw);
 #pragma unroll
         for (int k = 0; k < 8; ++k) A[c * L + t + k * T] = y[o][k];
         __syncthreads();
@@ -739,17 +757,25 @@ void default_tiles(int n1, int n2, int* R_out, int* C_out, int* P_out) {
     *C_out = C > W ? W : C;
 }
 
+// Shared memory of a row kernel with R rows of length L (staging: R L; exchange: two padded
+// buffers per transform, at most R transforms) and of the column kernel with C columns of
+// length L (staging C L, two padded buffers per column, and C L more for OP_DIV1).
+size_t row_smem(int R, int L) { return ((size_t)R * L + 2 * (size_t)R * fft_buf(L)) * sizeof(float2); }
+size_t col_smem(int C, int L, bool div1) {
+    return ((size_t)C * L * (div1 ? 2 : 1) + 2 * (size_t)C * fft_buf(L)) * sizeof(float2);
+}
+
 // Launch limits of the row kernels (32 to 512 threads; 2 CTAs per SM for
 // 1024-point rows) and the column kernel (32 to 256 threads), and 227 KB of
-// shared memory (3 complex buffers of R rows, up to 4 of C columns).
+// shared memory.
 bool tiles_valid(int n1, int n2, int R, int C, int P) {
     const size_t smax = 227 * 1024;
     if (P != 0 && (P != 1 || n2 > 512)) return false;
     const int W = n2 / 2;
     if (R < 4 || (R & 3) || R > n1 || (n1 % R)) return false;
-    if (R * (n2 / 8) < 32 || R * (n2 / 8) > 512 || 3 * (size_t)R * n2 * sizeof(float2) > smax) return false;
+    if (R * (n2 / 8) < 32 || R * (n2 / 8) > 512 || row_smem(R, n2) > smax) return false;
     if (C < 2 || (C & (C - 1)) || C > W || (W % C)) return false;
-    if (C * (n1 / 8) < 32 || C * (n1 / 8) > 256 || 4 * (size_t)C * n1 * sizeof(float2) > smax) return false;
+    if (C * (n1 / 8) < 32 || C * (n1 / 8) > 256 || col_smem(C, n1, true) > smax) return false;
     return true;
 }
 
@@ -816,7 +842,7 @@ static RowCfg row_cfg(reg_ctx* ctx) {
     c.R = rows_per_cta(ctx);
     c.pre = prefetch_rows(ctx);
     c.threads = c.R * (L / 8);
-    c.smem = 3 * (size_t)c.R * L * sizeof(float2);
+    c.smem = row_smem(c.R, L);
     c.grid = ctx->n1 / c.R;
     return c;
 }
@@ -914,7 +940,7 @@ static void launch_col_t(reg_ctx* ctx, const float2* const* in, float2* const* o
                          double* part) {
     const int L = ctx->n1, W = ctx->n2 / 2;
     const int cpb = cols_per_cta(ctx);
-    const size_t smem = (OP == OP_DIV1 ? 4 : 3) * (size_t)cpb * L * sizeof(float2);
+    const size_t smem = col_smem(cpb, L, OP == OP_DIV1);
     ColArgs a;
     for (int f = 0; f < 5; ++f) a.in[f] = (f < NIN) ? in[f] : nullptr;
     if (OP == OP_DIV1) a.in[1] = in[1];  // read untransformed in the store phase

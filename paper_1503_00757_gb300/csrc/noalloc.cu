@@ -21,8 +21,8 @@
 
 // Scratch of the three packed half spectra (f^, d1 f^, d2 f^): 3 MiB.
 static __device__ __align__(256) float2 g_static_scratch[3 * (REG_STATIC_MAX_NODES / 2)];
-// Twiddle table exp(-2 pi i t / 1024), filled at set-up.
-static __device__ __align__(256) float2 g_static_twiddles[REG_TW_N];
+// Twiddle tables (the layout of fft.cuh), filled at set-up.
+static __device__ __align__(256) float2 g_static_twiddles[REG_TW_TOTAL];
 
 namespace {
 struct StaticDevice {
@@ -45,11 +45,8 @@ int static_setup(int dev) {
     if (e != cudaSuccess) return reg_fail(REG_ERR_CUDA, std::string("cudaGetSymbolAddress(scratch): ") + cudaGetErrorString(e));
     e = cudaGetSymbolAddress((void**)&s.tw, g_static_twiddles);
     if (e != cudaSuccess) return reg_fail(REG_ERR_CUDA, std::string("cudaGetSymbolAddress(twiddles): ") + cudaGetErrorString(e));
-    float2 h[REG_TW_N];
-    for (int t = 0; t < REG_TW_N; ++t) {
-        const double a = -2.0 * M_PI * (double)t / (double)REG_TW_N;
-        h[t] = make_float2((float)std::cos(a), (float)std::sin(a));
-    }
+    static float2 h[REG_TW_TOTAL];  // under g_static_mu
+    fill_twiddles(h);
     e = cudaMemcpyToSymbol(g_static_twiddles, h, sizeof(h));
     if (e != cudaSuccess) return reg_fail(REG_ERR_CUDA, std::string("twiddle upload: ") + cudaGetErrorString(e));
     // A copy from pageable host memory may return once the data is staged; the first

@@ -52,26 +52,11 @@ constexpr int TC_THREADS = 512;
 // __syncthreads).  The caller must __syncthreads before the first call if buf
 // still holds data other threads are reading, and after it before writing buf.
 // ---------------------------------------------------------------------------
-// Twiddles of the radix-8 passes, staged per pass in shared memory so that the threads
-// of a warp read consecutive entries (or one entry): pass i (stride s = 8^i) multiplies
-// output k of butterfly group p = t >> 3i by w^(p k s), w = exp(-2 pi i / L); it reads
-// entry tw_off(i) + (k - 1) P_i + p with P_i = L / (8 s).  Filled by tw_stage.
-__host__ __device__ constexpr int tw_groups(int logl, int i) { return 1 << (logl - 3 * i - 3); }
-__host__ __device__ constexpr int tw_off(int logl, int i) { return i == 0 ? 0 : tw_off(logl, i - 1) + 7 * tw_groups(logl, i - 1); }
-// passes that apply twiddles: all radix-8 passes but a final one
-__host__ __device__ constexpr int tw_passes(int logl) { return (logl % 3 == 0) ? logl / 3 - 1 : logl / 3; }
-__host__ __device__ constexpr int tw_entries(int logl) { return tw_off(logl, tw_passes(logl)); }
-
+// The per-pass twiddle table of the transform length (fft.cuh layout: the threads of a warp
+// read consecutive entries) is staged in shared memory once per launch.
 template <int LOGL>
 __device__ void tw_stage(float2* twp, const float2* __restrict__ tw_global) {
-#pragma unroll
-    for (int i = 0; i < tw_passes(LOGL); ++i) {
-        const int P = tw_groups(LOGL, i), s = 1 << (3 * i);
-        for (int idx = threadIdx.x; idx < 7 * P; idx += TC_THREADS) {
-            const int k = idx / P + 1, p = idx - (k - 1) * P;
-            twp[tw_off(LOGL, i) + idx] = tw_global[(p * k * s) << (REG_LOG_TW_N - LOGL)];
-        }
-    }
+    for (int idx = threadIdx.x; idx < tw_entries(LOGL); idx += TC_THREADS) twp[idx] = tw_global[twp_base(LOGL) + idx];
 }
 
 template <int LOGL, bool INV>
@@ -95,7 +80,7 @@ struct TcGeom {
     static constexpr int QR = Q < R ? Q : R;  // rows per row-phase round
     static constexpr int QC = Q < C ? Q : C;  // columns per column-phase round
     static constexpr int RW = R * W;          // complex entries of one spectra buffer
-    static constexpr int SLOT = n + n / 8;    // one transform's exchange buffer (padded, see fft_pad)
+    static constexpr int SLOT = fft_buf(n);   // one transform's exchange buffer (padded, see fft_pad)
     static constexpr int GCOL = SLOT + 1;     // column stride of the column buffer
     static constexpr int OROW = QR * SLOT;    // row phase: offset of the real-valued staging rows
     static constexpr int ROWX = OROW + QR * n / 2;
@@ -106,11 +91,6 @@ struct TcGeom {
     static_assert(R % QR == 0 && C % QC == 0 && QR % 2 == 0 && C % 2 == 0, "tiling");
     static_assert(SMEM <= 227 * 1024, "shared memory per CTA");
 };
-
-// Exchange-buffer index with one padding slot every 8 entries: the radix-8 passes store
-// 8 consecutive entries per thread (stride 8 between threads), which without padding puts
-// 16 threads of a warp on the same banks.  A buffer holds L + L/8 entries.
-__device__ __forceinline__ int fft_pad(int i) { return i + (i >> 3); }
 
 template <int LOGL, bool INV>
 __device__ __forceinline__ void fft_ip(float2 (&x)[8], int t, bool active, float2* buf, const float2* tws) {

@@ -27,8 +27,11 @@ def valid_tiles(n1, n2):
     while R <= n1:
         C = 2
         while C <= n2 // 2:
-            ok = (n1 % R == 0 and 32 <= R * n2 // 8 <= 512 and 3 * R * n2 * 8 <= 227 * 1024 and
-                  (n2 // 2) % C == 0 and 32 <= C * n1 // 8 <= 256 and 4 * C * n1 * 8 <= 227 * 1024)
+            # shared memory: staging plus two exchange buffers of L + L/8 entries per transform
+            row_smem = (R * n2 + 2 * R * (n2 + n2 // 8)) * 8
+            col_smem = (2 * C * n1 + 2 * C * (n1 + n1 // 8)) * 8
+            ok = (n1 % R == 0 and 32 <= R * n2 // 8 <= 512 and row_smem <= 227 * 1024 and
+                  (n2 // 2) % C == 0 and 32 <= C * n1 // 8 <= 256 and col_smem <= 227 * 1024)
             if ok:
                 for P in ((0, 1) if n2 <= 512 else (0,)):
                     out.append((R, C, P))
