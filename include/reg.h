@@ -41,7 +41,7 @@ typedef struct {
     int n2; /* nodes along x^2 (columns, contiguous) */
 } reg_grid;
 
-enum reg_norm { REG_H1 = 1, REG_H2 = 2 };
+enum reg_norm { REG_H1 = 1, REG_H2 = 2, REG_H3 = 3 };
 
 enum reg_status {
     REG_OK = 0,
@@ -98,7 +98,8 @@ void reg_default_opts(reg_solve_opts* opts);
 
 /* Create a context.  Problem (Eq. (e:objective)-(e:constraint-divv)):
  *   nt       time steps of the RK2 transport solves (Sec. 4), >= 1;
- *   regnorm  REG_H1 or REG_H2 seminorm on v (Eq. (e:reg-v));
+ *   regnorm  REG_H1 or REG_H2 seminorm on v (Eq. (e:reg-v)), or REG_H3 (the
+ *            triharmonic control equation App. A.1 names: symbol |k|^6);
  *   beta     beta_v > 0;
  *   gamma    beta_w of the mass-source H1 norm (Eq. (e:reg-w)); 0 disables the
  *            divergence constraint (the paper's gamma = 0); +INFINITY enforces
@@ -143,7 +144,7 @@ int reg_apply_precond(reg_ctx* ctx, const float* r, float* out);
 /* Square root of the preconditioner, Q = (beta_v A')^(1/2) with A'(0) = 1
  * (App. E.2): out = Q x (inverse = 0) or Q^-1 x (inverse != 0), per Fourier
  * mode, on a velocity field (2 n1 n2 floats, device).  reg_solve iterates on
- * y = Q v for the H2 seminorm. */
+ * y = Q v for the H2 and H3 seminorms. */
 int reg_apply_precond_sqrt(reg_ctx* ctx, const float* x, float* out, int inverse);
 
 /* ---- state solve, objective, adjoint, reduced gradient ---- */
@@ -159,9 +160,24 @@ int reg_gradient(reg_ctx* ctx, const float* v, float* g, double* J);
 /* ---- Gauss-Newton Hessian matvec ---- */
 
 /* H v~ = beta_v B[v~] + L[b~] (Eq. (e:inc-control-eq-elim)) with the
- * Gauss-Newton approximation (lambda terms dropped, Sec. 4), at the v of the
- * last reg_gradient call (REG_ERR_STATE otherwise). */
+ * Gauss-Newton approximation (lambda terms dropped, Sec. 4), or the full
+ * Newton Hessian (reg_set_hessian), at the v of the last reg_gradient call
+ * (REG_ERR_STATE otherwise). */
 int reg_hessian_matvec(reg_ctx* ctx, const float* vt, float* Hvt);
+
+/* Hessian of reg_hessian_matvec and reg_solve.  full = 0 (default): Gauss-
+ * Newton (Sec. 4: lambda set to zero in Eq. (e:second-order-elim)).  full != 0:
+ * the full Newton Hessian of Eq. (e:second-order-elim): the incremental
+ * adjoint keeps its source -div(lam v~) and the incremental body force is
+ * b~ = int lam~ grad m + lam grad m~ dt (trapezoid in time), with lam the
+ * adjoint of the last reg_gradient (whose history the context then stores:
+ * (nt+1) n1 n2 floats more, and 2 (nt+1) n1 n2 for grad m~).  This Hessian
+ * need not be positive definite away from a minimizer; PCG stops at a
+ * non-positive curvature and the line search falls back to the
+ * preconditioned gradient step (reg_solve).  Transport solves then run on the
+ * row/column kernel pairs (reg_set_transport is ignored).  Invalidates the
+ * linearization point.  REG_ERR_NOMEM if the histories cannot be allocated. */
+int reg_set_hessian(reg_ctx* ctx, int full);
 
 /* Body force of the last reg_gradient (b = int lam grad m dt, Sec. 3.1) or
  * incremental body force of the last reg_hessian_matvec (b~ with the
@@ -174,12 +190,12 @@ int reg_body_force(reg_ctx* ctx, float* b_out);
 /* v_inout (device, 2*n1*n2): initial guess if opts->warm_start, else ignored
  * (v_0 = 0); receives the final velocity.  opts NULL = defaults.  stats
  * (nullable, host).  Returns REG_OK, REG_ERR_LINESEARCH, REG_ERR_MAXIT,
- * REG_ERR_NAN or an argument/CUDA error.  With the H2 seminorm (and no shear
- * term) the iteration runs on y = Q v, Q = (beta_v A')^(1/2) (see
+ * REG_ERR_NAN or an argument/CUDA error.  With the H2 or H3 seminorm (and no
+ * shear term) the iteration runs on y = Q v, Q = (beta_v A')^(1/2) (see
  * reg_apply_precond_sqrt): the same Algorithms 1 and 2, with PCG on v
  * becoming unpreconditioned CG on y and every test taken on v-space norms,
- * so that the FP32 rounding of v is not amplified by beta_v |k|^4 in the
- * gradient. */
+ * so that the FP32 rounding of v is not amplified by beta_v |k|^4 (|k|^6 for
+ * H3) in the gradient. */
 int reg_solve(reg_ctx* ctx, float* v_inout, const reg_solve_opts* opts, reg_solve_stats* stats);
 
 /* Same solve with HOST buffers: copies m_T, m_R (host, n1*n2 floats) to the

@@ -7,7 +7,8 @@ Follows, in the paper's order and notation:
   * reduced gradient g = beta_v A[v] + K[b] (Eq. (e:control-eq-elim)), with
     the state solve, adjoint solve and body force of Algorithm 1;
   * Gauss-Newton Hessian matvec H v~ = beta_v B[v~] + L[b~]
-    (Eq. (e:inc-control-eq-elim)) with the lambda terms dropped (Sec. 4);
+    (Eq. (e:inc-control-eq-elim)) with the lambda terms dropped (Sec. 4), or the
+    full Newton matvec that keeps them (hessian="full");
   * PCG inner iteration, Algorithm 2, preconditioned by (beta_v A)^-1
     (Appendix E);
   * Armijo backtracking line search (Sec. 4: Nocedal-Wright Algorithm 3.1,
@@ -32,7 +33,8 @@ Readings of passages the paper leaves open or garbles:
     w = div v (Eq. (e:reg-w)).
   * If PCG meets a non-positive curvature <s, H s> <= 0 it stops (a plain
     safeguard; the Gauss-Newton Hessian is positive definite in exact
-    arithmetic, Sec. 4).  If the returned step is not a descent direction
+    arithmetic, Sec. 4; the full Hessian need not be far from a minimizer, and
+    this guard is then what keeps the step a descent direction).  If the returned step is not a descent direction
     (<g, v~> >= 0) the preconditioned steepest-descent step -(beta_v A)^-1 g
     is used instead.
   * nt policy: "fixed" uses nt as given; "cfl" uses, at every outer
@@ -45,10 +47,10 @@ import math
 import numpy as np
 
 from . import shear as shear_ops
-from .spectral import (H1, H2, apply_A, apply_K, apply_precond, apply_W, div,
+from .spectral import (H1, H2, H3, apply_A, apply_K, apply_precond, apply_W, div,
                        inner, norm)
 from .transport import (adjoint_solve, body_force, grad_history,
-                        inc_state_solve, state_solve)
+                        inc_adjoint_solve_full, inc_state_solve, state_solve)
 
 STATUS_OK = 0
 STATUS_LINESEARCH = 5
@@ -61,7 +63,7 @@ class Registration:
     (0: gamma = 0; inf: incompressible; else mass source weight) and shear
     knob s (0 = quadratic model; s != 0 requires H1 and beta_w = inf)."""
 
-    def __init__(self, mT, mR, nt, regnorm=H1, beta_v=1e-2, beta_w=np.inf, shear=0.0):
+    def __init__(self, mT, mR, nt, regnorm=H1, beta_v=1e-2, beta_w=np.inf, shear=0.0, hessian="gn"):
         self.mT = np.asarray(mT, dtype=np.float64)
         self.mR = np.asarray(mR, dtype=np.float64)
         self.nt = int(nt)
@@ -69,6 +71,9 @@ class Registration:
         self.beta_v = float(beta_v)
         self.beta_w = float(beta_w)
         self.shear = float(shear)
+        if hessian not in ("gn", "full"):
+            raise ValueError("hessian must be 'gn' (Gauss-Newton) or 'full'")
+        self.hessian = hessian
         if self.shear != 0.0:
             if self.regnorm != H1 or not np.isinf(self.beta_w):
                 raise ValueError("shear control requires H1 and beta_w = inf")
@@ -117,15 +122,21 @@ class Registration:
         return g, J
 
     def matvec(self, vt):
-        """Gauss-Newton Hessian matvec H v~ (Eqs. (e:inc-state-eq-elim),
-        (e:inc-adj-eq-elim), (e:inc-control-eq-elim), lambda terms dropped)
-        at the point of the last ``gradient`` call (Algorithm 2)."""
+        """Hessian matvec H v~ (Eqs. (e:inc-state-eq-elim), (e:inc-adj-eq-elim),
+        (e:inc-control-eq-elim)) at the point of the last ``gradient`` call (Algorithm 2):
+        Gauss-Newton (lambda terms dropped, Sec. 4) unless ``self.hessian == "full"``, which
+        keeps them: the source -div(lam v~) of the incremental adjoint and the term
+        lam grad m~ of the incremental body force b~ = int lam~ grad m + lam grad m~ dt."""
         vt = np.asarray(vt, dtype=np.float64)
         nt = self.nt_lin
         mt = inc_state_solve(self.v, vt, self.gradm, nt)
-        lt = adjoint_solve(-mt[-1], self.v, nt)
         self.n_pde += 2
-        bt = body_force(lt, self.gradm)
+        if self.hessian == "full":
+            lt = inc_adjoint_solve_full(-mt[-1], self.v, vt, self.lam, nt)
+            bt = body_force(lt, self.gradm) + body_force(self.lam, grad_history(mt))
+        else:
+            lt = adjoint_solve(-mt[-1], self.v, nt)
+            bt = body_force(lt, self.gradm)
         self.bt = bt
         if self.shear != 0.0:
             return shear_ops.leray(self.beta_v * shear_ops.second_variation(self.v, vt, self.nu) + bt)

@@ -18,7 +18,8 @@ Fourier symbols (readings the paper leaves open, stated once here):
     the mass source) use the full |k|^2 with |k_Nyquist| = n/2.
 
 Operators:
-  * A[v] = -Lap v (H1) or Lap^2 v (H2), Eq. (e:var-reg-v): symbol |k|^2 or |k|^4.
+  * A[v] = -Lap v (H1), Lap^2 v (H2) or -Lap^3 v (H3), Eq. (e:var-reg-v) and App. A.1:
+    symbol |k|^2, |k|^4 or |k|^6.
   * K[b] = -grad M^-1 Lap^-1 div b + b, M = beta_v (beta_w(-Lap + I))^-1 + I,
     Eq. (e:project-body-force), derived in Appendix A.1 (Eqs. (e:mass-source),
     (e:pressure-elimination-relaxed-ic), (e:derive-control-eq-elim)).  Taking
@@ -42,6 +43,7 @@ from .fft import fft2, ifft2
 
 H1 = 1
 H2 = 2
+H3 = 3
 
 
 def spacing(shape):
@@ -113,13 +115,16 @@ def lap(f):
 
 
 def reg_symbol(n1, n2, regnorm):
-    """A^(k): |k|^2 for the H1 seminorm, |k|^4 for the H2 seminorm (Eq. (e:var-reg-v))."""
+    """A^(k): |k|^2 for the H1 seminorm, |k|^4 for the H2 seminorm (Eq. (e:var-reg-v)), |k|^6
+    for the H3 seminorm (the triharmonic control equation App. A.1 names as the next choice)."""
     _, _, KK = symbols(n1, n2)
     if regnorm == H1:
         return KK
     if regnorm == H2:
         return KK ** 2
-    raise ValueError("regnorm must be 1 (H1) or 2 (H2)")
+    if regnorm == H3:
+        return KK ** 3
+    raise ValueError("regnorm must be 1 (H1), 2 (H2) or 3 (H3)")
 
 
 def apply_A(v, regnorm):

@@ -87,6 +87,23 @@ def inc_state_solve(v, vt, gradm, nt):
     return mt
 
 
+def inc_adjoint_solve_full(lam_final, v, vt, lam, nt):
+    """Incremental adjoint of the full Newton step, Eq. (e:inc-adj-eq-elim) with the lambda
+    term kept: -d_t lam~ - div(lam~ v) - div(lam v~) = 0, solved backward from
+    lam~(1) = lam_final.  With tau = 1 - t: d_tau lam~ = div(lam~ v) + div(lam v~); the source
+    div(lam v~) is evaluated from the adjoint history lam[j] at the stage times t_j and
+    t_{j-1} (Heun, as for the incremental state).  Returns lam~[j], j = 0..nt."""
+    h = 1.0 / nt
+    lt = np.empty((nt + 1,) + lam_final.shape)
+    lt[nt] = lam_final
+    for j in range(nt, 0, -1):
+        k1 = div(lt[j] * v) + div(lam[j] * vt)
+        ls = lt[j] + h * k1
+        k2 = div(ls * v) + div(lam[j - 1] * vt)
+        lt[j - 1] = lt[j] + 0.5 * h * (k1 + k2)
+    return lt
+
+
 def grad_history(m):
     return np.stack([grad(m[j]) for j in range(m.shape[0])])
 

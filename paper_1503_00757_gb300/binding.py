@@ -12,7 +12,7 @@ import os
 
 from .build import LIB_PATH
 
-REG_H1, REG_H2 = 1, 2
+REG_H1, REG_H2, REG_H3 = 1, 2, 3
 REG_NT_FIXED, REG_NT_CFL = 0, 1
 STATUS = {0: "REG_OK", 1: "REG_ERR_ARG", 2: "REG_ERR_CUDA", 3: "REG_ERR_NOMEM", 4: "REG_ERR_NAN",
           5: "REG_ERR_LINESEARCH", 6: "REG_ERR_PCG_MAXIT", 7: "REG_ERR_TIMEOUT", 8: "REG_WARN_CFL",
@@ -85,6 +85,7 @@ _SIGS = {
     "reg_set_tiles": ([_P, _I, _I, _I], _I),
     "reg_set_pdl": ([_P, _I], _I),
     "reg_set_transport": ([_P, _I], _I),
+    "reg_set_hessian": ([_P, _I], _I),
     "reg_transport_config": ([_P, ctypes.POINTER(_I), ctypes.POINTER(_I), ctypes.POINTER(_I)], _I),
     "reg_fp32_peak": ([ctypes.POINTER(_D), ctypes.POINTER(_D)], _I),
     "reg_net_create": ([_I, _I, _I, ctypes.POINTER(_P)], _I),
@@ -471,3 +472,7 @@ class Context:
         a, b, c = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
         _check(lib().reg_transport_config(self.h, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)))
         return a.value, b.value, c.value
+
+    def set_hessian(self, full):
+        """Full Newton Hessian (True) or Gauss-Newton (False, default) for matvecs and solves."""
+        _check(lib().reg_set_hessian(self.h, 1 if full else 0))

@@ -70,7 +70,24 @@ static void free_hist(reg_ctx* c) {
     clear_graphs(c);  // captured sequences hold history pointers
     cudaFree(c->m_hist);
     cudaFree(c->gm_hist);
-    c->m_hist = c->gm_hist = nullptr;
+    cudaFree(c->lam_hist);
+    cudaFree(c->gmt_hist);
+    c->m_hist = c->gm_hist = c->lam_hist = c->gmt_hist = nullptr;
+}
+
+// full-Newton histories (adjoint lam_j, grad m~_j) at the current capacity
+static int alloc_newton_hist(reg_ctx* c) {
+    if (c->lam_hist) return REG_OK;
+    const size_t N = c->N;
+    if (cudaMalloc(&c->lam_hist, sizeof(float) * N * (c->nt_cap + 1)) != cudaSuccess ||
+        cudaMalloc(&c->gmt_hist, sizeof(float) * 2 * N * (c->nt_cap + 1)) != cudaSuccess) {
+        cudaGetLastError();
+        cudaFree(c->lam_hist);
+        cudaFree(c->gmt_hist);
+        c->lam_hist = c->gmt_hist = nullptr;
+        return reg_fail(REG_ERR_NOMEM, "cudaMalloc of the full-Newton histories failed");
+    }
+    return REG_OK;
 }
 
 static int alloc_hist(reg_ctx* c, int nt) {
@@ -86,6 +103,7 @@ static int alloc_hist(reg_ctx* c, int nt) {
     }
     c->nt_cap = nt;
     c->have_lin = false;
+    if (c->full_newton) return alloc_newton_hist(c);
     return REG_OK;
 }
 
@@ -109,7 +127,8 @@ extern "C" void reg_destroy(reg_ctx* c) {
 
 static int check_params(int nt, int regnorm, double beta, double gamma, double shear) {
     if (nt < 1 || nt > 100000) return reg_fail(REG_ERR_ARG, "nt must be in [1, 100000]");
-    if (regnorm != REG_H1 && regnorm != REG_H2) return reg_fail(REG_ERR_ARG, "regnorm must be REG_H1 or REG_H2");
+    if (regnorm != REG_H1 && regnorm != REG_H2 && regnorm != REG_H3)
+        return reg_fail(REG_ERR_ARG, "regnorm must be REG_H1, REG_H2 or REG_H3");
     if (!(beta > 0.0) || !std::isfinite(beta)) return reg_fail(REG_ERR_ARG, "beta must be finite and > 0");
     if (!(gamma >= 0.0)) return reg_fail(REG_ERR_ARG, "gamma must be >= 0 or +INFINITY");
     if (!(shear > -1.0 && shear < 1.0)) return reg_fail(REG_ERR_ARG, "shear must be in (-1, 1)");
@@ -127,7 +146,7 @@ static void set_params(reg_ctx* c, int nt, int regnorm, double beta, double gamm
     c->shear_model = shear != 0.0;
     c->nu = (1.0 + shear) / (1.0 - shear);
     c->pmode = (gamma == 0.0) ? PROJ_IDENTITY : (std::isinf(gamma) ? PROJ_LERAY : PROJ_MASS);
-    c->ypath = regnorm == REG_H2 && !c->shear_model;
+    c->ypath = regnorm != REG_H1 && !c->shear_model;
     c->have_lin = false;
 }
 
@@ -140,6 +159,8 @@ extern "C" int reg_create(reg_grid grid, int nt, int regnorm, double beta, doubl
 
     reg_ctx* c = new reg_ctx();
     memset(c->S, 0, sizeof(c->S));
+    c->full_newton = false;
+    c->lam_hist = c->gmt_hist = nullptr;
     c->n1 = grid.n1;
     c->n2 = grid.n2;
     c->N = grid.n1 * grid.n2;
@@ -241,9 +262,23 @@ extern "C" int reg_set_transport(reg_ctx* c, int cluster) {
     return REG_OK;
 }
 
+extern "C" int reg_set_hessian(reg_ctx* c, int full) {
+    if (!c) return reg_fail(REG_ERR_ARG, "ctx is NULL");
+    const bool on = full != 0;
+    if (on == c->full_newton) return REG_OK;
+    clear_graphs(c);  // captures bake in the matvec's launch sequence
+    c->have_lin = false;  // the adjoint history belongs to the next reg_gradient
+    c->full_newton = on;
+    if (on) return alloc_newton_hist(c);
+    cudaFree(c->lam_hist);
+    cudaFree(c->gmt_hist);
+    c->lam_hist = c->gmt_hist = nullptr;
+    return REG_OK;
+}
+
 extern "C" int reg_transport_config(reg_ctx* c, int* cluster, int* ctas_per_cluster, int* max_active_clusters) {
     if (!c) return reg_fail(REG_ERR_ARG, "ctx is NULL");
-    if (cluster) *cluster = c->use_tc ? 1 : 0;
+    if (cluster) *cluster = (c->use_tc && !c->full_newton) ? 1 : 0;
     if (ctas_per_cluster) *ctas_per_cluster = c->tc_ok ? tc_cluster_size(c->n1) : 0;
     if (max_active_clusters) *max_active_clusters = c->tc_ok ? tc_max_active_clusters(c->n1, c->n2) : 0;
     return REG_OK;
@@ -463,7 +498,7 @@ static float* gmh(reg_ctx* c, int j) { return c->gm_hist + (size_t)j * 2 * c->N;
 // spectra and is formed by the row kernel from the stage's own spectrum S[0].
 static void state_solve(reg_ctx* c, const float* v, int nt) {
     const float h = 1.0f / (float)nt;
-    if (c->use_tc) {
+    if (c->use_tc && !c->full_newton) {
         TcArgs a = {};
         a.nt = nt; a.h = h; a.v = v; a.mT = c->mT; a.m_hist = c->m_hist; a.gm_hist = c->gm_hist; a.us = c->w0;
         launch_transport_cluster(c, TC_STATE, a);
@@ -495,19 +530,51 @@ static void state_solve(reg_ctx* c, const float* v, int nt) {
 // Adjoint (Eq. (e:adj-eq-elim)) or Gauss-Newton incremental adjoint
 // (Eq. (e:inc-adj-eq-elim)) backward in time from lam_nt = ca*a + cb*cf, with
 // the body force b = int lam grad m dt (trapezoid) accumulated into bout.
+// lhist (nullable): store lam_j at lhist + j N for j = 0..nt (the full Newton matvec reads it).
 static void adjoint_solve(reg_ctx* c, const float* v, int nt, const float* a, float ca, const float* cf, float cb,
-                          float* bout, double* part_jdata) {
+                          float* bout, double* part_jdata, float* lhist = nullptr) {
     const float h = 1.0f / (float)nt;
-    if (c->use_tc && !part_jdata) {
+    if (c->use_tc && !part_jdata && !lhist) {
         TcArgs t = {};
         t.nt = nt; t.h = h; t.v = v; t.gm_hist = c->gm_hist; t.lj = c->w1; t.ls = c->w2;
         t.adj_a = a; t.adj_ca = ca; t.adj_c = cf; t.adj_cb = cb; t.b = bout;
         launch_transport_cluster(c, TC_ADJOINT, t);
         return;
     }
+    float* lst = c->w2;
+    auto lam_at = [&](int j) { return lhist ? lhist + (size_t)j * c->N : c->w1; };
+    launch_adj_init(c, a, ca, cf, cb, v, lam_at(nt), bout, gmh(c, nt), 0.5f * h, c->S[1], c->S[2], part_jdata);
+    const float2* Fin[2] = {c->S[1], c->S[2]};
+    float2* D[1] = {c->S[0]};
+    const SpecParams P = spec_params(c, 0.f);
+    for (int j = nt; j >= 1; --j) {
+        launch_col(c, OP_DIV1, Fin, D, P, nullptr);
+        AdjArgs s1 = {};
+        s1.D = c->S[0]; s1.lj = lam_at(j); s1.ls = nullptr; s1.v = v; s1.l_out = lst;
+        s1.b = nullptr; s1.gm = nullptr; s1.w = 0.f; s1.F1 = c->S[1]; s1.F2 = c->S[2]; s1.h = h; s1.stage = 1;
+        launch_row_adj(c, s1);
+        launch_col(c, OP_DIV1, Fin, D, P, nullptr);
+        AdjArgs s2 = s1;
+        s2.ls = lst; s2.l_out = lam_at(j - 1); s2.stage = 2;
+        s2.b = bout; s2.gm = gmh(c, j - 1); s2.w = (j - 1 == 0) ? 0.5f * h : h;
+        if (j == 1) { s2.F1 = nullptr; s2.F2 = nullptr; }
+        launch_row_adj(c, s2);
+    }
+}
+
+static float* lamh(reg_ctx* c, int j) { return c->lam_hist + (size_t)j * c->N; }
+static float* gmth(reg_ctx* c, int j) { return c->gmt_hist + (size_t)j * 2 * c->N; }
+
+// Full-Newton incremental adjoint (Eq. (e:inc-adj-eq-elim) with the lambda term), backward from
+// lam~_nt = -m~_nt (c->w3): the flux of every divergence is lam~ v + lam v~ with lam from the
+// gradient's adjoint history at the time the divergence is evaluated, and the incremental body
+// force is b~ = sum_j w_j (lam~_j grad m_j + lam_j grad m~_j) (trapezoid).
+static void inc_adjoint_full(reg_ctx* c, const float* v, const float* vt, int nt, float* bout) {
+    const float h = 1.0f / (float)nt;
     float* lam = c->w1;
     float* lst = c->w2;
-    launch_adj_init(c, a, ca, cf, cb, v, lam, bout, gmh(c, nt), 0.5f * h, c->S[1], c->S[2], part_jdata);
+    launch_adj_init(c, nullptr, 0.f, c->w3, -1.f, v, lam, bout, gmh(c, nt), 0.5f * h, c->S[1], c->S[2], nullptr,
+                    lamh(c, nt), vt, gmth(c, nt));
     const float2* Fin[2] = {c->S[1], c->S[2]};
     float2* D[1] = {c->S[0]};
     const SpecParams P = spec_params(c, 0.f);
@@ -516,19 +583,22 @@ static void adjoint_solve(reg_ctx* c, const float* v, int nt, const float* a, fl
         AdjArgs s1 = {};
         s1.D = c->S[0]; s1.lj = lam; s1.ls = nullptr; s1.v = v; s1.l_out = lst;
         s1.b = nullptr; s1.gm = nullptr; s1.w = 0.f; s1.F1 = c->S[1]; s1.F2 = c->S[2]; s1.h = h; s1.stage = 1;
+        s1.lsrc = lamh(c, j - 1); s1.vt = vt; s1.gmt = nullptr;
         launch_row_adj(c, s1);
         launch_col(c, OP_DIV1, Fin, D, P, nullptr);
         AdjArgs s2 = s1;
         s2.ls = lst; s2.l_out = lam; s2.stage = 2;
         s2.b = bout; s2.gm = gmh(c, j - 1); s2.w = (j - 1 == 0) ? 0.5f * h : h;
+        s2.gmt = gmth(c, j - 1);
         if (j == 1) { s2.F1 = nullptr; s2.F2 = nullptr; }
         launch_row_adj(c, s2);
     }
 }
 
 // Incremental state (Eq. (e:inc-state-eq-elim)); leaves m~(1) in c->w3.
-// m~(0) = 0 is passed as u_j = nullptr to both stages of the first step.
-static void inc_state_solve(reg_ctx* c, const float* v, const float* vt, int nt) {
+// m~(0) = 0 is passed as u_j = nullptr to both stages of the first step.  gmt (nullable):
+// store grad m~_j at gmt + j 2N for j = 0..nt (the full Newton matvec reads it).
+static void inc_state_solve(reg_ctx* c, const float* v, const float* vt, int nt, float* gmt = nullptr) {
     const float h = 1.0f / (float)nt;
     float* mj = c->w3;
     float* ms = c->w0;
@@ -542,7 +612,8 @@ static void inc_state_solve(reg_ctx* c, const float* v, const float* vt, int nt)
             a.G1 = c->S[1]; a.Sd2 = c->S[0];
         }
         a.uj = (j > 0) ? mj : nullptr; a.us = nullptr; a.v = v; a.gm = gmh(c, j); a.vt = vt;
-        a.u_out = ms; a.grad_out = nullptr; a.S_out = c->S[0]; a.h = h; a.stage = 1;
+        a.u_out = ms; a.grad_out = gmt ? gmt + (size_t)j * 2 * c->N : nullptr; a.S_out = c->S[0]; a.h = h;
+        a.stage = 1;
         // the first launch of the solve: v~ may come from the launch just before (Q^-1 s in
         // preconditioned coordinates, or a caller's kernel), so it is read after the wait
         a.late = (j == 0) ? 1 : 0;
@@ -550,10 +621,11 @@ static void inc_state_solve(reg_ctx* c, const float* v, const float* vt, int nt)
         a.late = 0;
         launch_col(c, OP_GRAD1, in, G, P, nullptr);
         a.G1 = c->S[1]; a.Sd2 = c->S[0];
-        a.us = ms; a.gm = gmh(c, j + 1); a.u_out = mj; a.stage = 2;
+        a.us = ms; a.gm = gmh(c, j + 1); a.u_out = mj; a.stage = 2; a.grad_out = nullptr;
         a.S_out = (j + 1 < nt) ? c->S[0] : nullptr;
         launch_row_adv(c, a);
     }
+    if (gmt) sp_grad(c, mj, gmt + (size_t)nt * 2 * c->N);
 }
 
 // ---------------------------------------------------------------------------
@@ -595,7 +667,7 @@ static int objective_dev(reg_ctx* c, const float* v, int nt, const float* y = nu
 }
 
 static void gradient_launches(reg_ctx* c, const float* v, float* g, int nt) {
-    adjoint_solve(c, v, nt, c->mR, 1.f, mh(c, nt), -1.f, c->bvec, nullptr);
+    adjoint_solve(c, v, nt, c->mR, 1.f, mh(c, nt), -1.f, c->bvec, nullptr, c->full_newton ? c->lam_hist : nullptr);
     if (c->shear_model) {
         sp_grad_vec(c, v, c->gtmp);
         launch_shear_strain(c, c->gtmp, (float)c->nu, c->E_lin, c->eta_lin, c->T3, nullptr);
@@ -619,7 +691,7 @@ static int gradient_dev(reg_ctx* c, const float* v, float* g, int nt) {
 static int gradient_dev_y(reg_ctx* c, const float* v, const float* y, float* gy, int nt) {
     RET(objective_dev(c, v, nt, y));
     RET(run_seq(c, GK_GRADIENT_Y, v, y, nt, [&] {  // gy is always c->g
-        adjoint_solve(c, v, nt, c->mR, 1.f, mh(c, nt), -1.f, c->bvec, nullptr);
+        adjoint_solve(c, v, nt, c->mR, 1.f, mh(c, nt), -1.f, c->bvec, nullptr, c->full_newton ? c->lam_hist : nullptr);
         sp_assemble_y(c, y, c->bvec, gy);
         if (v != c->v_lin)
             cudaMemcpyAsync(c->v_lin, v, sizeof(float) * 2 * c->N, cudaMemcpyDeviceToDevice, c->stream);
@@ -632,6 +704,11 @@ static int gradient_dev_y(reg_ctx* c, const float* v, const float* y, float* gy,
 // Incremental state and Gauss-Newton incremental adjoint of a matvec (Algorithm 2's product):
 // m~(1) in c->w3, b~ in c->bvec.  The cluster path runs both sweeps in one launch.
 static void inc_solves(reg_ctx* c, const float* vt, int nt) {
+    if (c->full_newton) {
+        inc_state_solve(c, c->v_lin, vt, nt, c->gmt_hist);
+        inc_adjoint_full(c, c->v_lin, vt, nt, c->bvec);
+        return;
+    }
     if (c->use_tc) {
         TcArgs a = {};
         a.nt = nt; a.h = 1.0f / (float)nt; a.v = c->v_lin; a.vt = vt; a.gm_hist = c->gm_hist;

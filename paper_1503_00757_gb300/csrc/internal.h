@@ -108,6 +108,11 @@ struct reg_ctx {
 
     float2* tw;      // twiddle tables (REG_TW_TOTAL entries, fft.cuh layout)
 
+    // full Newton Hessian (reg_set_hessian): adjoint history lam_j of the gradient and the
+    // incremental state's gradient history grad m~_j (allocated while enabled)
+    bool full_newton;
+    float *lam_hist;   // (nt_cap + 1) * N
+    float *gmt_hist;   // (nt_cap + 1) * 2N
     bool tc_ok;        // the cluster-resident transport kernel can run on this grid and device
     bool use_tc;       // transport solves run in the cluster-resident kernel (else the two-pass kernels)
     int tileR, tileC;  // rows per row-kernel CTA, spectrum columns per column-kernel CTA (0: default)
@@ -176,13 +181,19 @@ struct AdjArgs {
     float2 *F1, *F2;        // nullable: flux spectra of l_out
     float h;
     int stage;
+    // full Newton (nullable lsrc = Gauss-Newton): flux l_out v + lsrc v~; stage 2 also b += w lsrc gmt
+    const float* lsrc;      // adjoint state lam at the time of the next divergence
+    const float* vt;        // incremental velocity (2N)
+    const float* gmt;       // grad m~ at the output time (2N)
 };
 void launch_row_adj(reg_ctx* ctx, const AdjArgs& a);
 
 // lam = ca * a + cb * c (a nullable); b = w lam gm; flux spectra of lam v;
-// optional FP64 partials of 0.5 * sum(lam^2) * h1 h2.
+// optional FP64 partials of 0.5 * sum(lam^2) * h1 h2.  Full Newton (lsrc != nullptr):
+// b += w lsrc gmt and the flux is lam v + lsrc vt.
 void launch_adj_init(reg_ctx* ctx, const float* a, float ca, const float* c, float cb, const float* v,
-                     float* lam, float* b, const float* gm, float w, float2* F1, float2* F2, double* part);
+                     float* lam, float* b, const float* gm, float w, float2* F1, float2* F2, double* part,
+                     const float* lsrc = nullptr, const float* vt = nullptr, const float* gmt = nullptr);
 
 // ---- pointwise / reductions ----
 // part[...] <- partial sums of sum_i x_i y_i over n elements; returns #partials

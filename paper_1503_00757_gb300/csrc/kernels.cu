@@ -401,11 +401,16 @@ __device__ __forceinline__ void flux_fft_store(float2 (&x)[8], int q, int t, int
     }
 }
 
-template <int LOGL, bool PRE>
+// FULL (full Newton, Eq. (e:inc-adj-eq-elim) with the lambda term): the flux of the next
+// divergence is lam_out v + lam_src v~ (lam_src: the adjoint state at the time that divergence
+// is evaluated) and stage 2 adds w lam_src grad m~ to the body force.  Compiled only without
+// prefetch, with a smaller load batch (more operands per element).
+template <int LOGL, bool PRE, bool FULL>
 __global__ void __launch_bounds__(512, RowBlocks<PRE>::value) k_row_adj(AdjArgs a, int N, int R,
                                                                            const float2* __restrict__ tw) {
     extern __shared__ __align__(16) float2 sm[];
     constexpr int L = 1 << LOGL, T = L >> 3, W = L >> 1;
+    constexpr int BATCH = FULL ? 2 : ADJ_LOAD_BATCH;
     float2* A = sm;
     float2* X = sm + R * L;
     const int q = threadIdx.x / T, t = threadIdx.x - q * T;
@@ -415,6 +420,7 @@ __global__ void __launch_bounds__(512, RowBlocks<PRE>::value) k_row_adj(AdjArgs 
     // are loaded before waiting on the preceding column kernel, which writes D
     // (after the FFT with PRE = false, as in k_row_adv).
     float plj[8], pls[8], pv1[8], pv2[8], pb1[8], pb2[8], pg1[8], pg2[8];
+    float psrc[8], pt1[8], pt2[8], ph1[8], ph2[8];
     auto load_ops = [&](int k) {
         const size_t idx = rowbase + t + k * T;
         plj[k] = a.lj[idx];
@@ -427,8 +433,17 @@ __global__ void __launch_bounds__(512, RowBlocks<PRE>::value) k_row_adj(AdjArgs 
             pg1[k] = a.gm[idx];
             pg2[k] = a.gm[N + idx];
         }
+        if (FULL) {
+            psrc[k] = a.lsrc[idx];
+            pt1[k] = a.vt[idx];
+            pt2[k] = a.vt[N + idx];
+            if (a.b) {
+                ph1[k] = a.gmt[idx];
+                ph2[k] = a.gmt[N + idx];
+            }
+        }
     };
-    if (PRE) {
+    if (PRE && !FULL) {
 #pragma unroll
         for (int k = 0; k < 8; ++k) load_ops(k);
     }
@@ -452,13 +467,13 @@ __global__ void __launch_bounds__(512, RowBlocks<PRE>::value) k_row_adj(AdjArgs 
     }
     __syncthreads();
 #pragma unroll
-    for (int k0 = 0; k0 < 8; k0 += ADJ_LOAD_BATCH) {
-        if (!PRE) {
+    for (int k0 = 0; k0 < 8; k0 += BATCH) {
+        if (!PRE || FULL) {
 #pragma unroll
-            for (int k = k0; k < k0 + ADJ_LOAD_BATCH; ++k) load_ops(k);  // batched, as in k_row_adv
+            for (int k = k0; k < k0 + BATCH; ++k) load_ops(k);  // batched, as in k_row_adv
         }
 #pragma unroll
-        for (int k = k0; k < k0 + ADJ_LOAD_BATCH; ++k) {
+        for (int k = k0; k < k0 + BATCH; ++k) {
             const int j = t + k * T;
             const size_t idx = rowbase + j;
             const float dv = O[q * L + j];
@@ -466,22 +481,32 @@ __global__ void __launch_bounds__(512, RowBlocks<PRE>::value) k_row_adj(AdjArgs 
             a.l_out[idx] = out;
             if (a.b) {
                 const float wl = a.w * out;
-                a.b[idx] = fmaf(wl, pg1[k], pb1[k]);
-                a.b[N + idx] = fmaf(wl, pg2[k], pb2[k]);
+                float b1 = fmaf(wl, pg1[k], pb1[k]), b2 = fmaf(wl, pg2[k], pb2[k]);
+                if (FULL) {
+                    const float ws = a.w * psrc[k];
+                    b1 = fmaf(ws, ph1[k], b1);
+                    b2 = fmaf(ws, ph2[k], b2);
+                }
+                a.b[idx] = b1;
+                a.b[N + idx] = b2;
             }
-            x[k] = make_float2(out * pv1[k], out * pv2[k]);
+            x[k] = FULL ? make_float2(fmaf(out, pv1[k], psrc[k] * pt1[k]), fmaf(out, pv2[k], psrc[k] * pt2[k]))
+                        : make_float2(out * pv1[k], out * pv2[k]);
         }
     }
     if (!a.F1) return;
     flux_fft_store<LOGL>(x, q, t, R, row0, A, X, a.F1, a.F2, tw);
 }
 
-// lam = ca*a + cb*c; b = w lam gm; flux spectra; partial 0.5*sum(lam^2)
+// lam = ca*a + cb*c; b = w lam gm; flux spectra; partial 0.5*sum(lam^2).  With lsrc (full
+// Newton): b += w lsrc gmt and the flux is lam v + lsrc v~.
 template <int LOGL>
 __global__ void __launch_bounds__(512) k_adj_init(const float* __restrict__ a, float ca, const float* __restrict__ c,
                                                   float cb, const float* __restrict__ v, float* lam, float* b,
                                                   const float* __restrict__ gm, float w, float2* F1, float2* F2,
-                                                  double* part, int N, int R, const float2* __restrict__ tw) {
+                                                  double* part, int N, int R, const float2* __restrict__ tw,
+                                                  const float* __restrict__ lsrc, const float* __restrict__ vt,
+                                                  const float* __restrict__ gmt) {
     pdl_entry();
     extern __shared__ __align__(16) float2 sm[];
     constexpr int L = 1 << LOGL, T = L >> 3;
@@ -499,9 +524,16 @@ __global__ void __launch_bounds__(512) k_adj_init(const float* __restrict__ a, f
         if (a) l = fmaf(ca, a[idx], l);
         lam[idx] = l;
         acc += 0.5 * (double)l * (double)l;
-        b[idx] = w * l * gm[idx];
-        b[N + idx] = w * l * gm[N + idx];
-        x[k] = make_float2(l * v[idx], l * v[N + idx]);
+        if (lsrc) {
+            const float ls = lsrc[idx];
+            b[idx] = fmaf(w * ls, gmt[idx], w * l * gm[idx]);
+            b[N + idx] = fmaf(w * ls, gmt[N + idx], w * l * gm[N + idx]);
+            x[k] = make_float2(fmaf(l, v[idx], ls * vt[idx]), fmaf(l, v[N + idx], ls * vt[N + idx]));
+        } else {
+            b[idx] = w * l * gm[idx];
+            b[N + idx] = w * l * gm[N + idx];
+            x[k] = make_float2(l * v[idx], l * v[N + idx]);
+        }
     }
     if (part) {
         const double s = block_reduce<0>(acc);
@@ -528,7 +560,10 @@ struct ColArgs {
     int n2;
 };
 
-__device__ __forceinline__ float reg_sym(int regnorm, float kk) { return regnorm == 1 ? kk : kk * kk; }
+// |k|^2 (H1), |k|^4 (H2) or |k|^6 (H3): the regularization symbol A^(k)
+__device__ __forceinline__ float reg_sym(int regnorm, float kk) {
+    return regnorm == 1 ? kk : (regnorm == 2 ? kk * kk : kk * kk * kk);
+}
 
 __device__ __forceinline__ void proj_sym(const SpecParams& P, int pmode, float k1o, float k2o, float kk, float& K11,
                                          float& K12, float& K22) {
@@ -908,11 +943,14 @@ void launch_row_adv(reg_ctx* ctx, const AdvArgs& a) {
 
 void launch_row_adj(reg_ctx* ctx, const AdjArgs& a) {
     const RowCfg g = row_cfg(ctx);
-    // D 1, lam_j 1, lam* 1 (stage 2), v 2, l_out 1, body force b read+write 4 and gm 2, flux spectra 2
-    double fl = 1 + 1 + 2 + 1 + (a.stage == 2 ? 1 : 0) + (a.b ? 6 : 0) + (a.F1 ? 2 : 0);
+    // D 1, lam_j 1, lam* 1 (stage 2), v 2, l_out 1, body force b read+write 4 and gm 2, flux spectra 2;
+    // full Newton: lam_src 1, v~ 2, grad m~ 2 (stage 2)
+    double fl = 1 + 1 + 2 + 1 + (a.stage == 2 ? 1 : 0) + (a.b ? 6 : 0) + (a.F1 ? 2 : 0) +
+                (a.lsrc ? 3 + (a.b ? 2 : 0) : 0);
     ktimer_begin(ctx, KC_ROWSTAGE, 4.0 * fl * ctx->N);
     DISPATCH_LOG(ctx->log2, {
-        auto kern = (g.pre && LG <= 9) ? k_row_adj<LG, (LG <= 9)> : k_row_adj<LG, false>;
+        auto kern = a.lsrc ? k_row_adj<LG, false, true>
+                           : ((g.pre && LG <= 9) ? k_row_adj<LG, (LG <= 9), false> : k_row_adj<LG, false, false>);
         set_smem(kern, g.smem);
         launch_k(ctx, kern, g.grid, g.threads, g.smem, a, ctx->N, g.R, ctx->tw);
     });
@@ -920,15 +958,16 @@ void launch_row_adj(reg_ctx* ctx, const AdjArgs& a) {
 }
 
 void launch_adj_init(reg_ctx* ctx, const float* a, float ca, const float* c, float cb, const float* v, float* lam,
-                     float* b, const float* gm, float w, float2* F1, float2* F2, double* part) {
+                     float* b, const float* gm, float w, float2* F1, float2* F2, double* part, const float* lsrc,
+                     const float* vt, const float* gmt) {
     const RowCfg g = row_cfg(ctx);
-    // a 1 (optional), c 1, v 2, lam 1, b 2 + gm 2, flux spectra 2
-    ktimer_begin(ctx, KC_ROW, 4.0 * ((a ? 1 : 0) + 1 + 2 + 1 + 4 + 2) * ctx->N);
+    // a 1 (optional), c 1, v 2, lam 1, b 2 + gm 2, flux spectra 2; full Newton: lsrc 1, v~ 2, grad m~ 2
+    ktimer_begin(ctx, KC_ROW, 4.0 * ((a ? 1 : 0) + 1 + 2 + 1 + 4 + 2 + (lsrc ? 5 : 0)) * ctx->N);
     DISPATCH_LOG(ctx->log2, {
         auto kern = k_adj_init<LG>;
         set_smem(kern, g.smem);
         launch_k(ctx, kern, g.grid, g.threads, g.smem, a, ca, c, cb, v, lam, b, gm, w, F1, F2, part, ctx->N, g.R,
-                                                           ctx->tw);
+                 ctx->tw, lsrc, vt, gmt);
     });
     ktimer_end(ctx);
 }

@@ -46,7 +46,7 @@ def test_invalid_arguments_rejected_without_gpu(lib):
         (reg_grid(8, 64), 4, 1, 1e-2, math.inf, 0.0),     # below 16
         (reg_grid(2048, 64), 4, 1, 1e-2, math.inf, 0.0),  # above 1024
         (reg_grid(64, 64), 0, 1, 1e-2, math.inf, 0.0),    # nt < 1
-        (reg_grid(64, 64), 4, 3, 1e-2, math.inf, 0.0),    # bad norm
+        (reg_grid(64, 64), 4, 4, 1e-2, math.inf, 0.0),    # bad norm (H1, H2, H3 only)
         (reg_grid(64, 64), 4, 1, 0.0, math.inf, 0.0),     # beta <= 0
         (reg_grid(64, 64), 4, 1, 1e-2, -1.0, 0.0),        # gamma < 0
         (reg_grid(64, 64), 4, 1, 1e-2, math.inf, 1.0),    # shear out of range

@@ -32,14 +32,17 @@ def op_cond(beta_v, regnorm, x, y, b=None):
     return terms / ny
 
 
-def op_tol(beta_v, regnorm, n1, n2, x, y, b=None):
+def op_tol(beta_v, regnorm, n1, n2, x, y, b=None, eta_max=1.0):
     """Tolerance for y = beta_v A x + K b: 1e-5 times max(1, op_cond), plus the FP32
-    rounding bound of the regularization term, u * beta_v * max A^ * ||x|| / ||y||, which
-    matters where the H2 symbol |k|^4 amplifies the rounding of the FP32 operand (rounding
-    the inputs alone moves the FP64 result that much)."""
+    rounding bound of the regularization term, u * beta_v * max A^ * eta_max * ||x|| / ||y||,
+    which matters where the H2 / H3 symbol |k|^4 / |k|^6 amplifies the rounding of the FP32
+    operand (rounding the inputs alone moves the FP64 result that much).  eta_max: the largest
+    viscosity of the shear model's second variation B = -div(2 eta (...)), which multiplies
+    the same rounding (1 for the quadratic seminorms)."""
     Amax = S.reg_symbol(n1, n2, regnorm).max()
     ny = np.linalg.norm(y)
-    return OP_TOL * max(1.0, op_cond(beta_v, regnorm, x, y, b)) + U32 * beta_v * Amax * np.linalg.norm(x) / ny
+    return (OP_TOL * max(1.0, op_cond(beta_v, regnorm, x, y, b)) +
+            U32 * beta_v * Amax * eta_max * np.linalg.norm(x) / ny)
 
 
 @pytest.fixture(scope="module", autouse=True)
