@@ -340,6 +340,32 @@ int reg_fp32_peak(double* tflops, double* ms_per_launch);
  * mean of D = ||F1 - I||_F (Appendix F). */
 int reg_detgrad(reg_ctx* ctx, const float* v, float* detF, double* stats);
 
+/* ---- deformation map and label overlap (App. D, App. F) ---- */
+
+/* Displacement field u_1 = u(t = 1) of Eq. (e:displacement): d_t u + (grad u) v
+ * = v, u(0) = 0, over the context's nt Heun steps (per component a transport
+ * with the source v_a).  The deformation map is y = x - u_1 (Eulerian: where
+ * the points originate from; App. D).  v: device, 2*n1*n2; u_out: device,
+ * 2*n1*n2 (component planes).  Uses the context's work fields only;
+ * asynchronous. */
+int reg_displacement(reg_ctx* ctx, const float* v, float* u_out);
+
+/* Label-map overlap after registration (the measures table of App. F and the
+ * label evaluation of Sec. 5): the template label map (device, n1*n2 floats,
+ * 1 inside the label, 0 outside) is smoothed with a Gaussian of standard
+ * deviation 3 h_x, transported with v by the state equation
+ * (Eq. (e:state-eq-elim), nt Heun steps) and thresholded at 0.5 (L_T); the
+ * reference label map (device, n1*n2 floats, inside where > 0.5) is L_R.
+ * measures (host, 4 doubles): Jaccard #(L_R and L_T) / #(L_R or L_T), Dice
+ * 2 #(L_R and L_T) / (#L_R + #L_T), false positive error #(L_T minus L_R) /
+ * #L_T, false negative error #(L_R minus L_T) / #L_R.  transported (device,
+ * n1*n2 floats, nullable) receives the transported smoothed template labels
+ * before the threshold.  Overwrites the state history, so the linearization
+ * point is invalidated (REG_ERR_STATE for a matvec until the next
+ * reg_gradient).  Synchronous. */
+int reg_label_overlap(reg_ctx* ctx, const float* v, const float* labels_T, const float* labels_R,
+                      float* transported, double* measures);
+
 /* ---- learned warm start (the paper has no learned component) ---- */
 
 /* An 8-layer 3x3 convolutional network with circular padding (channel

@@ -108,6 +108,24 @@ def grad_history(m):
     return np.stack([grad(m[j]) for j in range(m.shape[0])])
 
 
+def displacement_solve(v, nt):
+    """Displacement field, Eq. (e:displacement): d_t u + (grad u) v = v, u(0) = 0, i.e. per
+    component c the transport d_t u_c + grad u_c . v = v_c with a source constant in time
+    (Heun, as for the state equation).  Returns u_1 = u(t = 1) as (2, n1, n2); the
+    deformation map (Eulerian, where points originate from) is y = x - u_1."""
+    h = 1.0 / nt
+    u = np.zeros_like(np.asarray(v, dtype=np.float64))
+    for c in range(2):
+        uc = np.zeros(v.shape[1:])
+        for _ in range(nt):
+            k1 = -advect(uc, v) + v[c]
+            us = uc + h * k1
+            k2 = -advect(us, v) + v[c]
+            uc = uc + 0.5 * h * (k1 + k2)
+        u[c] = uc
+    return u
+
+
 def defgrad_solve(v, nt):
     """Deformation gradient, Eq. (e:def-grad): d_t F + (v . grad) F = (grad v) F,
     F(0) = I, with (grad v)_{ac} = d_c v_a.  Returns F1 = F(t=1) as (2, 2, n1, n2)."""

@@ -86,6 +86,8 @@ _SIGS = {
     "reg_set_pdl": ([_P, _I], _I),
     "reg_set_transport": ([_P, _I], _I),
     "reg_set_hessian": ([_P, _I], _I),
+    "reg_displacement": ([_P, _P, _P], _I),
+    "reg_label_overlap": ([_P, _P, _P, _P, _P, ctypes.POINTER(_D)], _I),
     "reg_transport_config": ([_P, ctypes.POINTER(_I), ctypes.POINTER(_I), ctypes.POINTER(_I)], _I),
     "reg_fp32_peak": ([ctypes.POINTER(_D), ctypes.POINTER(_D)], _I),
     "reg_net_create": ([_I, _I, _I, ctypes.POINTER(_P)], _I),
@@ -476,3 +478,17 @@ class Context:
     def set_hessian(self, full):
         """Full Newton Hessian (True) or Gauss-Newton (False, default) for matvecs and solves."""
         _check(lib().reg_set_hessian(self.h, 1 if full else 0))
+
+    def displacement(self, v, u_out):
+        """Displacement u_1 of the flow of v (the deformation map is y = x - u_1)."""
+        _check(lib().reg_displacement(self.h, _ptr(v, 2 * self.N, "v"), _ptr(u_out, 2 * self.N, "u_out")))
+
+    def label_overlap(self, v, labels_T, labels_R, transported=None):
+        """(Jaccard, Dice, false positive error, false negative error) of the template labels
+        transported with v against the reference labels; transported (optional) receives the
+        smoothed, transported template labels before the threshold."""
+        out = (ctypes.c_double * 4)()
+        _check(lib().reg_label_overlap(self.h, _ptr(v, 2 * self.N, "v"), _ptr(labels_T, self.N, "labels_T"),
+                                       _ptr(labels_R, self.N, "labels_R"), _ptr(transported, self.N, "transported"),
+                                       out))
+        return tuple(out)

@@ -496,15 +496,17 @@ static float* gmh(reg_ctx* c, int j) { return c->gm_hist + (size_t)j * 2 * c->N;
 // State equation (Eq. (e:state-eq-elim)), Heun in time: fills m_hist[0..nt], gm_hist[0..nt].
 // The column pass transforms only d1 (OP_GRAD1); d2 is diagonal in the row
 // spectra and is formed by the row kernel from the stage's own spectrum S[0].
-static void state_solve(reg_ctx* c, const float* v, int nt) {
+// init (nullable): the field transported instead of the template m_T.
+static void state_solve(reg_ctx* c, const float* v, int nt, const float* init = nullptr) {
     const float h = 1.0f / (float)nt;
+    const float* m0 = init ? init : c->mT;
     if (c->use_tc && !c->full_newton) {
         TcArgs a = {};
-        a.nt = nt; a.h = h; a.v = v; a.mT = c->mT; a.m_hist = c->m_hist; a.gm_hist = c->gm_hist; a.us = c->w0;
+        a.nt = nt; a.h = h; a.v = v; a.mT = m0; a.m_hist = c->m_hist; a.gm_hist = c->gm_hist; a.us = c->w0;
         launch_transport_cluster(c, TC_STATE, a);
         return;
     }
-    cudaMemcpyAsync(mh(c, 0), c->mT, sizeof(float) * c->N, cudaMemcpyDeviceToDevice, c->stream);
+    cudaMemcpyAsync(mh(c, 0), m0, sizeof(float) * c->N, cudaMemcpyDeviceToDevice, c->stream);
     launch_r2c_scalar(c, mh(c, 0), c->S[0]);
     const float2* in[1] = {c->S[0]};
     float2* G[1] = {c->S[1]};
@@ -598,7 +600,9 @@ static void inc_adjoint_full(reg_ctx* c, const float* v, const float* vt, int nt
 // Incremental state (Eq. (e:inc-state-eq-elim)); leaves m~(1) in c->w3.
 // m~(0) = 0 is passed as u_j = nullptr to both stages of the first step.  gmt (nullable):
 // store grad m~_j at gmt + j 2N for j = 0..nt (the full Newton matvec reads it).
-static void inc_state_solve(reg_ctx* c, const float* v, const float* vt, int nt, float* gmt = nullptr) {
+// gm_fixed (nullable): a source gradient used at every time instead of the grad m history.
+static void inc_state_solve(reg_ctx* c, const float* v, const float* vt, int nt, float* gmt = nullptr,
+                            const float* gm_fixed = nullptr) {
     const float h = 1.0f / (float)nt;
     float* mj = c->w3;
     float* ms = c->w0;
@@ -611,7 +615,7 @@ static void inc_state_solve(reg_ctx* c, const float* v, const float* vt, int nt,
             launch_col(c, OP_GRAD1, in, G, P, nullptr);
             a.G1 = c->S[1]; a.Sd2 = c->S[0];
         }
-        a.uj = (j > 0) ? mj : nullptr; a.us = nullptr; a.v = v; a.gm = gmh(c, j); a.vt = vt;
+        a.uj = (j > 0) ? mj : nullptr; a.us = nullptr; a.v = v; a.gm = gm_fixed ? gm_fixed : gmh(c, j); a.vt = vt;
         a.u_out = ms; a.grad_out = gmt ? gmt + (size_t)j * 2 * c->N : nullptr; a.S_out = c->S[0]; a.h = h;
         a.stage = 1;
         // the first launch of the solve: v~ may come from the launch just before (Q^-1 s in
@@ -621,7 +625,7 @@ static void inc_state_solve(reg_ctx* c, const float* v, const float* vt, int nt,
         a.late = 0;
         launch_col(c, OP_GRAD1, in, G, P, nullptr);
         a.G1 = c->S[1]; a.Sd2 = c->S[0];
-        a.us = ms; a.gm = gmh(c, j + 1); a.u_out = mj; a.stage = 2; a.grad_out = nullptr;
+        a.us = ms; a.gm = gm_fixed ? gm_fixed : gmh(c, j + 1); a.u_out = mj; a.stage = 2; a.grad_out = nullptr;
         a.S_out = (j + 1 < nt) ? c->S[0] : nullptr;
         launch_row_adv(c, a);
     }
@@ -1140,6 +1144,62 @@ extern "C" int reg_register_host(reg_ctx* c, const float* mT_host, const float* 
     CK(cudaMemcpyAsync(v_host, v, sizeof(float) * 2 * N, cudaMemcpyDeviceToHost, c->stream));
     CK(cudaStreamSynchronize(c->stream));
     return st;
+}
+
+// ---------------------------------------------------------------------------
+// displacement field (Eq. (e:displacement)) and label overlap (Appendix F)
+// ---------------------------------------------------------------------------
+extern "C" int reg_displacement(reg_ctx* c, const float* v, float* u_out) {
+    CTX_CHECK(c);
+    RET(check_ptr(v, "v")); RET(check_ptr(u_out, "u_out"));
+    const int nt = c->nt;
+    const size_t N = c->N;
+    // Component a solves d_t u_a + grad u_a . v = v_a from u_a = 0: the incremental-state
+    // stage with source -(e . grad) where grad := v at every time and e = -(unit vector a),
+    // so that the source is exactly v_a in FP32.
+    float* e = c->vtmp;
+    for (int comp = 0; comp < 2; ++comp) {
+        launch_fill(c, 2 * (long long)N, e, 0.f);
+        launch_fill(c, N, e + comp * N, -1.f);
+        inc_state_solve(c, v, e, nt, nullptr, v);
+        CK(cudaMemcpyAsync(u_out + comp * N, c->w3, sizeof(float) * N, cudaMemcpyDeviceToDevice, c->stream));
+    }
+    CKL();
+    return REG_OK;
+}
+
+extern "C" int reg_label_overlap(reg_ctx* c, const float* v, const float* labels_T, const float* labels_R,
+                                 float* transported, double* measures) {
+    CTX_CHECK(c);
+    RET(check_ptr(v, "v")); RET(check_ptr(labels_T, "labels_T")); RET(check_ptr(labels_R, "labels_R"));
+    if (transported) RET(check_ptr(transported, "transported"));
+    if (!measures) return reg_fail(REG_ERR_ARG, "measures is NULL");
+    const int nt = c->nt;
+    RET(ensure_nt(c, nt));
+    // Gaussian filter, standard deviation 3 h_x (h_x = 2 pi / n1): symbol exp(-sigma^2 |k|^2 / 2)
+    const double hx = 2.0 * M_PI / c->n1;
+    const float a = (float)(0.5 * 9.0 * hx * hx);
+    float* sm = c->vtmp;
+    launch_r2c_scalar(c, labels_T, c->S[0]);
+    const float2* in[1] = {c->S[0]};
+    float2* o[1] = {c->S[1]};
+    launch_col(c, OP_SMOOTH, in, o, spec_params(c, a), nullptr);
+    launch_c2r_scalar(c, c->S[1], sm);
+    state_solve(c, v, nt, sm);  // overwrites the state history
+    c->have_lin = false;
+    if (transported)
+        CK(cudaMemcpyAsync(transported, mh(c, nt), sizeof(float) * c->N, cudaMemcpyDeviceToDevice, c->stream));
+    const int np = launch_overlap_counts(c, mh(c, nt), labels_R, 0.5f, c->d_part);
+    for (int q = 0; q < 3; ++q) launch_finalize(c, c->d_part + q * np, np, c->d_scal + SL_DOT0 + q, 1.0, 0, 0);
+    CKL();
+    RET(read_scalars(c));
+    const double nT = c->h_scal[SL_DOT0], nR = c->h_scal[SL_DOT1], nB = c->h_scal[SL_DOT2];
+    const double nU = nT + nR - nB;
+    measures[0] = nU > 0 ? nB / nU : 1.0;                    // Jaccard
+    measures[1] = nT + nR > 0 ? 2.0 * nB / (nT + nR) : 1.0;  // Dice
+    measures[2] = nT > 0 ? (nT - nB) / nT : 0.0;             // false positive error
+    measures[3] = nR > 0 ? (nR - nB) / nR : 0.0;             // false negative error
+    return REG_OK;
 }
 
 // ---------------------------------------------------------------------------

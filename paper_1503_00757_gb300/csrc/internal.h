@@ -26,7 +26,8 @@ enum SpecOp {
     OP_QMUL = 12,        // 2 in -> 2 out: Q x
     OP_ASSEMBLE_Y = 13,  // 4 in -> 2 out: Pi0 x01 + Q^-1 K^ x23 (Pi0 drops k = 0): gradient / Hessian in y
     OP_QNORM = 14,       // 2 in -> 0 out: FP64 sum of |Q x|^2 (the v-norm of a y-space gradient or residual)
-    OP_ENERGY_Y = 15     // 2 in -> 0 out: FP64 regularization energy of v = Q^-1 x from x
+    OP_ENERGY_Y = 15,    // 2 in -> 0 out: FP64 regularization energy of v = Q^-1 x from x
+    OP_SMOOTH = 16       // 1 in -> 1 out: exp(-coefA |k|^2) x (Gaussian filter of a scalar field)
 };
 
 // Projection modes (Eq. (e:project-body-force)):
@@ -210,6 +211,10 @@ int launch_pcg_update(reg_ctx* ctx, long long n, float* vt, const float* s, floa
 // s = z + (d_scal[SL_RZNEW] / d_scal[SL_RZ]) s
 void launch_pcg_dir(reg_ctx* ctx, long long n, const float* z, float* s);
 void launch_fill(reg_ctx* ctx, long long n, float* y, float val);
+
+// label overlap: part[0 * nb + b], part[1 * nb + b], part[2 * nb + b] <- block b's counts of
+// (f > thr), (L > 0.5) and both; returns nb
+int launch_overlap_counts(reg_ctx* ctx, const float* f, const float* L, float thr, double* part);
 
 // deformation gradient
 void launch_defgrad_stage(reg_ctx* ctx, int stage, const float* F, const float* Fs, const float* gF,

@@ -627,6 +627,8 @@ __device__ __forceinline__ void spec_apply(const SpecParams& P, float k1o, float
             e += P.ebw * (1.0 + kk) * (dr * dr + di * di) / ((double)P.beta_v * a);
         }
         eacc += ew * e;
+    } else if (OP == OP_SMOOTH) {
+        y[0] = cscale(x[0], expf(-P.coefA * kk) * s);
     } else if (OP == OP_SMOOTH_PROJ) {
         float K11, K12, K22;
         proj_sym(P, PROJ_LERAY, k1o, k2o, kk, K11, K12, K22);
@@ -1015,6 +1017,7 @@ void launch_col(reg_ctx* ctx, int op, const float2* const* in, float2* const* ou
         case OP_GRAD1: launch_col_t<1, 1, OP_GRAD1>(ctx, in, out, P, part); break;
         case OP_DIV1: launch_col_t<1, 1, OP_DIV1>(ctx, in, out, P, part); break;
         case OP_SMOOTH_PROJ: launch_col_t<2, 2, OP_SMOOTH_PROJ>(ctx, in, out, P, part); break;
+        case OP_SMOOTH: launch_col_t<1, 1, OP_SMOOTH>(ctx, in, out, P, part); break;
         case OP_QINV: launch_col_t<2, 2, OP_QINV>(ctx, in, out, P, part); break;
         case OP_QMUL: launch_col_t<2, 2, OP_QMUL>(ctx, in, out, P, part); break;
         case OP_ASSEMBLE_Y: launch_col_t<4, 2, OP_ASSEMBLE_Y>(ctx, in, out, P, part); break;
@@ -1146,6 +1149,34 @@ void launch_fill(reg_ctx* ctx, long long n, float* y, float val) {
     ktimer_begin(ctx, KC_POINT, 4.0 * n);
     launch_k(ctx, k_fill, NBLK_RED, NTHREADS, 0, n, y, val);
     ktimer_end(ctx);
+}
+
+// counts for the label overlap measures (App. F): nodes with f > thr (transported template
+// labels), with L > 0.5 (reference labels) and with both
+__global__ void k_overlap_counts(int N, const float* __restrict__ f, const float* __restrict__ L, float thr,
+                                 double* part) {
+    pdl_entry();
+    double nT = 0.0, nR = 0.0, nB = 0.0;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < N; i += gridDim.x * blockDim.x) {
+        const bool t = f[i] > thr, r = L[i] > 0.5f;
+        nT += t ? 1.0 : 0.0;
+        nR += r ? 1.0 : 0.0;
+        nB += (t && r) ? 1.0 : 0.0;
+    }
+    double c;
+    c = block_reduce<0>(nT);
+    if (threadIdx.x == 0) part[0 * gridDim.x + blockIdx.x] = c;
+    c = block_reduce<0>(nR);
+    if (threadIdx.x == 0) part[1 * gridDim.x + blockIdx.x] = c;
+    c = block_reduce<0>(nB);
+    if (threadIdx.x == 0) part[2 * gridDim.x + blockIdx.x] = c;
+}
+
+int launch_overlap_counts(reg_ctx* ctx, const float* f, const float* L, float thr, double* part) {
+    ktimer_begin(ctx, KC_POINT, 8.0 * ctx->N);
+    launch_k(ctx, k_overlap_counts, NBLK_RED, NTHREADS, 0, ctx->N, f, L, thr, part);
+    ktimer_end(ctx);
+    return NBLK_RED;
 }
 
 // deformation gradient stage (Eq. (e:def-grad)); F planes (F11, F12, F21, F22),

@@ -16,6 +16,8 @@ Workloads (stand-ins for the paper's image data, which are not available):
     sigma = 0.01, then Gaussian pre-smoothing with width 2 h (Sec. 4 of the
     paper pre-smooths its data); velocity with modes |k| <= 8 and a
     compressible (gradient) part.
+  * ``ellipse_labels``: binary label maps of one of ellipses_pair's ellipses for the
+    template and the reference (the label-overlap measures);
   * ``ellipses_pair``: "brain-like" nested smoothed ellipses with 5 labels and
     random contrasts in [0.1, 1]; divergence-free velocity with |k| <= 16.
 All images are rescaled to [0, 1] (Sec. 4).
@@ -161,6 +163,25 @@ def ellipses_pair(n, seed, vmax, kmax=16, nlabels=5):
     mR = _ellipses(X1 - v[0], X2 - v[1], params, width)
     lo, hi = mT.min(), mT.max()
     return (mT - lo) / (hi - lo), (mR - lo) / (hi - lo), v
+
+
+def ellipse_labels(n, seed, vmax, kmax=16, nlabels=5, label=1):
+    """Binary label maps (1 inside, 0 outside) of the pair ellipses_pair(n, seed, vmax, kmax,
+    nlabels) draws: the region inside ellipse `label` (0 = the outermost), for the template
+    and, at the displaced coordinates x - v*(x), for the reference; (L_T, L_R)."""
+    rng = np.random.default_rng(seed)
+    params = _ellipse_params(rng, nlabels)
+    v = velocity(n, n, kmax, vmax, rng)
+    X1, X2 = coords(n, n)
+
+    def inside(Y1, Y2):
+        c1, c2, a, b, th, _ = params[label]
+        d1, d2 = _wrap(Y1 - c1), _wrap(Y2 - c2)
+        p = np.cos(th) * d1 + np.sin(th) * d2
+        q = -np.sin(th) * d1 + np.cos(th) * d2
+        return ((p / a) ** 2 + (q / b) ** 2 < 1.0).astype(np.float64)
+
+    return inside(X1, X2), inside(X1 - v[0], X2 - v[1])
 
 
 def gaussian_smooth(f, sigma):
