@@ -351,13 +351,13 @@ def _oracle_register(spec):
     returns (seconds, Newton iterations, matvecs, status)."""
     from oracle.registration import Registration
     from paper_1503_00757_gb300 import synth
-    kind, n, nt, seed, regnorm, beta, gamma, vmax = spec
+    kind, n, nt, seed, regnorm, beta, gamma, vmax, policy = spec
     if kind == "blobs":
         mT, mR, _ = synth.blobs_pair(n, seed)
     else:
         mT, mR, _ = synth.ellipses_pair(n, seed, vmax=vmax)
     t0 = time.perf_counter()
-    _, st = Registration(mT, mR, nt, regnorm=regnorm, beta_v=beta, beta_w=gamma).solve(tol=1e-2)
+    _, st = Registration(mT, mR, nt, regnorm=regnorm, beta_v=beta, beta_w=gamma).solve(tol=1e-2, nt_policy=policy)
     return time.perf_counter() - t0, st["n_newton"], st["n_mv"], st["status"]
 
 
@@ -380,8 +380,10 @@ def _oracle_pool(workers, init_seed=None):
 
 
 def c1_specs(count):
-    """C1 plain FP64 problems: 64^2 Gaussian blobs, nt = 4, H1, div v = 0, beta_v = 1e-2 (seeds 1000+)."""
-    return [("blobs", 64, 4, 1000 + i, 1, 1e-2, math.inf, None) for i in range(count)]
+    """C1 plain FP64 problems: 64^2 Gaussian blobs, H1, div v = 0, beta_v = 1e-2 (seeds 1000+), nt
+    adapted to CFL 0.25 from nt = 4 per outer iteration (at the literal nt = 4, CFL 1.27, some
+    seeds do not converge within 50 Newton iterations)."""
+    return [("blobs", 64, 4, 1000 + i, 1, 1e-2, math.inf, None, "cfl") for i in range(count)]
 
 
 def c4_subset_specs(count):
@@ -389,7 +391,8 @@ def c4_subset_specs(count):
     out = []
     for s in c4_specs():
         if s["n"] == 128 and len(out) < count:
-            out.append(("ellipses", 128, C4_NT, s["seed"], s["regnorm"], s["beta"], s["gamma"], C4_VMAX[128]))
+            out.append(("ellipses", 128, C4_NT, s["seed"], s["regnorm"], s["beta"], s["gamma"], C4_VMAX[128],
+                        "fixed"))
     return out
 
 
@@ -424,8 +427,8 @@ def cpu_oracle_baseline(pde_per_reg):
     return {"value": value, "unit": "registrations/s", "cores": nproc, "kind": "oracle",
             "sample": (f"FP64 oracle on {nproc} host cores: {nproc} Gauss-Newton matvecs at 512^2 nt=32 (one per "
                        f"core) timed, registrations/s = matvecs/s / {pde_per_reg / 2:g} matvec equivalents per "
-                       f"registration of this workload; also timed: full 64^2 (C1) registrations on 1 and "
-                       f"{nproc} cores, 3 matvecs on 1 core, 16 full 128^2 mixed-batch registrations"),
+                       f"registration of this workload; also timed: full 64^2 (C1, CFL nt) registrations on 1 "
+                       f"and {nproc} cores, 3 matvecs on 1 core, 16 full 128^2 mixed-batch registrations"),
             "measured": res}
 
 
