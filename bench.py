@@ -216,7 +216,7 @@ def run_batched_mixed(dev, stream, opts, nworkers=16):
     gen_s = time.perf_counter() - t0
     tiles = {}
     for n in C4_SIZES:
-        R, C, P, D, ms = autotune(n, n, nt=8, concurrency=8, force=True)
+        R, C, P, D, ms = autotune(n, n, nt=C4_NT, concurrency=8, force=True)
         tiles[str(n)] = {"rows_per_cta": R, "cols_per_cta": C, "prefetch": P, "pdl": D}
     pairs = []
     for s, (a, b) in zip(specs, imgs):
@@ -532,7 +532,7 @@ def main():
 
     # FFT tiles of the workload's grid, picked once by the autotuner before any context exists
     # (with --profile-grid: the tiles of that grid instead)
-    tR, tC, tP, tD, _ = autotune(args.profile_grid or N_GRID, args.profile_grid or N_GRID, nt=8,
+    tR, tC, tP, tD, _ = autotune(args.profile_grid or N_GRID, args.profile_grid or N_GRID, nt=NT,
                                  concurrency=1 if args.profile_grid else PAIRS)
 
     # the step's batch: PAIRS independent registrations of this rank (seeds differ per rank)
@@ -544,6 +544,7 @@ def main():
     mT, mR = pairs[0]["mT"], pairs[0]["mR"]
     stream = torch.cuda.Stream(device=dev)
     ctx = Context(N_GRID, N_GRID, NT, regnorm=1, beta=BETA, gamma=math.inf, shear=0.0, stream=stream)
+    transport_tuned = ctx.transport_config()  # (cluster kernel chosen, CTAs per cluster, clusters that fit)
     v = torch.zeros(2, N_GRID, N_GRID, device=dev)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)  # > 129 MB L2
     opts = default_opts(tol=1e-2)
@@ -628,7 +629,7 @@ def main():
 
         # single-stream measurements (one registration alone, matvecs/s) with the tiles and launch mode
         # tuned for one solve at a time
-        sR, sC, sP, sD, _ = autotune(N_GRID, N_GRID, nt=8, concurrency=1, force=True)
+        sR, sC, sP, sD, _ = autotune(N_GRID, N_GRID, nt=NT, concurrency=1, force=True)
         ctx.set_tiles(sR, sC, sP)
         ctx.set_pdl(sD)
         # single-registration latency (one pair alone on one stream)
@@ -727,7 +728,7 @@ def main():
             nb = 1024
             from paper_1503_00757_gb300 import synth
             bT, bR, bv = synth.ellipses_pair(nb, SEED, vmax=0.049)
-            autotune(nb, nb, nt=8, concurrency=1)
+            autotune(nb, nb, nt=NT, concurrency=1)
             ctxb = Context(nb, nb, NT, regnorm=1, beta=BETA, gamma=math.inf, shear=0.0, stream=stream)
             ctxb.set_images(torch.from_numpy(bT.astype(np.float32)).to(dev), torch.from_numpy(bR.astype(np.float32)).to(dev))
             vb = torch.from_numpy((0.5 * bv).astype(np.float32)).to(dev).contiguous()
@@ -825,6 +826,7 @@ def main():
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": WORKLOAD, "grid": [N_GRID, N_GRID], "nt": NT, "pairs_per_step": PAIRS,
                        "tiles": {"rows_per_cta": tR, "cols_per_cta": tC, "prefetch": tP, "pdl": tD,
+                                 "transport": "cluster-resident" if transport_tuned[0] else "row/column kernel pairs",
                                  "tuned_for": f"{PAIRS} concurrent solves"},
                        "tiles_single_stream": {"rows_per_cta": sR, "cols_per_cta": sC, "prefetch": sP, "pdl": sD,
                                                "used_for": "latency_ms_single_registration, matvec_per_s"},

@@ -232,7 +232,8 @@ typedef struct {
  * and re-parameterizes per pair (reg_set_params), so the pairs' kernels run
  * concurrently.  Pairs are taken largest grid first.  Before the first pair
  * of a grid size is solved, reg_autotune picks that size's FFT tiles for
- * min(nworkers, 8) concurrent solves (once per process and device).  Every pair's result is identical to reg_solve on
+ * min(nworkers, 8) concurrent solves at the largest nt of the batch's pairs
+ * of that size (once per process and device).  Every pair's result is identical to reg_solve on
  * that pair alone with a context created after that tuning.  Synchronous.  Returns REG_OK if
  * every pair returned REG_OK, else the first failing pair's status (each
  * item's own status is in item.status); REG_ERR_ARG for invalid arguments. */
@@ -256,10 +257,8 @@ void reg_executor_destroy(reg_executor* ex);
  * choice (R rows per row-kernel CTA, C spectrum columns per column-kernel
  * CTA, P = 1 if the RK2 row kernels prefetch their operands before waiting on
  * the preceding kernel) with programmatic dependent launch on and off
- * (D, see reg_set_pdl), and, on grids where it runs, the cluster-resident
- * transport kernel (see reg_set_transport), on the current device with zero
- * images and velocity and private streams, and records the fastest in a
- * process-wide table;
+ * (D, see reg_set_pdl), on the current device with zero images and velocity
+ * and private streams, and records the fastest in a process-wide table;
  * contexts created afterwards on this device and grid use it (existing
  * contexts keep theirs).  Valid: R a multiple of 4 dividing n1,
  * 32 <= R n2 / 8 <= 512 threads; C a power of two >= 2 dividing n2 / 2,
@@ -297,8 +296,9 @@ int reg_set_tiles(reg_ctx* ctx, int rows_per_cta, int cols_per_cta, int prefetch
  *     16 <= n <= 512, on devices with thread-block clusters);
  *   cluster == 0: a row kernel and a column kernel per Heun stage, the spectra
  *     passing through global memory (every grid).
- * Default: the two-kernel path, unless reg_autotune measured the cluster path
- * faster for this device and grid before the context was created.  Results
+ * Default: the two-kernel path (faster on a GB300 at every grid size and
+ * concurrency measured: the cluster kernel keeps 16 warps per SM, too few to
+ * hide the latency of its per-stage operand loads).  Results
  * agree to FP32 rounding (the transforms are the same; the order of a few
  * additions differs).  REG_ERR_ARG if cluster != 0 and this grid or device
  * cannot run it. */

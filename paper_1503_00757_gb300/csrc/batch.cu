@@ -65,11 +65,14 @@ extern "C" int reg_executor_solve(reg_executor* ex, reg_batch_item* items, int c
     // FFT tiles of every grid size in the batch (measured once per process and device)
     {
         cudaSetDevice(ex->dev);
-        std::map<std::pair<int, int>, int> sizes;
-        for (int i = 0; i < count; ++i) sizes[std::make_pair(items[i].grid.n1, items[i].grid.n2)] = 1;
+        std::map<std::pair<int, int>, int> sizes;  // grid -> largest nt of its pairs
+        for (int i = 0; i < count; ++i) {
+            int& nt = sizes[std::make_pair(items[i].grid.n1, items[i].grid.n2)];
+            nt = std::max(nt, std::min(items[i].nt, 4096));
+        }
         for (const auto& kv : sizes) {
-            const int st = reg_autotune(reg_grid{kv.first.first, kv.first.second}, 8, std::min(nworkers, 8), 0,
-                                        nullptr, nullptr, nullptr, nullptr, nullptr);
+            const int st = reg_autotune(reg_grid{kv.first.first, kv.first.second}, std::max(kv.second, 1),
+                                        std::min(nworkers, 8), 0, nullptr, nullptr, nullptr, nullptr, nullptr);
             if (st != REG_OK) return st;
         }
     }

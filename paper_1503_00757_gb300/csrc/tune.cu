@@ -9,10 +9,11 @@
 // every valid (R, C, P) with a given number of solves running concurrently on
 // their own streams, each with and without programmatic dependent launch
 // (D): early launch hides one solve's launch latency but lets waiting CTAs
-// hold SM resources, and which wins depends on the concurrency.  Where the
-// cluster-resident transport kernel runs (square grids up to 512^2) it is one
-// more candidate (T = 1; its transports do not use the row / column tiles).
-// Results live in a process-wide table per (device, n1, n2); contexts created
+// hold SM resources, and which wins depends on the concurrency.  The
+// cluster-resident transport kernel (T = 1) is not a candidate: measured on a
+// GB300 it is slower than the row / column kernel pairs at every grid size,
+// nt and concurrency tried (reg_set_transport selects it by hand).  Results
+// live in a process-wide table per (device, n1, n2); contexts created
 // afterwards on that device and grid use them.
 #include <cmath>
 #include <map>
@@ -117,7 +118,7 @@ extern "C" int reg_autotune(reg_grid grid, int nt, int concurrency, int force, i
     int R0, C0, P0;
     default_tiles(grid.n1, grid.n2, &R0, &C0, &P0);
     if (cands.empty()) cands.emplace_back(R0, C0, P0, 1, 0);
-    if (tc_max_active_clusters(grid.n1, grid.n2) > 0) cands.emplace_back(R0, C0, P0, 1, 1);
+
 
     const size_t N = (size_t)grid.n1 * grid.n2;
     const int K = concurrency;

@@ -98,22 +98,25 @@ def test_cluster_transport_matches_oracle_and_two_kernel_path(case):
 
 def test_cluster_solve_matches_oracle_solve():
     """A full registration (Algorithm 1) on each transport path reaches the tolerance with the
-    FP64 oracle's Newton count and its velocity to 1e-3 (the end-to-end bar)."""
+    FP64 oracle's Newton count and its velocity to 1e-3 (the end-to-end bar).  The solves run
+    to ||g|| <= 1e-3 ||g(0)||: at 1e-2 the stopping test itself admits velocities about 2e-3
+    apart (measured between the two FP32 paths), so a tighter solve is what determines v to
+    the bar."""
     import torch
-    from paper_1503_00757_gb300.binding import Context
+    from paper_1503_00757_gb300.binding import Context, default_opts
     n, nt = 128, 16
     mT, mR, _ = synth.ellipses_pair(n, 3100, vmax=0.2)
-    v_ref, st_ref = Registration(mT, mR, nt, regnorm=1, beta_v=1e-3, beta_w=math.inf).solve(tol=1e-2)
+    v_ref, st_ref = Registration(mT, mR, nt, regnorm=1, beta_v=1e-3, beta_w=math.inf).solve(tol=1e-3)
     assert st_ref["status"] == 0
     for cluster in (True, False):
         ctx = Context(n, n, nt, regnorm=1, beta=1e-3, gamma=math.inf)
         ctx.set_transport(cluster)
         ctx.set_images(to_gpu(mT), to_gpu(mR))
         v = torch.zeros(2, n, n, device="cuda")
-        st = ctx.solve(v)
+        st = ctx.solve(v, default_opts(tol=1e-3))
         torch.cuda.synchronize()
         ctx.close()
         tag = "cluster" if cluster else "two-kernel"
-        assert st["status"] == 0 and st["gnorm_rel"] <= 1e-2
+        assert st["status"] == 0 and st["gnorm_rel"] <= 1e-3
         assert st["n_newton"] == st_ref["n_newton"]
         check_rel(f"solve v ({tag} path)", to_np(v), v_ref, 1e-3)
