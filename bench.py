@@ -488,6 +488,8 @@ def main():
                     help="run 4 training steps of the warm-start network (256^2, batch 8) and exit (for ncu)")
     ap.add_argument("--profile-grid", type=int, default=0,
                     help="with --profile: instead run a gradient and 3 GN matvecs on this grid (nt=32)")
+    ap.add_argument("--transport", default="auto", choices=["auto", "cluster", "two-kernel"],
+                    help="with --profile-grid: the transport path of the profiled context (auto: the tuned one)")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
@@ -570,17 +572,23 @@ def main():
         from paper_1503_00757_gb300 import synth
         bT, bR, bv = synth.ellipses_pair(nb, SEED, vmax=VMAX * N_GRID / nb)
         cb = Context(nb, nb, NT, regnorm=1, beta=BETA, gamma=math.inf, shear=0.0, stream=stream)
+        if args.transport != "auto":
+            cb.set_transport(args.transport == "cluster")
         with torch.cuda.stream(stream):
             cb.set_images(torch.from_numpy(bT.astype(np.float32)).to(dev), torch.from_numpy(bR.astype(np.float32)).to(dev))
             vb = torch.from_numpy((0.5 * bv).astype(np.float32)).to(dev).contiguous()
             gb = torch.empty_like(vb)
-            cb.gradient(vb, gb)
             vtb = torch.randn_like(vb)
             Hb = torch.empty_like(vb)
+            torch.cuda.synchronize()
+            torch.cuda.nvtx.range_push("profile")  # ncu --nvtx --nvtx-include profile/ captures this part only
+            cb.gradient(vb, gb)
             for _ in range(3):
                 cb.hessian_matvec(vtb, Hb)
             torch.cuda.synchronize()
-        print(json.dumps({"profile": True, "grid": nb, "launches": cb.launch_count()}))
+            torch.cuda.nvtx.range_pop()
+        print(json.dumps({"profile": True, "grid": nb, "launches": cb.launch_count(),
+                          "transport": "cluster" if cb.transport_config()[0] else "two-kernel"}))
         cb.close()
         return
 
@@ -590,8 +598,10 @@ def main():
                 single()
             torch.cuda.synchronize()
             l0 = ctx.launch_count()
+            torch.cuda.nvtx.range_push("profile")  # ncu --nvtx --nvtx-include profile/ captures this part only
             st, _ = single()
             torch.cuda.synchronize()
+            torch.cuda.nvtx.range_pop()
         print(json.dumps({"profile": True, "launches_warmup": l0, "launches_step": ctx.launch_count() - l0,
                           "solve": {k: st[k] for k in ("n_newton", "n_mv", "n_pde", "n_ls")}}))
         ctx.close()
