@@ -111,10 +111,11 @@ def stream_bytes(n1, n2, nt):
     return (24 * nt + 40) * n1 * n2
 
 
-# DRAM bytes (read + write) per Gauss-Newton matvec at 512^2, nt = 32, summed over its kernels
-# from an ncu capture of the current kernels (dram__bytes_read.sum + dram__bytes_write.sum); None
-# until a capture of the current kernels has been taken.
-MATVEC_TRAFFIC_512 = None
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per Gauss-Newton matvec at 512^2,
+# nt = 32, summed over its 260 launches from one ncu capture of the current kernels (ncu flushes
+# the caches before each launch, so this is the cold-cache traffic; command in the profiles
+# folder's matvec traffic summary).
+MATVEC_TRAFFIC_512 = 1.2932e9
 
 
 def roofline(bytes_per_matvec, conc, ms_single, peak, peak_kind):
