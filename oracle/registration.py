@@ -59,9 +59,9 @@ STATUS_MAXIT = 10
 
 class Registration:
     """One registration problem: template m_T, reference m_R (both (n1, n2)),
-    nt time steps, regularization norm (1 = H1, 2 = H2), beta_v, beta_w
+    nt time steps, regularization norm (1 = H1, 2 = H2, 3 = H3), beta_v, beta_w
     (0: gamma = 0; inf: incompressible; else mass source weight) and shear
-    knob s (0 = quadratic model; s != 0 requires H1 and beta_w = inf)."""
+    knob s (0 = quadratic model; s != 0 requires H1)."""
 
     def __init__(self, mT, mR, nt, regnorm=H1, beta_v=1e-2, beta_w=np.inf, shear=0.0, hessian="gn"):
         self.mT = np.asarray(mT, dtype=np.float64)
@@ -75,17 +75,19 @@ class Registration:
             raise ValueError("hessian must be 'gn' (Gauss-Newton) or 'full'")
         self.hessian = hessian
         if self.shear != 0.0:
-            if self.regnorm != H1 or not np.isinf(self.beta_w):
-                raise ValueError("shear control requires H1 and beta_w = inf")
+            if self.regnorm != H1:
+                raise ValueError("shear control requires H1")
             self.nu = shear_ops.nu_from_shear(self.shear)
         self.v = None
         self.n_pde = 0
 
     # ---- regularization pieces -------------------------------------------
     def reg_energy(self, v):
+        e = 0.0
         if self.shear != 0.0:
-            return shear_ops.energy(v, self.nu, self.beta_v)
-        e = 0.5 * self.beta_v * inner(apply_A(v, self.regnorm), v)
+            e = shear_ops.energy(v, self.nu, self.beta_v)
+        else:
+            e = 0.5 * self.beta_v * inner(apply_A(v, self.regnorm), v)
         if 0.0 < self.beta_w < np.inf:
             w = div(v)
             e += 0.5 * self.beta_w * inner(apply_W(w), w)
@@ -114,8 +116,12 @@ class Registration:
         self.n_pde += 1
         gm = grad_history(m)
         b = body_force(lam, gm)
-        if self.shear != 0.0:
+        if self.shear != 0.0 and np.isinf(self.beta_w):
             g = shear_ops.leray(self.beta_v * shear_ops.first_variation(v, self.nu) + b)
+        elif self.shear != 0.0 and self.beta_w > 0.0:
+            g = shear_ops.reduced_gradient_mass(v, b, self.nu, self.beta_v, self.beta_w)
+        elif self.shear != 0.0:
+            g = self.beta_v * shear_ops.first_variation(v, self.nu) + b
         else:
             g = self.beta_v * apply_A(v, self.regnorm) + apply_K(b, self.regnorm, self.beta_v, self.beta_w)
         self.v, self.m, self.gradm, self.lam, self.b, self.nt_lin = v, m, gm, lam, b, nt
@@ -138,8 +144,12 @@ class Registration:
             lt = adjoint_solve(-mt[-1], self.v, nt)
             bt = body_force(lt, self.gradm)
         self.bt = bt
-        if self.shear != 0.0:
+        if self.shear != 0.0 and np.isinf(self.beta_w):
             return shear_ops.leray(self.beta_v * shear_ops.second_variation(self.v, vt, self.nu) + bt)
+        if self.shear != 0.0 and self.beta_w > 0.0:
+            return shear_ops.hessian_mass(self.v, vt, bt, self.nu, self.beta_v, self.beta_w)
+        if self.shear != 0.0:
+            return self.beta_v * shear_ops.second_variation(self.v, vt, self.nu) + bt
         return self.beta_v * apply_A(vt, self.regnorm) + apply_K(bt, self.regnorm, self.beta_v, self.beta_w)
 
     # ---- Algorithm 2 -----------------------------------------------------
