@@ -84,8 +84,9 @@ def test_shear_gradient_matches_fd_and_solve_converges():
     assert np.abs(S.div(v)).max() < 1e-11
 
 
-def test_shear_requires_h1_incompressible():
+def test_shear_requires_h1():
+    """The shear model is defined for the H1-type strain energy only; any beta_w is allowed
+    (the mass-source variant, App. A.2, is pinned in test_oracle_shear_mass)."""
     with pytest.raises(ValueError):
         Registration(np.zeros((8, 8)), np.zeros((8, 8)), 2, regnorm=S.H2, beta_w=np.inf, shear=0.5)
-    with pytest.raises(ValueError):
-        Registration(np.zeros((8, 8)), np.zeros((8, 8)), 2, regnorm=S.H1, beta_w=1e-3, shear=0.5)
+    Registration(np.zeros((8, 8)), np.zeros((8, 8)), 2, regnorm=S.H1, beta_w=1e-3, shear=0.5)
