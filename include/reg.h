@@ -107,7 +107,10 @@ void reg_default_opts(reg_solve_opts* opts);
  *            weight beta_w;
  *   shear    s in (-1, 1); s != 0 selects the nonlinear Stokes model
  *            (Eq. (e:shear-control-reg-v)) with nu = (1 + s) / (1 - s); it
- *            requires REG_H1 and gamma = +INFINITY.
+ *            requires REG_H1.  With 0 < gamma < inf the mass source is
+ *            eliminated as in App. A.2 (M = 2 beta_v eta_bar (beta_w(-Lap +
+ *            I))^-1 + I with eta_bar the mean viscosity); gamma = 0 applies
+ *            no projection.
  * Allocates the device workspace on the current device. */
 int reg_create(reg_grid grid, int nt, int regnorm, double beta, double gamma, double shear, reg_ctx** out);
 void reg_destroy(reg_ctx* ctx);

@@ -110,7 +110,7 @@ static int alloc_hist(reg_ctx* c, int nt) {
 extern "C" void reg_destroy(reg_ctx* c) {
     if (!c) return;
     float** fl[] = {&c->mT, &c->mR, &c->v_lin, &c->E_lin, &c->eta_lin, &c->w0, &c->w1, &c->w2, &c->w3,
-                    &c->bvec, &c->vtmp, &c->vtmp2, &c->gtmp, &c->T3, &c->g, &c->r, &c->z, &c->s, &c->Hs,
+                    &c->bvec, &c->vtmp, &c->vtmp2, &c->gtmp, &c->T3, &c->T3b, &c->vx, &c->g, &c->r, &c->z, &c->s, &c->Hs,
                     &c->vt, &c->vtrial, &c->F, &c->Fs, &c->gF, &c->gv, &c->ybuf, &c->ytrial, &c->vtil};
     for (auto p : fl) cudaFree(*p);
     for (int i = 0; i < 6; ++i) cudaFree(c->S[i]);
@@ -132,8 +132,7 @@ static int check_params(int nt, int regnorm, double beta, double gamma, double s
     if (!(beta > 0.0) || !std::isfinite(beta)) return reg_fail(REG_ERR_ARG, "beta must be finite and > 0");
     if (!(gamma >= 0.0)) return reg_fail(REG_ERR_ARG, "gamma must be >= 0 or +INFINITY");
     if (!(shear > -1.0 && shear < 1.0)) return reg_fail(REG_ERR_ARG, "shear must be in (-1, 1)");
-    if (shear != 0.0 && (regnorm != REG_H1 || !std::isinf(gamma)))
-        return reg_fail(REG_ERR_ARG, "shear control requires REG_H1 and gamma = +INFINITY");
+    if (shear != 0.0 && regnorm != REG_H1) return reg_fail(REG_ERR_ARG, "shear control requires REG_H1");
     return REG_OK;
 }
 
@@ -194,6 +193,7 @@ extern "C" int reg_create(reg_grid grid, int nt, int regnorm, double beta, doubl
     A(&c->mT, N); A(&c->mR, N); A(&c->v_lin, 2 * N); A(&c->E_lin, 3 * N); A(&c->eta_lin, N);
     A(&c->w0, N); A(&c->w1, N); A(&c->w2, N); A(&c->w3, N);
     A(&c->bvec, 2 * N); A(&c->vtmp, 2 * N); A(&c->vtmp2, 2 * N); A(&c->gtmp, 4 * N); A(&c->T3, 3 * N);
+    A(&c->T3b, 3 * N); A(&c->vx, 2 * N);
     A(&c->g, 2 * N); A(&c->r, 2 * N); A(&c->z, 2 * N); A(&c->s, 2 * N); A(&c->Hs, 2 * N);
     A(&c->vt, 2 * N); A(&c->vtrial, 2 * N);
     A(&c->ybuf, 2 * N); A(&c->ytrial, 2 * N); A(&c->vtil, 2 * N);
@@ -221,6 +221,13 @@ extern "C" int reg_create(reg_grid grid, int nt, int regnorm, double beta, doubl
     }
     cudaMemset(c->mT, 0, sizeof(float) * N);
     cudaMemset(c->mR, 0, sizeof(float) * N);
+    {
+        const double one = 1.0;  // the unit denominator of device-scalar-scaled updates
+        if (cudaMemcpy(c->d_scal + SL_ONE, &one, sizeof(double), cudaMemcpyHostToDevice) != cudaSuccess) {
+            reg_destroy(c);
+            return reg_fail(REG_ERR_CUDA, "scalar upload failed");
+        }
+    }
     *out = c;
     return REG_OK;
 }
@@ -398,6 +405,7 @@ static SpecParams spec_params(reg_ctx* c, float coefA) {
     P.escale = h1 * h2 / (double)c->N;
     P.ebv = 0.5 * c->beta_v;
     P.ebw = (c->pmode == PROJ_MASS) ? 0.5 * c->beta_w : 0.0;
+    P.eta_bar = c->d_scal + SL_ETABAR;
     return P;
 }
 
@@ -463,6 +471,37 @@ static void sp_grad_vec(reg_ctx* c, const float* u, float* gv) {
     sp_grad(c, u + c->N, gv + 2 * (size_t)c->N);
 }
 
+// out = div T (2 planes) of a symmetric tensor T = (T11, T12, T22)
+static void sp_div_tensor(reg_ctx* c, const float* T, float* out) {
+    const size_t N = c->N;
+    launch_r2c_vec(c, T, T + N, c->S[0], c->S[1]);
+    const float2* in0[2] = {c->S[0], c->S[1]};
+    float2* o0[1] = {c->S[2]};
+    launch_col(c, OP_DIV, in0, o0, spec_params(c, 0.f), nullptr);
+    launch_r2c_vec(c, T + N, T + 2 * N, c->S[0], c->S[1]);
+    float2* o1[1] = {c->S[3]};
+    launch_col(c, OP_DIV, in0, o1, spec_params(c, 0.f), nullptr);
+    launch_c2r_vec(c, c->S[2], c->S[3], out, out + N);
+}
+
+// Shear model with a mass source (App. A.2) or without a constraint: out = -beta_v div T + b
+// + P(beta_v div T' - b), T' = T - 2 eta_bar Et (eta_bar in d_scal[SL_ETABAR]), P the
+// multiplier OP_MASSP (mass source) or 0 (gamma = 0).  T = 2 eta E[v] and Et = E[v] for the
+// reduced gradient; T = 2 eta (I + Q) E[v~] and Et = E[v~] for the Hessian (Et is overwritten).
+static void shear_mass_assemble(reg_ctx* c, const float* T, float* Et, const float* b, float* out) {
+    const long long N = c->N;
+    const float bv = (float)c->beta_v;
+    sp_div_tensor(c, T, c->gtmp);
+    if (c->pmode == PROJ_MASS) {
+        launch_axpby(c, 3 * N, -2.f, Et, 1.f, const_cast<float*>(T), SL_ETABAR, SL_ONE, Et);  // Et := T - 2 eta_bar Et
+        sp_div_tensor(c, Et, c->gtmp + 2 * N);
+        launch_axpby(c, 2 * N, bv, c->gtmp + 2 * N, -1.f, const_cast<float*>(b), -1, -1, c->vx);  // beta_v div T' - b
+        sp_vec(c, OP_MASSP, 0.f, c->vx, c->vx);
+    }
+    launch_axpby(c, 2 * N, -bv, c->gtmp, 1.f, const_cast<float*>(b), -1, -1, out);
+    if (c->pmode == PROJ_MASS) launch_axpby(c, 2 * N, 1.f, c->vx, 1.f, out, -1, -1, out);
+}
+
 // out = P_L(coefA div T + b), T = 3 planes (shear model)
 static void sp_divt_proj(reg_ctx* c, float coefA, const float* T, const float* b, float* out) {
     const size_t N = c->N;
@@ -482,6 +521,15 @@ static void reg_energy(reg_ctx* c, const float* v) {
         int np = launch_shear_strain(c, c->gtmp, (float)c->nu, nullptr, nullptr, nullptr, c->d_part);
         const double coef = c->beta_v * (2.0 * c->nu / (c->nu + 1.0)) * hh(c);
         launch_finalize(c, c->d_part, np, c->d_scal + SL_JREG, coef, 0, 0);
+        if (c->pmode == PROJ_MASS) {
+            // + (beta_w / 2) <(-Lap + I) w, w>, w = div v (OP_ENERGY with the beta_v part off)
+            SpecParams P = spec_params(c, 0.f);
+            P.ebv = 0.0;
+            launch_r2c_vec(c, v, v + c->N, c->S[0], c->S[1]);
+            const float2* in[2] = {c->S[0], c->S[1]};
+            launch_col(c, OP_ENERGY, in, nullptr, P, c->d_part);
+            launch_finalize(c, c->d_part, col_blocks(c), c->d_scal + SL_JREG, 1.0, 1, 0);
+        }
         return;
     }
     launch_r2c_vec(c, v, v + c->N, c->S[0], c->S[1]);
@@ -675,7 +723,15 @@ static void gradient_launches(reg_ctx* c, const float* v, float* g, int nt) {
     if (c->shear_model) {
         sp_grad_vec(c, v, c->gtmp);
         launch_shear_strain(c, c->gtmp, (float)c->nu, c->E_lin, c->eta_lin, c->T3, nullptr);
-        sp_divt_proj(c, -(float)c->beta_v, c->T3, c->bvec, g);
+        // mean viscosity of the linearization point (App. A.2: eta = eta^ + eta_bar)
+        const int np = launch_sum_partial(c, c->eta_lin, c->N, c->d_part);
+        launch_finalize(c, c->d_part, np, c->d_scal + SL_ETABAR, 1.0 / (double)c->N, 0, 0);
+        if (c->pmode == PROJ_LERAY) {
+            sp_divt_proj(c, -(float)c->beta_v, c->T3, c->bvec, g);
+        } else {
+            cudaMemcpyAsync(c->T3b, c->E_lin, sizeof(float) * 3 * c->N, cudaMemcpyDeviceToDevice, c->stream);
+            shear_mass_assemble(c, c->T3, c->T3b, c->bvec, g);
+        }
     } else {
         sp_assemble(c, (float)c->beta_v, v, c->bvec, g);
     }
@@ -739,7 +795,12 @@ static void matvec_launches(reg_ctx* c, const float* vt, float* Hvt) {
     if (c->shear_model) {
         sp_grad_vec(c, vt, c->gtmp);
         launch_shear_second(c, c->gtmp, c->E_lin, c->eta_lin, (float)c->nu, c->T3);
-        sp_divt_proj(c, -(float)c->beta_v, c->T3, c->bvec, Hvt);
+        if (c->pmode == PROJ_LERAY) {
+            sp_divt_proj(c, -(float)c->beta_v, c->T3, c->bvec, Hvt);
+        } else {
+            launch_shear_strain(c, c->gtmp, (float)c->nu, c->T3b, nullptr, nullptr, nullptr);  // E[v~]
+            shear_mass_assemble(c, c->T3, c->T3b, c->bvec, Hvt);
+        }
     } else {
         sp_assemble(c, (float)c->beta_v, vt, c->bvec, Hvt);
     }

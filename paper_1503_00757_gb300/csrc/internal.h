@@ -27,7 +27,8 @@ enum SpecOp {
     OP_ASSEMBLE_Y = 13,  // 4 in -> 2 out: Pi0 x01 + Q^-1 K^ x23 (Pi0 drops k = 0): gradient / Hessian in y
     OP_QNORM = 14,       // 2 in -> 0 out: FP64 sum of |Q x|^2 (the v-norm of a y-space gradient or residual)
     OP_ENERGY_Y = 15,    // 2 in -> 0 out: FP64 regularization energy of v = Q^-1 x from x
-    OP_SMOOTH = 16       // 1 in -> 1 out: exp(-coefA |k|^2) x (Gaussian filter of a scalar field)
+    OP_SMOOTH = 16,      // 1 in -> 1 out: exp(-coefA |k|^2) x (Gaussian filter of a scalar field)
+    OP_MASSP = 17        // 2 in -> 2 out: k~ k~^T x / (|k~|^2 m), m = 1 + 2 beta_v eta_bar / (beta_w (1 + |k|^2))
 };
 
 // Projection modes (Eq. (e:project-body-force)):
@@ -43,6 +44,7 @@ struct SpecParams {
     double escale;  // OP_ENERGY: h1 h2 / (n1 n2)
     double ebv;     // OP_ENERGY: beta_v / 2
     double ebw;     // OP_ENERGY: beta_w / 2 (0 unless PROJ_MASS)
+    const double* eta_bar;  // OP_MASSP: device scalar, the mean viscosity of the shear model
 };
 
 enum KClass { KC_COL = 0, KC_ROWSTAGE = 1, KC_ROW = 2, KC_POINT = 3, KC_TRANSPORT = 4, KC_COUNT = 5 };
@@ -51,7 +53,7 @@ enum KClass { KC_COL = 0, KC_ROWSTAGE = 1, KC_ROW = 2, KC_POINT = 3, KC_TRANSPOR
 enum Slot {
     SL_JDATA = 0, SL_JREG = 1, SL_DOT0 = 2, SL_DOT1 = 3, SL_DOT2 = 4, SL_RZ = 5, SL_SHS = 6,
     SL_RZNEW = 7, SL_RNORM2 = 8, SL_VMAX = 9, SL_GNORM2 = 10, SL_GV = 11,
-    SL_DET0 = 12, /* 5 slots */ SL_COUNT = 20
+    SL_DET0 = 12, /* 5 slots */ SL_ETABAR = 17, SL_ONE = 18, SL_COUNT = 20
 };
 
 struct EventPair { cudaEvent_t a, b; int kclass; double bytes; };
@@ -94,6 +96,7 @@ struct reg_ctx {
     float *w0, *w1, *w2, *w3;
     // vector work fields (2N each)
     float *bvec, *vtmp, *vtmp2, *gtmp, *T3;  // T3: 3 planes
+    float *T3b, *vx;  // shear model with a mass source: a second tensor (3 planes), a vector (2N)
     // PCG / solve workspace (2N each)
     float *g, *r, *z, *s, *Hs, *vt, *vtrial;
     // preconditioned coordinates y = Q v of reg_solve (2N each): iterate, trial iterate, Q^-1 of a direction
@@ -199,6 +202,8 @@ void launch_adj_init(reg_ctx* ctx, const float* a, float ca, const float* c, flo
 // ---- pointwise / reductions ----
 // part[...] <- partial sums of sum_i x_i y_i over n elements; returns #partials
 int launch_dot_partial(reg_ctx* ctx, const float* x, const float* y, long long n, double* part);
+// part[...] <- partial sums of sum_i x_i over n elements; returns #partials
+int launch_sum_partial(reg_ctx* ctx, const float* x, long long n, double* part);
 int launch_maxnorm_partial(reg_ctx* ctx, const float* v, int N, double* part);
 // out[slot] = scale * sum(part[0..np)) (+ out[slot] if accumulate); op 0 = sum, 1 = max, 2 = min
 void launch_finalize(reg_ctx* ctx, const double* part, int np, double* out, double scale, int accumulate, int op);

@@ -627,6 +627,18 @@ __device__ __forceinline__ void spec_apply(const SpecParams& P, float k1o, float
             e += P.ebw * (1.0 + kk) * (dr * dr + di * di) / ((double)P.beta_v * a);
         }
         eacc += ew * e;
+    } else if (OP == OP_MASSP) {
+        const float kko = k1o * k1o + k2o * k2o;
+        if (kko == 0.f) {
+            y[0] = make_float2(0.f, 0.f);
+            y[1] = make_float2(0.f, 0.f);
+        } else {
+            const float m = 1.f + 2.f * P.beta_v * (float)__ldg(P.eta_bar) / (P.beta_w * (1.f + kk));
+            const float c = s / (kko * m);
+            const float2 pr = cadd(cscale(x[0], k1o), cscale(x[1], k2o));
+            y[0] = cscale(pr, c * k1o);
+            y[1] = cscale(pr, c * k2o);
+        }
     } else if (OP == OP_SMOOTH) {
         y[0] = cscale(x[0], expf(-P.coefA * kk) * s);
     } else if (OP == OP_SMOOTH_PROJ) {
@@ -1018,6 +1030,7 @@ void launch_col(reg_ctx* ctx, int op, const float2* const* in, float2* const* ou
         case OP_DIV1: launch_col_t<1, 1, OP_DIV1>(ctx, in, out, P, part); break;
         case OP_SMOOTH_PROJ: launch_col_t<2, 2, OP_SMOOTH_PROJ>(ctx, in, out, P, part); break;
         case OP_SMOOTH: launch_col_t<1, 1, OP_SMOOTH>(ctx, in, out, P, part); break;
+        case OP_MASSP: launch_col_t<2, 2, OP_MASSP>(ctx, in, out, P, part); break;
         case OP_QINV: launch_col_t<2, 2, OP_QINV>(ctx, in, out, P, part); break;
         case OP_QMUL: launch_col_t<2, 2, OP_QMUL>(ctx, in, out, P, part); break;
         case OP_ASSEMBLE_Y: launch_col_t<4, 2, OP_ASSEMBLE_Y>(ctx, in, out, P, part); break;
@@ -1042,6 +1055,22 @@ __global__ void k_dot_partial(const float* __restrict__ x, const float* __restri
 int launch_dot_partial(reg_ctx* ctx, const float* x, const float* y, long long n, double* part) {
     ktimer_begin(ctx, KC_POINT, 8.0 * n);
     launch_k(ctx, k_dot_partial, NBLK_RED, NTHREADS, 0, x, y, n, part);
+    ktimer_end(ctx);
+    return NBLK_RED;
+}
+
+__global__ void k_sum_partial(const float* __restrict__ x, long long n, double* part) {
+    pdl_entry();
+    double acc = 0.0;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        acc += (double)x[i];
+    const double s = block_reduce<0>(acc);
+    if (threadIdx.x == 0) part[blockIdx.x] = s;
+}
+
+int launch_sum_partial(reg_ctx* ctx, const float* x, long long n, double* part) {
+    ktimer_begin(ctx, KC_POINT, 4.0 * n);
+    launch_k(ctx, k_sum_partial, NBLK_RED, NTHREADS, 0, x, n, part);
     ktimer_end(ctx);
     return NBLK_RED;
 }

@@ -51,7 +51,7 @@ def test_invalid_arguments_rejected_without_gpu(lib):
         (reg_grid(64, 64), 4, 1, 1e-2, -1.0, 0.0),        # gamma < 0
         (reg_grid(64, 64), 4, 1, 1e-2, math.inf, 1.0),    # shear out of range
         (reg_grid(64, 64), 4, 2, 1e-2, math.inf, 0.5),    # shear needs H1
-        (reg_grid(64, 64), 4, 1, 1e-2, 1e-3, 0.5),        # shear needs w = 0
+        (reg_grid(64, 64), 4, 1, -1e-3, 1e-3, 0.5),       # beta_v must be positive
     ]
     for args in bad:
         assert lib.reg_create(*args, ctypes.byref(h)) == 1
