@@ -487,6 +487,8 @@ def main():
                     help="run --warmup registrations then one registration and exit (for ncu launch lists)")
     ap.add_argument("--profile-net", action="store_true",
                     help="run 4 training steps of the warm-start network (256^2, batch 8) and exit (for ncu)")
+    ap.add_argument("--conv-kernel", default="tcgen05", choices=["tcgen05", "mma_sync"],
+                    help="with --profile-net: the convolution kernel of the network")
     ap.add_argument("--profile-grid", type=int, default=0,
                     help="with --profile: instead run a gradient and 3 GN matvecs on this grid (nt=32)")
     ap.add_argument("--transport", default="auto", choices=["auto", "cluster", "two-kernel"],
@@ -501,11 +503,31 @@ def main():
         from paper_1503_00757_gb300.binding import Net, flatten_params
         x = torch.from_numpy(ws.make_images(256, range(ws.TRAIN_SEED, ws.TRAIN_SEED + 8))).cuda().contiguous()
         t = torch.zeros(8, 2, 256, 256, device="cuda")
+        from paper_1503_00757_gb300.binding import REG_CONV_MMA_SYNC, REG_CONV_TCGEN05
         net = Net(256, 256, 8)
+        net.set_conv_kernel(REG_CONV_TCGEN05 if args.conv_kernel == "tcgen05" else REG_CONV_MMA_SYNC)
         net.set_params(torch.tensor(flatten_params(ws.he_init(1)), dtype=torch.float32, device="cuda"))
         losses = [net.train_step(x, t, 1e-3) for _ in range(4)]
+        # forward passes (8 convolutions + the output projection), timed with CUDA events
+        v = torch.empty(8, 2, 256, 256, device="cuda")
+        for _ in range(3):
+            net.forward(x, v)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         torch.cuda.synchronize()
-        print(json.dumps({"profile_net": True, "losses": losses}))
+        e0.record()
+        for _ in range(20):
+            net.forward(x, v)
+        e1.record()
+        torch.cuda.synchronize()
+        fwd_ms = e0.elapsed_time(e1) / 20
+        # training steps (forward, backward, Adam; each reads its loss back)
+        e0.record()
+        for _ in range(10):
+            net.train_step(x, t, 1e-4)
+        e1.record()
+        torch.cuda.synchronize()
+        print(json.dumps({"profile_net": True, "conv_kernel": args.conv_kernel, "losses": losses,
+                          "forward_ms": fwd_ms, "train_step_ms": e0.elapsed_time(e1) / 10}))
         net.close()
         return
 

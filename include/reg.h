@@ -403,6 +403,34 @@ int reg_net_set_output_scale(reg_net* net, float scale);
 int reg_net_loss_grad(reg_net* net, const float* images, const float* targets, int B, double* loss, float* grads);
 /* One Adam step with learning rate lr on that loss.  Synchronous (loss is read back). */
 int reg_net_train_step(reg_net* net, const float* images, const float* targets, int B, float lr, double* loss);
+/* Convolution kernel of every forward and input-gradient convolution:
+ * REG_CONV_TCGEN05 (default): 5th-generation tensor cores, FP32 accumulator in
+ *   tensor memory; a persistent CTA per tile slot, MMAs issued by one thread.
+ *   An MMA batch that does not complete within 1 s makes the kernel stop and
+ *   set a flag; the next reg_net_forward / loss_grad / train_step call (and
+ *   loss_grad / train_step themselves) then return REG_ERR_TIMEOUT.
+ * REG_CONV_MMA_SYNC: warp-level mma.sync m16n8k16 tensor-core kernel.
+ * Both accumulate the same products in FP32 (summation order differs). */
+#define REG_CONV_TCGEN05 1
+#define REG_CONV_MMA_SYNC 0
+int reg_net_set_conv_kernel(reg_net* net, int kind);
+/* Keep (on != 0) every layer's output gradient during reg_net_loss_grad /
+ * train_step for reg_net_layer_tensor (allocates 8 x max_batch x H x W x 32
+ * BF16 values on first use). */
+int reg_net_set_record(reg_net* net, int on);
+/* Copy one layer tensor of the last pass (device out, B x C x H x W floats,
+ * B <= the batch of that pass):
+ *   REG_NET_INPUT:       the BF16 input of layer l (C = Cin; l = 0: the packed images);
+ *   REG_NET_OUTPUT:      its output after the ReLU (BF16, C = Cout), for the last layer
+ *                        the FP32 raw network output (C = 2);
+ *   REG_NET_OUTPUT_GRAD: the BF16 gradient w.r.t. the layer's pre-activation output as
+ *                        the backward pass used it (C = Cout; reg_net_set_record), scaled by
+ *                        M = 2 B H W (the 1 / M of the loss is applied to the parameter
+ *                        gradients).  Asynchronous on the net's stream. */
+#define REG_NET_INPUT 0
+#define REG_NET_OUTPUT 1
+#define REG_NET_OUTPUT_GRAD 2
+int reg_net_layer_tensor(reg_net* net, int kind, int layer, int B, float* out);
 
 /* ---- allocation-free entry point (the paper has no counterpart) ---- */
 

@@ -14,6 +14,8 @@ from .build import LIB_PATH
 
 REG_H1, REG_H2, REG_H3 = 1, 2, 3
 REG_NT_FIXED, REG_NT_CFL = 0, 1
+REG_CONV_MMA_SYNC, REG_CONV_TCGEN05 = 0, 1
+REG_NET_INPUT, REG_NET_OUTPUT, REG_NET_OUTPUT_GRAD = 0, 1, 2
 STATUS = {0: "REG_OK", 1: "REG_ERR_ARG", 2: "REG_ERR_CUDA", 3: "REG_ERR_NOMEM", 4: "REG_ERR_NAN",
           5: "REG_ERR_LINESEARCH", 6: "REG_ERR_PCG_MAXIT", 7: "REG_ERR_TIMEOUT", 8: "REG_WARN_CFL",
           9: "REG_ERR_STATE", 10: "REG_ERR_MAXIT"}
@@ -100,6 +102,9 @@ _SIGS = {
     "reg_net_set_output_scale": ([_P, ctypes.c_float], _I),
     "reg_net_loss_grad": ([_P, _P, _P, _I, ctypes.POINTER(_D), _P], _I),
     "reg_net_train_step": ([_P, _P, _P, _I, ctypes.c_float, ctypes.POINTER(_D)], _I),
+    "reg_net_set_conv_kernel": ([_P, _I], _I),
+    "reg_net_set_record": ([_P, _I], _I),
+    "reg_net_layer_tensor": ([_P, _I, _I, _I, _P], _I),
 }
 
 _lib = None
@@ -303,6 +308,18 @@ class Net:
         _check(lib().reg_net_train_step(self.h, _ptr(images, n, "images"), _ptr(targets, n, "targets"), B,
                                         ctypes.c_float(lr), ctypes.byref(loss)))
         return loss.value
+
+
+    def set_conv_kernel(self, kind):
+        """REG_CONV_TCGEN05 (default) or REG_CONV_MMA_SYNC."""
+        _check(lib().reg_net_set_conv_kernel(self.h, int(kind)))
+
+    def set_record(self, on=True):
+        _check(lib().reg_net_set_record(self.h, 1 if on else 0))
+
+    def layer_tensor(self, kind, layer, out):
+        """Layer tensor of the last pass into out (device, B x C x H x W floats)."""
+        _check(lib().reg_net_layer_tensor(self.h, int(kind), int(layer), out.shape[0], _ptr(out, out.numel(), "out")))
 
 
 def flatten_params(params):

@@ -21,14 +21,19 @@
 // are zero); forward weights [Cout][tap][Cin] BF16; transposed-flipped
 // weights [Cin][8 - tap][Cout] for the input gradient (the adjoint of a
 // circular correlation is the correlation with the flipped kernel).
+#include <cuda.h>
 #include <cuda_bf16.h>
+#include <cudaTypedefs.h>
 
+#include <algorithm>
 #include <cmath>
+#include <mutex>
 #include <cstdint>
 #include <string>
 #include <vector>
 
 #include "internal.h"
+#include "tc.cuh"
 
 typedef __nv_bfloat16 bf16;
 
@@ -197,6 +202,322 @@ __global__ void __launch_bounds__(256) k_conv3x3(const bf16* __restrict__ in, co
 }
 
 // ---------------------------------------------------------------------------
+// conv3x3 on the 5th-generation tensor cores (tcgen05, accumulator in TMEM),
+// operands staged by TMA: the same implicit GEMM and the same MODEs as
+// k_conv3x3.  A CTA owns one TH x TW tile at a time (persistent loop over
+// tiles); its 256 pixels form two M = 128 blocks (tile rows 0-3 and 4-7),
+// N = COUT, and each of the 9 taps adds CIN / 16 MMAs of K = 16 per block,
+// issued by one thread; TMEM columns 0 and 32 hold the two FP32 accumulators.
+//
+// Shared-memory operands, canonical K-major without swizzle (16-byte rows of
+// 8 channels, 8-row core matrices of 128 contiguous bytes):
+//   B (weights, staged once per CTA): row (tap, c, co) at ((tap NC + c) COUT + co) 16,
+//     so an MMA's K = 16 slice (chunks c, c + 1) has LBO = 16 COUT, SBO = 128;
+//   A (input tile, two buffers): three column-shifted copies s = 0, 1, 2 of the
+//     halo tile; block (s, c) holds channels 8c..8c+7 of halo pixel (hr, x + s)
+//     at row hr TW + x, blocks ABS = (TH + 2) TW 16 bytes apart.  Tap (dy, dx) of
+//     M block mt starts at block (dx, c), row (4 mt + dy) TW: 128 consecutive
+//     rows with the uniform stride the descriptor needs (LBO = ABS, SBO = 128).
+// Each block (s, c) is one TMA box (8 channels x TW columns x TH + 2 rows) of
+// a 5-D view of the NHWC activations, dims (C, rx, X, ry, Y + (H/d) b), in
+// which the sub-grid (ry, rx) of dilation d is a plain 3-D box.  TMA cannot
+// wrap around the periodic boundary (it zero-fills outside the view and reads
+// across image boundaries), so halo rows 0 / TH+1 and columns 0 / TW+1 of
+// tiles at a sub-grid edge are rewritten from global memory by the threads.
+// Pipeline over a CTA's tiles i = 0, 1, ...: three A buffers and two TMEM
+// accumulator sets.  In iteration i thread 0 issues the MMAs of tile i, then,
+// once the MMAs of tile i - 1 have completed, the TMA of tile i + 2 into the
+// buffer tile i - 1 used, while all threads load tile i + 1's wrap-around
+// pieces into registers and drain tile i - 1's accumulators (epilogue), so
+// TMA, tensor cores and epilogue overlap.
+// ---------------------------------------------------------------------------
+template <int CIN, int COUT>
+struct TcConv {
+    static constexpr int NC = CIN / 8;
+    static constexpr int ABS = (TH + 2) * TW * 16;                 // one TMA box
+    static constexpr int BBYTES = 9 * NC * COUT * 16;
+    static constexpr int ABYTES = 3 * NC * ABS;                    // one A buffer
+    static constexpr int NBUF = 3;                                 // A buffers (TMA two tiles ahead)
+    static constexpr int SMEM = 128 + BBYTES + NBUF * ABYTES + 64 + COUT * 4;
+    static constexpr int TMEM_COLS = 128;                          // two accumulator sets of 2 x 32 columns
+    static constexpr int THREADS = 256;
+    // wrap-around pieces of a tile: halo rows 0 and TH + 1 (TW + 2 columns each), then halo
+    // columns 0 and TW + 1 (all TH + 2 rows: a corner is wrong whenever its row or its
+    // column lies outside the sub-grid), each NC 16-byte chunks
+    static constexpr int NROWP = 2 * (TW + 2) * NC;
+    static constexpr int NFIX = NROWP + 2 * (TH + 2) * NC;
+    static constexpr int NFIXK = (NFIX + THREADS - 1) / THREADS;   // per thread
+    static_assert(ABS % 128 == 0 && BBYTES % 128 == 0, "TMA destinations 128-byte aligned");
+    static_assert((3 * NC - 1) * ABS + (TH + 2) * TW * 16 <= ABYTES, "A operand out of range");
+    static_assert(TW == 32 && TH == 8, "two M = 128 blocks of four 32-pixel rows");
+    static_assert(COUT == 16 || COUT == 32, "N = 16 or 32");
+};
+
+constexpr uint64_t TC_WAIT_NS = 1000000000ull;  // 1 s bound on any TMA or MMA completion wait
+
+// wrap-around piece j of a tile at a sub-grid edge: its halo position (packed hr | hx << 8 |
+// c << 16, or -1 when the tile does not need it) and its 16 bytes of input
+template <int CIN>
+__device__ __forceinline__ int tc_fix_piece(const bf16* __restrict__ in, const TileMap& tm, int b, int H, int W,
+                                            int j, uint4& val) {
+    constexpr int NC = CIN / 8;
+    constexpr int NROWP = 2 * (TW + 2) * NC;
+    int hr, hx, c;
+    bool need;
+    if (j < NROWP) {
+        const int r = j / ((TW + 2) * NC), rem = j - r * ((TW + 2) * NC);
+        hx = rem / NC;
+        c = rem - hx * NC;
+        hr = r ? TH + 1 : 0;
+        need = r ? (tm.Y0 + TH == tm.Hs) : (tm.Y0 == 0);
+    } else {
+        const int jj = j - NROWP;
+        const int e = jj / ((TH + 2) * NC), rem = jj - e * ((TH + 2) * NC);
+        hr = rem / NC;
+        c = rem - hr * NC;
+        hx = e ? TW + 1 : 0;
+        need = e ? (tm.X0 + TW == tm.Ws) : (tm.X0 == 0);
+    }
+    if (!need) return -1;
+    const int gy = tm.gy(tm.Y0 + hr - 1 + tm.Hs), gx = tm.gx(tm.X0 + hx - 1 + tm.Ws);
+    val = __ldg(reinterpret_cast<const uint4*>(in + (((size_t)b * H + gy) * W + gx) * CIN) + c);
+    return hr | (hx << 8) | (c << 16);
+}
+
+// TMA of a tile's halo into an A buffer: one box per shifted copy s and channel chunk c
+// (completion on *bar, whose expected byte count the caller has raised)
+template <int CIN>
+__device__ __forceinline__ void tc_issue_halo(const CUtensorMap* map, unsigned char* dst, uint64_t* bar,
+                                              const TileMap& tm, int b) {
+    constexpr int NC = CIN / 8;
+    constexpr int ABS = TcConv<CIN, 16>::ABS;
+#pragma unroll
+    for (int s = 0; s < 3; ++s)
+#pragma unroll
+        for (int c = 0; c < NC; ++c)
+            tc::tma_load_5d(dst + (s * NC + c) * ABS, map, bar, 8 * c, tm.rx, tm.X0 - 1 + s, tm.ry,
+                            b * tm.Hs + tm.Y0 - 1);
+}
+
+// this thread's wrap-around pieces of tile t (none for an interior tile)
+template <int CIN, int K>
+__device__ __forceinline__ void tc_load_fix(const bf16* __restrict__ in, int t, int tiles_per_img, int H, int W,
+                                            int dil, uint4 (&fixv)[K], int (&fixp)[K]) {
+    constexpr int NFIX = TcConv<CIN, 16>::NFIX;
+    const int b = t / tiles_per_img;
+    const TileMap tm = tile_map(t - b * tiles_per_img, H, W, dil);
+    const bool edge = tm.Y0 == 0 || tm.Y0 + TH == tm.Hs || tm.X0 == 0 || tm.X0 + TW == tm.Ws;
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+        const int j = threadIdx.x + (int)blockDim.x * k;
+        fixp[k] = (edge && j < NFIX) ? tc_fix_piece<CIN>(in, tm, b, H, W, j, fixv[k]) : -1;
+    }
+}
+
+// the pieces into every shifted copy that holds them
+template <int CIN, int K>
+__device__ __forceinline__ void tc_store_fix(unsigned char* sA, const uint4 (&fixv)[K], const int (&fixp)[K]) {
+    constexpr int NC = CIN / 8;
+    constexpr int ABS = TcConv<CIN, 16>::ABS;
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+        if (fixp[k] < 0) continue;
+        const int hr = fixp[k] & 255, hx = (fixp[k] >> 8) & 255, c = fixp[k] >> 16;
+#pragma unroll
+        for (int s = 0; s < 3; ++s) {
+            const int x = hx - s;
+            if (x >= 0 && x < TW) *reinterpret_cast<uint4*>(sA + (s * NC + c) * ABS + (hr * TW + x) * 16) = fixv[k];
+        }
+    }
+}
+
+template <int CIN, int COUT, int MODE>
+__global__ void __launch_bounds__(256) k_conv3x3_tc(const __grid_constant__ CUtensorMap tmap,
+                                                    const bf16* __restrict__ in, const bf16* __restrict__ w,
+                                                    const float* __restrict__ bias, void* out,
+                                                    const bf16* __restrict__ mask, int H, int W, int dil,
+                                                    int tiles_per_img, int B, int* err) {
+    using G = TcConv<CIN, COUT>;
+    constexpr int NC = G::NC;
+    extern __shared__ unsigned char smraw[];
+    unsigned char* sB = smraw + ((128u - (tc::smem_u32(smraw) & 127u)) & 127u);
+    unsigned char* sA0 = sB + G::BBYTES;
+    uint64_t* bars = reinterpret_cast<uint64_t*>(sA0 + G::NBUF * G::ABYTES);  // TMA of buffer 0..2; MMA set 0, 1
+    uint32_t* s_tmem = reinterpret_cast<uint32_t*>(bars + 5);
+    float* s_bias = reinterpret_cast<float*>(bars + 8);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int total = tiles_per_img * B;
+    const int G0 = gridDim.x;
+    auto issue = [&](int t, int buf) {
+        const int b = t / tiles_per_img;
+        const TileMap tm = tile_map(t - b * tiles_per_img, H, W, dil);
+        tc::mbar_arrive_expect_tx(&bars[buf], G::ABYTES);
+        tc_issue_halo<CIN>(&tmap, sA0 + buf * G::ABYTES, &bars[buf], tm, b);
+    };
+    uint4 fixv[G::NFIXK];
+    int fixp[G::NFIXK];
+    auto load_fix = [&](int t) { tc_load_fix<CIN>(in, t, tiles_per_img, H, W, dil, fixv, fixp); };
+    // epilogue of tile t from accumulator set `set`: warp w reads TMEM lanes 32 (w % 4).. of
+    // M block w / 4, i.e. tile row 4 (w / 4) + w % 4, one pixel per thread
+    auto epilogue = [&](int t, int set, uint32_t tmem) {
+        const int b = t / tiles_per_img;
+        const TileMap tm = tile_map(t - b * tiles_per_img, H, W, dil);
+        const int q = warp & 3, mt = warp >> 2;
+        const uint32_t taddr = tmem + ((uint32_t)(32 * q) << 16) + 64 * set + 32 * mt;
+        float v[COUT];
+        if constexpr (COUT == 32) {
+            uint32_t r[32];
+            tc::ld_32x32b_x32(taddr, r);
+            tc::wait_ld();
+#pragma unroll
+            for (int j = 0; j < 32; ++j) v[j] = __uint_as_float(r[j]);
+        } else {
+            uint32_t r[16];
+            tc::ld_32x32b_x16(taddr, r);
+            tc::wait_ld();
+#pragma unroll
+            for (int j = 0; j < 16; ++j) v[j] = __uint_as_float(r[j]);
+        }
+        const int y = tm.gy(tm.Y0 + 4 * mt + q), x = tm.gx(tm.X0 + lane);
+        const size_t pix = ((size_t)b * H + y) * W + x;
+        if (MODE == 1) {
+            float* o = reinterpret_cast<float*>(out);
+            const size_t plane = (size_t)H * W;
+            o[((size_t)b * 2 + 0) * plane + (size_t)y * W + x] = v[0] + s_bias[0];
+            o[((size_t)b * 2 + 1) * plane + (size_t)y * W + x] = v[1] + s_bias[1];
+        } else {
+            uint4* o = reinterpret_cast<uint4*>(reinterpret_cast<bf16*>(out) + pix * COUT);
+            const uint4* mk = MODE == 2 ? reinterpret_cast<const uint4*>(mask + pix * COUT) : nullptr;
+#pragma unroll
+            for (int j = 0; j < COUT / 8; ++j) {
+                float e[8];
+#pragma unroll
+                for (int k = 0; k < 8; ++k) e[k] = v[8 * j + k];
+                if (MODE == 0) {
+#pragma unroll
+                    for (int k = 0; k < 8; ++k) e[k] = fmaxf(e[k] + s_bias[8 * j + k], 0.f);
+                } else if (MODE == 2) {
+                    const uint4 m4 = __ldg(mk + j);
+                    const uint32_t mw[4] = {m4.x, m4.y, m4.z, m4.w};
+#pragma unroll
+                    for (int k = 0; k < 8; ++k) {
+                        const unsigned short h = (unsigned short)(mw[k >> 1] >> (16 * (k & 1)));
+                        if (!(__bfloat162float(__ushort_as_bfloat16(h)) > 0.f)) e[k] = 0.f;
+                    }
+                }
+                o[j] = make_uint4(pack2(e[0], e[1]), pack2(e[2], e[3]), pack2(e[4], e[5]), pack2(e[6], e[7]));
+            }
+        }
+    };
+    if (threadIdx.x == 0) {
+        for (int k = 0; k < 5; ++k) tc::mbar_init(&bars[k], 1);
+        if ((int)blockIdx.x < total) issue(blockIdx.x, 0);
+        if ((int)blockIdx.x + G0 < total) issue(blockIdx.x + G0, 1);
+    }
+    if (warp == 1) {
+        tc::alloc(s_tmem, G::TMEM_COLS);
+        tc::relinquish();
+    }
+    if ((int)blockIdx.x < total) load_fix(blockIdx.x);
+    // weights w[co][tap][ci] -> B rows (tap, c, co); the bias
+    for (int i = threadIdx.x; i < COUT * 9 * NC; i += G::THREADS) {
+        const int co = i / (9 * NC), r = i - co * (9 * NC);
+        *reinterpret_cast<uint4*>(sB + (r * COUT + co) * 16) = __ldg(reinterpret_cast<const uint4*>(w) + i);
+    }
+    if (MODE != 2 && threadIdx.x < COUT) s_bias[threadIdx.x] = __ldg(bias + threadIdx.x);
+    tc::fence_before();
+    __syncthreads();
+    tc::fence_after();
+    const uint32_t tmem = *s_tmem;
+    const uint64_t a_desc0 = tc::desc_noswz(tc::smem_u32(sA0), G::ABS, 128);
+    const uint64_t b_desc0 = tc::desc_noswz(tc::smem_u32(sB), COUT * 16, 128);
+    constexpr uint32_t IDESC = tc::idesc_bf16(128, COUT);
+    // on a timeout: report, give everything in flight one more bounded wait (thread 0)
+    // (MMAs of tiles i - 1 and, if issued, i; TMAs of tiles i and i + 1; the TMA of tile i + 2
+    // is issued only after both waits of iteration i have succeeded)
+    auto drain = [&](int i, int t, bool mma_i) {
+        if (threadIdx.x == 0) {
+            atomicExch(err, 1);
+            if (i >= 1) tc::mbar_wait(&bars[3 + ((i - 1) & 1)], ((i - 1) >> 1) & 1, TC_WAIT_NS);
+            if (mma_i) tc::mbar_wait(&bars[3 + (i & 1)], (i >> 1) & 1, TC_WAIT_NS);
+            tc::mbar_wait(&bars[i % 3], (i / 3) & 1, TC_WAIT_NS);
+            if (t + G0 < total) tc::mbar_wait(&bars[(i + 1) % 3], ((i + 1) / 3) & 1, TC_WAIT_NS);
+        }
+        __syncthreads();
+    };
+    int i = 0;
+    bool failed = false;
+    for (int t = blockIdx.x; t < total; t += G0, ++i) {
+        const int buf = i % 3;
+        unsigned char* sA = sA0 + buf * G::ABYTES;
+        const bool landed = tc::mbar_wait(&bars[buf], (i / 3) & 1, TC_WAIT_NS);
+        if (__syncthreads_or(!landed)) {
+            drain(i, t, false);
+            failed = true;
+            break;
+        }
+        tc_store_fix<CIN>(sA, fixv, fixp);
+        tc::fence_async_smem();
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            tc::fence_after();
+            const uint64_t a_buf = a_desc0 + (uint64_t)((buf * G::ABYTES) >> 4);
+            const uint32_t d_set = tmem + 64 * (i & 1);
+#pragma unroll 1
+            for (int mt = 0; mt < 2; ++mt) {
+#pragma unroll
+                for (int tap = 0; tap < 9; ++tap) {
+                    const int dy = tap / 3, dx = tap - 3 * dy;
+#pragma unroll
+                    for (int kk = 0; kk < NC / 2; ++kk) {
+                        // start addresses advance in 16-byte units in the descriptor's low bits
+                        const uint64_t a =
+                            a_buf + (uint64_t)(((dx * NC + 2 * kk) * G::ABS + (4 * mt + dy) * TW * 16) >> 4);
+                        const uint64_t bd = b_desc0 + (uint64_t)(((tap * NC + 2 * kk) * COUT * 16) >> 4);
+                        tc::mma_bf16(d_set + 32 * mt, a, bd, IDESC, (tap | kk) != 0);
+                    }
+                }
+            }
+            tc::commit(&bars[3 + (i & 1)]);
+        }
+        if (i >= 1) {
+            // the previous tile's MMAs: then its A buffer takes the TMA two tiles ahead and its
+            // accumulators are drained while this tile's MMAs run
+            const bool done = tc::mbar_wait(&bars[3 + ((i - 1) & 1)], ((i - 1) >> 1) & 1, TC_WAIT_NS);
+            if (__syncthreads_or(!done)) {
+                drain(i, t, true);
+                failed = true;
+                break;
+            }
+            tc::fence_after();
+        }
+        if (threadIdx.x == 0 && t + 2 * G0 < total) issue(t + 2 * G0, (i + 2) % 3);
+        if (t + G0 < total) load_fix(t + G0);
+        if (i >= 1) epilogue(t - G0, (i - 1) & 1, tmem);
+        // TMEM reads complete before the MMAs of tile i + 1 overwrite accumulator set (i + 1) & 1
+        tc::fence_before();
+        __syncthreads();
+    }
+    if (!failed && i >= 1) {
+        const int tl = blockIdx.x + (i - 1) * G0;
+        const bool done = tc::mbar_wait(&bars[3 + ((i - 1) & 1)], ((i - 1) >> 1) & 1, TC_WAIT_NS);
+        if (__syncthreads_or(!done)) {
+            if (threadIdx.x == 0) {
+                atomicExch(err, 1);
+                tc::mbar_wait(&bars[3 + ((i - 1) & 1)], ((i - 1) >> 1) & 1, TC_WAIT_NS);
+            }
+        } else {
+            tc::fence_after();
+            epilogue(tl, (i - 1) & 1, tmem);
+        }
+    }
+    tc::fence_before();
+    __syncthreads();
+    tc::fence_after();
+    if (warp == 1) tc::dealloc(tmem, G::TMEM_COLS);
+}
+
+// ---------------------------------------------------------------------------
 // weight gradient: dW[co][tap][ci] = sum_pixels dz[p][co] a[p + tap][ci], as a
 // GEMM with M = COUT, N = 9 * CIN (warp w = tap w), K = pixels; each CTA
 // accumulates a strided set of TH x TW tiles and writes its partial sums
@@ -299,6 +620,181 @@ __global__ void k_wgrad_reduce(const float* __restrict__ partial, const float* _
         for (int p = 0; p < nparts; ++p) s += bpartial[(size_t)p * nb + j];
         db[j] = s;
     }
+}
+
+// ---------------------------------------------------------------------------
+// weight gradient on the tcgen05 tensor cores (CIN = 32), operands staged by TMA:
+// D[m][co] = sum_p A[m][p] dz[p][co] with M rows m = (dx, ci) of one dy, i.e.
+// the taps (dy, 0..2) times 32 input channels, and K = the pixels of the CTA's
+// tiles.  Both operands are MN-major (16-byte rows of 8 consecutive M or N
+// elements, one row per pixel), which is the NHWC layout itself: A is the
+// forward kernel's three column-shifted halo copies (blocks (s, c), ABS bytes
+// apart, so the 16 8-row groups of an M block are blocks 0..15 at SBO = ABS,
+// and pixel rows advance by LBO = 128 per 8 pixels); the row offset dy selects
+// the tap row.  Block s = 3 (the 4th group of four) is a constant block of
+// ones, so M rows 96..127 of the dy = 0 block accumulate sum_p dz[p][co], the
+// bias gradient.  dz of a tile is COUT / 8 TMA boxes (8 channels x TW x TH)
+// at DBS = TH TW 16 bytes.  Three accumulators (dy = 0, 1, 2) of N = COUT
+// columns stay in TMEM over all of the CTA's tiles and are written once as
+// the CTA's partial sums (reduced by k_wgrad_reduce).
+// ---------------------------------------------------------------------------
+template <int COUT>
+struct TcWgrad {
+    static constexpr int CIN = 32, NC = 4;
+    static constexpr int ABS = TcConv<32, 16>::ABS;
+    static constexpr int DBS = TH * TW * 16;
+    static constexpr int ABLK = 4 * NC * ABS;                     // three shifted copies + the ones block
+    static constexpr int STAGE = ABLK + (COUT / 8) * DBS;        // one buffer: A then dz
+    static constexpr int TXBYTES = 3 * NC * ABS + (COUT / 8) * DBS;
+    static constexpr int NBUF = 2;
+    static constexpr int SMEM = 128 + NBUF * STAGE + 64;
+    static constexpr int TMEM_COLS = 128;
+    static constexpr int THREADS = 256;
+    static constexpr int NFIXK = (TcConv<32, 16>::NFIX + THREADS - 1) / THREADS;
+    static_assert(STAGE % 128 == 0 && ABS % 128 == 0, "TMA destinations 128-byte aligned");
+    // an M block reads groups 0..15 at ABS from block 0, rows up to (dy + TH) TW of each
+    static_assert(15 * ABS + (TH + 2) * TW * 16 <= ABLK, "A operand out of range");
+};
+
+template <int COUT>
+__global__ void __launch_bounds__(256) k_wgrad_tc(const __grid_constant__ CUtensorMap amap,
+                                                  const __grid_constant__ CUtensorMap dzmap,
+                                                  const bf16* __restrict__ a, float* partial, float* bpartial,
+                                                  int H, int W, int B, int dil, int* err) {
+    using G = TcWgrad<COUT>;
+    constexpr int CIN = 32, NC = 4;
+    extern __shared__ unsigned char smraw[];
+    unsigned char* s0 = smraw + ((128u - (tc::smem_u32(smraw) & 127u)) & 127u);
+    uint64_t* bars = reinterpret_cast<uint64_t*>(s0 + G::NBUF * G::STAGE);  // TMA of buffer 0, 1; MMA
+    uint32_t* s_tmem = reinterpret_cast<uint32_t*>(bars + 3);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int tiles_per_img = (H / TH) * (W / TW), total = tiles_per_img * B;
+    const int G0 = gridDim.x;
+    auto issue = [&](int t, int buf) {
+        const int b = t / tiles_per_img;
+        const TileMap tm = tile_map(t - b * tiles_per_img, H, W, dil);
+        unsigned char* st = s0 + buf * G::STAGE;
+        tc::mbar_arrive_expect_tx(&bars[buf], G::TXBYTES);
+        tc_issue_halo<CIN>(&amap, st, &bars[buf], tm, b);
+#pragma unroll
+        for (int c = 0; c < COUT / 8; ++c)
+            tc::tma_load_5d(st + G::ABLK + c * G::DBS, &dzmap, &bars[buf], 8 * c, tm.rx, tm.X0, tm.ry,
+                            b * tm.Hs + tm.Y0);
+    };
+    uint4 fixv[G::NFIXK];
+    int fixp[G::NFIXK];
+    if (threadIdx.x == 0) {
+        for (int k = 0; k < 3; ++k) tc::mbar_init(&bars[k], 1);
+        if ((int)blockIdx.x < total) issue(blockIdx.x, 0);
+        if ((int)blockIdx.x + G0 < total) issue(blockIdx.x + G0, 1);
+    }
+    if (warp == 1) {
+        tc::alloc(s_tmem, G::TMEM_COLS);
+        tc::relinquish();
+    }
+    if ((int)blockIdx.x < total) tc_load_fix<CIN>(a, blockIdx.x, tiles_per_img, H, W, dil, fixv, fixp);
+    // the ones blocks (s = 3) of both buffers: BF16 1.0 = 0x3F80
+    for (int i = threadIdx.x; i < G::NBUF * NC * G::ABS / 16; i += G::THREADS) {
+        const int buf = i / (NC * G::ABS / 16), r = i - buf * (NC * G::ABS / 16);
+        *reinterpret_cast<uint4*>(s0 + buf * G::STAGE + 3 * NC * G::ABS + r * 16) =
+            make_uint4(0x3F803F80u, 0x3F803F80u, 0x3F803F80u, 0x3F803F80u);
+    }
+    tc::fence_async_smem();
+    tc::fence_before();
+    __syncthreads();
+    tc::fence_after();
+    const uint32_t tmem = *s_tmem;
+    // MN-major operands: LBO = the step between 8-pixel groups along K, SBO = between 8-element groups along M / N
+    const uint64_t a_desc0 = tc::desc_noswz(tc::smem_u32(s0), 128, G::ABS);
+    const uint64_t d_desc0 = tc::desc_noswz(tc::smem_u32(s0 + G::ABLK), 128, G::DBS);
+    constexpr uint32_t IDESC = tc::idesc_bf16(128, COUT) | (1u << 15) | (1u << 16);
+    int i = 0;
+    bool failed = false;
+    for (int t = blockIdx.x; t < total; t += G0, ++i) {
+        const int buf = i & 1;
+        unsigned char* st = s0 + buf * G::STAGE;
+        const bool landed = tc::mbar_wait(&bars[buf], (i >> 1) & 1, TC_WAIT_NS);
+        if (__syncthreads_or(!landed)) {
+            if (threadIdx.x == 0) {
+                atomicExch(err, 1);
+                tc::mbar_wait(&bars[buf], (i >> 1) & 1, TC_WAIT_NS);
+                if (t + G0 < total) tc::mbar_wait(&bars[buf ^ 1], ((i + 1) >> 1) & 1, TC_WAIT_NS);
+            }
+            __syncthreads();
+            failed = true;
+            break;
+        }
+        tc_store_fix<CIN>(st, fixv, fixp);
+        if (t + G0 < total) tc_load_fix<CIN>(a, t + G0, tiles_per_img, H, W, dil, fixv, fixp);
+        tc::fence_async_smem();
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            tc::fence_after();
+            const uint64_t a_st = a_desc0 + (uint64_t)((buf * G::STAGE) >> 4);
+            const uint64_t d_st = d_desc0 + (uint64_t)((buf * G::STAGE) >> 4);
+#pragma unroll 1
+            for (int dy = 0; dy < 3; ++dy) {
+#pragma unroll 4
+                for (int ks = 0; ks < TH * TW / 16; ++ks) {
+                    // K slice ks: 16 pixels of tile row r = ks / 2 from column x0 = 16 (ks & 1)
+                    const int r = ks >> 1, x0 = (ks & 1) * 16;
+                    const uint64_t ad = a_st + (uint64_t)((((r + dy) * TW + x0) * 16) >> 4);
+                    const uint64_t dd = d_st + (uint64_t)(((r * TW + x0) * 16) >> 4);
+                    tc::mma_bf16(tmem + 32 * dy, ad, dd, IDESC, (i | ks) != 0);
+                }
+            }
+            tc::commit(&bars[2]);
+        }
+        const bool done = tc::mbar_wait(&bars[2], i & 1, TC_WAIT_NS);
+        if (__syncthreads_or(!done)) {
+            if (threadIdx.x == 0) {
+                atomicExch(err, 1);
+                tc::mbar_wait(&bars[2], i & 1, TC_WAIT_NS);
+                if (t + G0 < total) tc::mbar_wait(&bars[buf ^ 1], ((i + 1) >> 1) & 1, TC_WAIT_NS);
+            }
+            __syncthreads();
+            failed = true;
+            break;
+        }
+        // this buffer is free again: the TMA of the tile after next
+        if (threadIdx.x == 0 && t + 2 * G0 < total) issue(t + 2 * G0, buf);
+    }
+    if (!failed && i > 0) {
+        tc::fence_after();
+        // warp w: lane quarter q = w % 4 holds M rows 32 q + lane = (dx = q, ci = lane); warps 0-3
+        // drain the dy = 0 and dy = 2 accumulators, warps 4-7 the dy = 1 one
+        const int q = warp & 3;
+        float* P = partial + (size_t)blockIdx.x * COUT * 9 * CIN;
+        for (int dy = warp >> 2; dy < 3; dy += 2) {
+            const uint32_t taddr = tmem + ((uint32_t)(32 * q) << 16) + 32 * dy;
+            float v[COUT];
+            if constexpr (COUT == 32) {
+                uint32_t r[32];
+                tc::ld_32x32b_x32(taddr, r);
+                tc::wait_ld();
+#pragma unroll
+                for (int j = 0; j < 32; ++j) v[j] = __uint_as_float(r[j]);
+            } else {
+                uint32_t r[16];
+                tc::ld_32x32b_x16(taddr, r);
+                tc::wait_ld();
+#pragma unroll
+                for (int j = 0; j < 16; ++j) v[j] = __uint_as_float(r[j]);
+            }
+            if (q < 3) {
+                const int tap = 3 * dy + q;
+#pragma unroll
+                for (int co = 0; co < COUT; ++co) P[(co * 9 + tap) * CIN + lane] = v[co];
+            } else if (dy == 0 && lane == 0) {
+#pragma unroll
+                for (int co = 0; co < COUT; ++co) bpartial[(size_t)blockIdx.x * COUT + co] = v[co];
+            }
+        }
+    }
+    tc::fence_before();
+    __syncthreads();
+    tc::fence_after();
+    if (warp == 1) tc::dealloc(tmem, G::TMEM_COLS);
 }
 
 // images (fp32 planar [B][2][H][W]) -> NHWC bf16 with 16 channels (2 real)
@@ -427,11 +923,118 @@ struct reg_net {
     double *d_part, *h_part;
     int adam_t;
     float out_scale;           // reg_net_forward multiplies its prediction by this
+    int conv_kind;             // REG_CONV_TCGEN05 or REG_CONV_MMA_SYNC
+    int tc_grid[2][2][3];      // persistent grid of k_conv3x3_tc<CIN 16/32, COUT 16/32, MODE>
+    int tc_wgrad_grid[2];      // grid of k_wgrad_tc<COUT 16/32>
+    int* d_err;                // set by a tensor-core conv whose MMAs did not complete in time
+    int* h_err;                // pinned copy, refreshed at the end of every forward / backward
+    bool record;               // keep every layer's output gradient (reg_net_layer_tensor)
+    bf16* dz_rec[NLAYER];
 };
 
 static size_t conv_smem(int cin, int cout) {
     return (size_t)((TH + 2) * (TW + 2) * (cin + 8) + cout * (9 * cin + 8)) * sizeof(bf16);
 }
+// cuTensorMapEncodeTiled from the driver (resolved once through the runtime)
+static PFN_cuTensorMapEncodeTiled_v12000 tmap_encoder() {
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+        cudaGetLastError();
+    });
+    return fn;
+}
+
+// 5-D view (C, rx, X, ry, Y + (H/d) b) of B NHWC images with C channels: the sub-grid
+// (ry, rx) of dilation d is the 3-D box (C, X, Y) at fixed (rx, ry); boxes of 8 channels x TW x rows
+static bool halo_tensor_map(CUtensorMap* m, const bf16* act, int C, int d, int H, int W, int B, int rows = TH + 2) {
+    const PFN_cuTensorMapEncodeTiled_v12000 enc = tmap_encoder();
+    if (!enc) return false;
+    const cuuint64_t e = sizeof(bf16);
+    cuuint64_t dims[5] = {(cuuint64_t)C, (cuuint64_t)d, (cuuint64_t)(W / d), (cuuint64_t)d, (cuuint64_t)(H / d) * B};
+    cuuint64_t strides[4] = {C * e, (cuuint64_t)d * C * e, (cuuint64_t)W * C * e, (cuuint64_t)d * W * C * e};
+    cuuint32_t box[5] = {8, 1, TW, 1, (cuuint32_t)rows};
+    cuuint32_t estr[5] = {1, 1, 1, 1, 1};
+    return enc(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 5, const_cast<bf16*>(act), dims, strides, box, estr,
+               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+template <int CIN, int COUT, int MODE>
+static bool conv_launch(reg_net* n, const bf16* in, const bf16* w, const float* bias, void* out, const bf16* mask,
+                        int B, int d) {
+    const int tiles = (n->H / TH) * (n->W / TW);
+    if (n->conv_kind == REG_CONV_TCGEN05) {
+        CUtensorMap map;
+        if (!halo_tensor_map(&map, in, CIN, d, n->H, n->W, B)) return false;
+        const int total = tiles * B;
+        int grid = n->tc_grid[CIN == 32][COUT == 32][MODE];
+        if (grid > total) grid = total;
+        k_conv3x3_tc<CIN, COUT, MODE><<<grid, TcConv<CIN, COUT>::THREADS, TcConv<CIN, COUT>::SMEM, n->stream>>>(
+            map, in, w, bias, out, mask, n->H, n->W, d, tiles, B, n->d_err);
+    } else {
+        k_conv3x3<CIN, COUT, MODE><<<dim3(tiles, B), 256, conv_smem(CIN, COUT), n->stream>>>(in, w, bias, out, mask,
+                                                                                           n->H, n->W, d);
+    }
+    return true;
+}
+
+// weight and bias gradient partials of a CIN = 32 layer on the tensor cores; returns the
+// number of partials (CTAs), 0 if the tensor maps could not be encoded
+template <int COUT>
+static int wgrad_tc_launch(reg_net* n, const bf16* a, const bf16* dz, int B, int d) {
+    CUtensorMap am, dm;
+    if (!halo_tensor_map(&am, a, 32, d, n->H, n->W, B) || !halo_tensor_map(&dm, dz, COUT, d, n->H, n->W, B, TH))
+        return 0;
+    const int total = (n->H / TH) * (n->W / TW) * B;
+    const int grid = std::min(total, n->tc_wgrad_grid[COUT == 32]);
+    k_wgrad_tc<COUT><<<grid, TcWgrad<COUT>::THREADS, TcWgrad<COUT>::SMEM, n->stream>>>(
+        am, dm, a, n->partial, n->bpartial, n->H, n->W, B, d, n->d_err);
+    return grid;
+}
+
+template <int COUT>
+static int tc_wgrad_prepare(reg_net* n, int dev) {
+    using G = TcWgrad<COUT>;
+    auto k = k_wgrad_tc<COUT>;
+    if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, G::SMEM) != cudaSuccess) return 0;
+    cudaDeviceProp pr;
+    if (cudaGetDeviceProperties(&pr, dev) != cudaSuccess) return 0;
+    // one CTA per SM (the shared memory of two stages); never more CTAs than partial slots
+    n->tc_wgrad_grid[COUT == 32] = std::min(pr.multiProcessorCount, n->nwg);
+    return 1;
+}
+
+// resident CTAs per SM of k_conv3x3_tc<CIN, COUT, MODE> from its registers and shared memory
+// and the device limits (at most 512 / TMEM_COLS, the TMEM columns of an SM)
+template <int CIN, int COUT, int MODE>
+static int tc_prepare(reg_net* n, int dev) {
+    using G = TcConv<CIN, COUT>;
+    auto k = k_conv3x3_tc<CIN, COUT, MODE>;
+    if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, G::SMEM) != cudaSuccess ||
+        cudaFuncSetAttribute(k, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared) !=
+            cudaSuccess)
+        return 0;
+    cudaFuncAttributes fa;
+    cudaDeviceProp pr;
+    if (cudaFuncGetAttributes(&fa, k) != cudaSuccess || cudaGetDeviceProperties(&pr, dev) != cudaSuccess) return 0;
+    const int warps = G::THREADS / 32;
+    const int regs_warp = ((fa.numRegs * 32 + 255) / 256) * 256;
+    int occ = pr.regsPerMultiprocessor / (regs_warp * warps);
+    occ = std::min(occ, (int)(pr.sharedMemPerMultiprocessor / (G::SMEM + fa.sharedSizeBytes + pr.reservedSharedMemPerBlock)));
+    occ = std::min(occ, pr.maxThreadsPerMultiProcessor / G::THREADS);
+    occ = std::min(occ, 512 / G::TMEM_COLS);
+    if (occ < 1) return 0;
+    n->tc_grid[CIN == 32][COUT == 32][MODE] = occ * pr.multiProcessorCount;
+    return occ;
+}
+
 static size_t wgrad_smem(int cin, int cout) {
     return (size_t)(cout * (TH * TW + 8) + cin * ((TH + 2) * (TW + 2) + 8)) * sizeof(bf16);
 }
@@ -446,10 +1049,14 @@ extern "C" void reg_net_destroy(reg_net* n) {
     if (n->proj) reg_destroy(n->proj);
     void* ptrs[] = {n->d_layers, n->params, n->m1, n->m2, n->gW, n->gb, n->d_gwoff, n->d_gboff, n->d_wfoff,
                     n->wf, n->wt, n->bpad, n->dzA, n->dzB, n->out, n->pred, n->res, n->dout, n->partial,
-                    n->bpartial, n->d_part};
+                    n->bpartial, n->d_part, n->d_err};
     for (void* p : ptrs) cudaFree(p);
-    for (int l = 0; l < NLAYER; ++l) cudaFree(n->act[l]);
+    for (int l = 0; l < NLAYER; ++l) {
+        cudaFree(n->act[l]);
+        cudaFree(n->dz_rec[l]);
+    }
     cudaFreeHost(n->h_part);
+    cudaFreeHost(n->h_err);
     delete n;
 }
 
@@ -502,7 +1109,9 @@ extern "C" int reg_net_create(int H, int W, int max_batch, reg_net** out) {
     M((void**)&n->partial, sizeof(float) * n->nwg * 32 * 9 * 32);
     M((void**)&n->bpartial, sizeof(float) * n->nwg * 32);
     M((void**)&n->d_part, sizeof(double) * 1024);
+    M((void**)&n->d_err, sizeof(int));
     if (ok && cudaMallocHost((void**)&n->h_part, sizeof(double) * 1024) != cudaSuccess) ok = false;
+    if (ok && cudaMallocHost((void**)&n->h_err, sizeof(int)) != cudaSuccess) ok = false;
     if (!ok) {
         cudaGetLastError();
         reg_net_destroy(n);
@@ -527,7 +1136,16 @@ extern "C" int reg_net_create(int H, int W, int max_batch, reg_net** out) {
     opt_in(k_wgrad<16, 32>, wgrad_smem(16, 32));
     opt_in(k_wgrad<32, 32>, wgrad_smem(32, 32));
     opt_in(k_wgrad<32, 16>, wgrad_smem(32, 16));
-    if (cudaDeviceSynchronize() != cudaSuccess) {
+    cudaMemset(n->d_err, 0, sizeof(int));
+    *n->h_err = 0;
+    n->conv_kind = REG_CONV_TCGEN05;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    const bool tc_ok = tc_prepare<16, 32, 0>(n, dev) && tc_prepare<32, 32, 0>(n, dev) &&
+                       tc_prepare<32, 16, 1>(n, dev) && tc_prepare<16, 32, 2>(n, dev) &&
+                       tc_prepare<32, 32, 2>(n, dev) && tc_wgrad_prepare<16>(n, dev) &&
+                       tc_wgrad_prepare<32>(n, dev) && tmap_encoder() != nullptr;
+    if (!tc_ok || cudaDeviceSynchronize() != cudaSuccess) {
         reg_net_destroy(n);
         return reg_fail(REG_ERR_CUDA, "network initialisation failed");
     }
@@ -583,21 +1201,31 @@ static int leray_batch(reg_net* n, const float* in, float* out, int B) {
     return REG_OK;
 }
 
+// a tensor-core conv of an earlier call that reported an MMA timeout (sticky; read from
+// the pinned copy, refreshed at the end of every forward pass)
+static int conv_status(reg_net* n) {
+    return *n->h_err ? reg_fail(REG_ERR_TIMEOUT, "tensor-core convolution: MMA completion timed out") : REG_OK;
+}
+
 static int net_forward(reg_net* n, const float* images, int B) {
     const int H = n->H, W = n->W;
+    int st = conv_status(n);
+    if (st != REG_OK) return st;
     k_pack_input<<<304, 256, 0, n->stream>>>(images, n->act[0], B, H, W);
-    const dim3 grid((H / TH) * (W / TW), B);
     for (int l = 0; l < NLAYER; ++l) {
         const float* bias = n->bpad + 32 * l;
         const bf16* wl = n->wf + n->wfoff[l];
         const int d = layer_dil(l, H, W);
+        bool ok;
         if (l == 0)
-            k_conv3x3<16, 32, 0><<<grid, 256, conv_smem(16, 32), n->stream>>>(n->act[0], wl, bias, n->act[1], nullptr, H, W, d);
+            ok = conv_launch<16, 32, 0>(n, n->act[0], wl, bias, n->act[1], nullptr, B, d);
         else if (l < NLAYER - 1)
-            k_conv3x3<32, 32, 0><<<grid, 256, conv_smem(32, 32), n->stream>>>(n->act[l], wl, bias, n->act[l + 1], nullptr, H, W, d);
+            ok = conv_launch<32, 32, 0>(n, n->act[l], wl, bias, n->act[l + 1], nullptr, B, d);
         else
-            k_conv3x3<32, 16, 1><<<grid, 256, conv_smem(32, 16), n->stream>>>(n->act[l], wl, bias, n->out, nullptr, H, W, d);
+            ok = conv_launch<32, 16, 1>(n, n->act[l], wl, bias, n->out, nullptr, B, d);
+        if (!ok) return reg_fail(REG_ERR_CUDA, "net forward: tensor map encoding failed");
     }
+    cudaMemcpyAsync(n->h_err, n->d_err, sizeof(int), cudaMemcpyDeviceToHost, n->stream);
     const cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return reg_fail(REG_ERR_CUDA, std::string("net forward: ") + cudaGetErrorString(e));
     return leray_batch(n, n->out, n->pred, B);
@@ -637,7 +1265,6 @@ static int net_loss_grad(reg_net* n, const float* images, const float* targets, 
     st = leray_batch(n, n->res, n->dout, B);  // dL/d out = G P r / M (scaled below)
     if (st != REG_OK) return st;
     k_pack_grad<<<304, 256, 0, n->stream>>>(n->dout, n->dzA, B, H, W);
-    const dim3 grid((H / TH) * (W / TW), B);
     const float invM = 1.0f / (float)M;
     bf16* dz = n->dzA;
     bf16* dnext = n->dzB;
@@ -646,21 +1273,29 @@ static int net_loss_grad(reg_net* n, const float* images, const float* targets, 
         float* gWl = n->gW + n->gwoff[l];
         float* gbl = n->gb + n->gboff[l];
         const int d = layer_dil(l, H, W);
-        if (l == NLAYER - 1)
+        if (n->record)
+            cudaMemcpyAsync(n->dz_rec[l], dz, sizeof(bf16) * (size_t)B * H * W * L.coutp, cudaMemcpyDeviceToDevice,
+                            n->stream);
+        int nparts = n->nwg;
+        if (l > 0 && n->conv_kind == REG_CONV_TCGEN05) {
+            nparts = l == NLAYER - 1 ? wgrad_tc_launch<16>(n, n->act[l], dz, B, d) : wgrad_tc_launch<32>(n, n->act[l], dz, B, d);
+            if (nparts == 0) return reg_fail(REG_ERR_CUDA, "net backward: tensor map encoding failed");
+        } else if (l == NLAYER - 1) {
             k_wgrad<32, 16><<<n->nwg, 288, wgrad_smem(32, 16), n->stream>>>(n->act[l], dz, n->partial, n->bpartial, H, W, B, d);
-        else if (l > 0)
+        } else if (l > 0) {
             k_wgrad<32, 32><<<n->nwg, 288, wgrad_smem(32, 32), n->stream>>>(n->act[l], dz, n->partial, n->bpartial, H, W, B, d);
-        else
+        } else {
+            // layer 0 (2 real input channels padded to 16) keeps the mma.sync kernel on either path
             k_wgrad<16, 32><<<n->nwg, 288, wgrad_smem(16, 32), n->stream>>>(n->act[0], dz, n->partial, n->bpartial, H, W, B, d);
+        }
         const int nw = L.coutp * 9 * L.cinp, nb = L.coutp;
-        k_wgrad_reduce<<<(nw + nb + 255) / 256, 256, 0, n->stream>>>(n->partial, n->bpartial, n->nwg, nw, nb, gWl, gbl);
+        k_wgrad_reduce<<<(nw + nb + 255) / 256, 256, 0, n->stream>>>(n->partial, n->bpartial, nparts, nw, nb, gWl, gbl);
         if (l > 0) {
             // input gradient through the ReLU of layer l-1: correlation with the flipped, transposed kernel
             const bf16* wtl = n->wt + n->wfoff[l];
-            if (l == NLAYER - 1)
-                k_conv3x3<16, 32, 2><<<grid, 256, conv_smem(16, 32), n->stream>>>(dz, wtl, nullptr, dnext, n->act[l], H, W, d);
-            else
-                k_conv3x3<32, 32, 2><<<grid, 256, conv_smem(32, 32), n->stream>>>(dz, wtl, nullptr, dnext, n->act[l], H, W, d);
+            const bool ok = l == NLAYER - 1 ? conv_launch<16, 32, 2>(n, dz, wtl, nullptr, dnext, n->act[l], B, d)
+                                            : conv_launch<32, 32, 2>(n, dz, wtl, nullptr, dnext, n->act[l], B, d);
+            if (!ok) return reg_fail(REG_ERR_CUDA, "net backward: tensor map encoding failed");
             bf16* tmp = dz; dz = dnext; dnext = tmp;
         }
     }
@@ -672,8 +1307,11 @@ static int net_loss_grad(reg_net* n, const float* images, const float* targets, 
     // scale gradients in place
     launch_axpby(n->proj, ngw, invM, n->gW, 0.f, n->gW, -1, -1, n->gW);
     launch_axpby(n->proj, ngb, invM, n->gb, 0.f, n->gb, -1, -1, n->gb);
+    cudaMemcpyAsync(n->h_err, n->d_err, sizeof(int), cudaMemcpyDeviceToHost, n->stream);
     e = cudaStreamSynchronize(n->stream);
     if (e != cudaSuccess) return reg_fail(REG_ERR_CUDA, std::string("net backward: ") + cudaGetErrorString(e));
+    st = conv_status(n);
+    if (st != REG_OK) return st;
     double s = 0.0;
     for (int i = 0; i < 256; ++i) s += n->h_part[i];
     if (loss) *loss = 0.5 * s / (double)M;
@@ -715,6 +1353,67 @@ extern "C" int reg_net_train_step(reg_net* n, const float* images, const float* 
     const int st = net_loss_grad(n, images, targets, B, loss);
     if (st != REG_OK) return st;
     repack(n, 1, lr);
+    const cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? REG_OK : reg_fail(REG_ERR_CUDA, cudaGetErrorString(e));
+}
+
+extern "C" int reg_net_set_conv_kernel(reg_net* n, int kind) {
+    if (!n) return reg_fail(REG_ERR_ARG, "net is NULL");
+    if (kind != REG_CONV_TCGEN05 && kind != REG_CONV_MMA_SYNC) return reg_fail(REG_ERR_ARG, "unknown conv kernel");
+    n->conv_kind = kind;
+    return REG_OK;
+}
+
+extern "C" int reg_net_set_record(reg_net* n, int on) {
+    if (!n) return reg_fail(REG_ERR_ARG, "net is NULL");
+    if (on && !n->record) {
+        const size_t pix = (size_t)n->maxB * n->H * n->W;
+        for (int l = 0; l < NLAYER; ++l)
+            if (!n->dz_rec[l] && cudaMalloc((void**)&n->dz_rec[l], sizeof(bf16) * pix * n->layers[l].coutp) != cudaSuccess) {
+                cudaGetLastError();
+                return reg_fail(REG_ERR_NOMEM, "record buffers");
+            }
+    }
+    n->record = on != 0;
+    return REG_OK;
+}
+
+namespace {
+// NHWC BF16 with cs channels per pixel -> planar FP32 [B][c][H][W], first c channels
+__global__ void k_unpack_nhwc(const bf16* __restrict__ a, float* __restrict__ out, int cs, int c, long long npix,
+                              long long plane) {
+    const long long total = npix * c;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total; i += (long long)gridDim.x * blockDim.x) {
+        const long long p = i / c;
+        const int ch = (int)(i - p * c);
+        const long long b = p / plane, r = p - b * plane;
+        out[(b * c + ch) * plane + r] = __bfloat162float(a[p * cs + ch]);
+    }
+}
+}  // namespace
+
+extern "C" int reg_net_layer_tensor(reg_net* n, int kind, int layer, int B, float* out) {
+    if (!n || !out) return reg_fail(REG_ERR_ARG, "net or out is NULL");
+    if (layer < 0 || layer >= NLAYER || B < 1 || B > n->maxB) return reg_fail(REG_ERR_ARG, "layer or batch out of range");
+    const LayerDesc& L = n->layers[layer];
+    const long long plane = (long long)n->H * n->W, npix = plane * B;
+    const bf16* src = nullptr;
+    int cs = 0, c = 0;
+    if (kind == REG_NET_INPUT) {
+        src = n->act[layer]; cs = L.cinp; c = L.cin;
+    } else if (kind == REG_NET_OUTPUT) {
+        if (layer == NLAYER - 1) {
+            const cudaError_t e = cudaMemcpyAsync(out, n->out, sizeof(float) * 2 * npix, cudaMemcpyDeviceToDevice, n->stream);
+            return e == cudaSuccess ? REG_OK : reg_fail(REG_ERR_CUDA, cudaGetErrorString(e));
+        }
+        src = n->act[layer + 1]; cs = L.coutp; c = L.cout;
+    } else if (kind == REG_NET_OUTPUT_GRAD) {
+        if (!n->record) return reg_fail(REG_ERR_ARG, "output gradients are kept only after reg_net_set_record(net, 1)");
+        src = n->dz_rec[layer]; cs = L.coutp; c = L.cout;
+    } else {
+        return reg_fail(REG_ERR_ARG, "unknown tensor kind");
+    }
+    k_unpack_nhwc<<<304, 256, 0, n->stream>>>(src, out, cs, c, npix, plane);
     const cudaError_t e = cudaGetLastError();
     return e == cudaSuccess ? REG_OK : reg_fail(REG_ERR_CUDA, cudaGetErrorString(e));
 }
