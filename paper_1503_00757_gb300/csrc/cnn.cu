@@ -231,24 +231,48 @@ __global__ void __launch_bounds__(256) k_conv3x3(const bf16* __restrict__ in, co
 // pieces into registers and drain tile i - 1's accumulators (epilogue), so
 // TMA, tensor cores and epilogue overlap.
 // ---------------------------------------------------------------------------
+// A-buffer layouts of a staged halo tile (three column-shifted copies s, halo rows hr,
+// columns x, channel chunks c of 8):
+//   SW = false: blocks (s, c) of (TH + 2) TW 16-byte rows, ABS bytes apart (canonical layout
+//     without swizzle; also the MN-major layout of the weight gradient);
+//   SW = true (CIN = 32): copies of (TH + 2) TW 64-byte rows (a whole pixel), 16-byte chunks
+//     permuted by the 64-byte swizzle (chunk c of row r at chunk c ^ ((r >> 1) & 3)), the
+//     layout a TMA box with the 64-byte swizzle writes: one box per copy instead of NC.
+template <int CIN, bool SW>
+struct HaloLayout {
+    static constexpr int NC = CIN / 8;
+    static constexpr int ABS = (TH + 2) * TW * 16;        // one block (SW = false)
+    static constexpr int CPY = NC * ABS;                  // one shifted copy
+    static constexpr int ABYTES = 3 * CPY;
+    static_assert(!SW || CIN == 32, "64-byte rows hold 32 channels");
+    __device__ __forceinline__ static int off(int s, int c, int hr, int x) {
+        const int row = hr * TW + x;
+        if constexpr (SW) return s * CPY + row * 64 + ((c ^ ((row >> 1) & 3)) << 4);
+        else return (s * NC + c) * ABS + row * 16;
+    }
+};
+
 template <int CIN, int COUT>
 struct TcConv {
     static constexpr int NC = CIN / 8;
-    static constexpr int ABS = (TH + 2) * TW * 16;                 // one TMA box
+    static constexpr bool SW = CIN == 32;
+    using L = HaloLayout<CIN, SW>;
+    static constexpr int ABS = L::ABS;
+    static constexpr int CPY = L::CPY;
+    static constexpr int ALIGN = SW ? 1024 : 128;                  // swizzle atoms / TMA destinations
     static constexpr int BBYTES = 9 * NC * COUT * 16;
-    static constexpr int ABYTES = 3 * NC * ABS;                    // one A buffer
+    static constexpr int ABYTES = L::ABYTES;                       // one A buffer
     static constexpr int NBUF = 3;                                 // A buffers (TMA two tiles ahead)
-    static constexpr int SMEM = 128 + BBYTES + NBUF * ABYTES + 64 + COUT * 4;
+    static constexpr int SMEM = ALIGN + BBYTES + NBUF * ABYTES + 96 + COUT * 4;
     static constexpr int TMEM_COLS = 128;                          // two accumulator sets of 2 x 32 columns
-    static constexpr int THREADS = 256;
+    static constexpr int THREADS = 288;                            // 8 worker warps + 1 control warp
     // wrap-around pieces of a tile: halo rows 0 and TH + 1 (TW + 2 columns each), then halo
     // columns 0 and TW + 1 (all TH + 2 rows: a corner is wrong whenever its row or its
     // column lies outside the sub-grid), each NC 16-byte chunks
     static constexpr int NROWP = 2 * (TW + 2) * NC;
     static constexpr int NFIX = NROWP + 2 * (TH + 2) * NC;
-    static constexpr int NFIXK = (NFIX + THREADS - 1) / THREADS;   // per thread
-    static_assert(ABS % 128 == 0 && BBYTES % 128 == 0, "TMA destinations 128-byte aligned");
-    static_assert((3 * NC - 1) * ABS + (TH + 2) * TW * 16 <= ABYTES, "A operand out of range");
+    static constexpr int NFIXK = (NFIX + 255) / 256;              // per worker thread (256 workers)
+    static_assert(CPY % ALIGN == 0 && BBYTES % ALIGN == 0 && ABS % 128 == 0, "aligned TMA destinations");
     static_assert(TW == 32 && TH == 8, "two M = 128 blocks of four 32-pixel rows");
     static_assert(COUT == 16 || COUT == 32, "N = 16 or 32");
 };
@@ -284,22 +308,28 @@ __device__ __forceinline__ int tc_fix_piece(const bf16* __restrict__ in, const T
     return hr | (hx << 8) | (c << 16);
 }
 
-// TMA of a tile's halo into an A buffer: one box per shifted copy s and channel chunk c
-// (completion on *bar, whose expected byte count the caller has raised)
-template <int CIN>
+// TMA of a tile's halo into an A buffer (completion on *bar, whose expected byte count the
+// caller has raised): one box per shifted copy s and channel chunk c, or with the 64-byte
+// swizzle one box of all 32 channels per copy
+template <int CIN, bool SW>
 __device__ __forceinline__ void tc_issue_halo(const CUtensorMap* map, unsigned char* dst, uint64_t* bar,
                                               const TileMap& tm, int b) {
-    constexpr int NC = CIN / 8;
-    constexpr int ABS = TcConv<CIN, 16>::ABS;
+    using L = HaloLayout<CIN, SW>;
 #pragma unroll
-    for (int s = 0; s < 3; ++s)
+    for (int s = 0; s < 3; ++s) {
+        if constexpr (SW) {
+            tc::tma_load_5d(dst + s * L::CPY, map, bar, 0, tm.rx, tm.X0 - 1 + s, tm.ry, b * tm.Hs + tm.Y0 - 1);
+        } else {
 #pragma unroll
-        for (int c = 0; c < NC; ++c)
-            tc::tma_load_5d(dst + (s * NC + c) * ABS, map, bar, 8 * c, tm.rx, tm.X0 - 1 + s, tm.ry,
-                            b * tm.Hs + tm.Y0 - 1);
+            for (int c = 0; c < L::NC; ++c)
+                tc::tma_load_5d(dst + (s * L::NC + c) * L::ABS, map, bar, 8 * c, tm.rx, tm.X0 - 1 + s, tm.ry,
+                                b * tm.Hs + tm.Y0 - 1);
+        }
+    }
 }
 
-// this thread's wrap-around pieces of tile t (none for an interior tile)
+// this thread's wrap-around pieces of tile t (none for an interior tile); pieces are dealt to
+// the 256 threads 0..255 round-robin
 template <int CIN, int K>
 __device__ __forceinline__ void tc_load_fix(const bf16* __restrict__ in, int t, int tiles_per_img, int H, int W,
                                             int dil, uint4 (&fixv)[K], int (&fixp)[K]) {
@@ -309,16 +339,15 @@ __device__ __forceinline__ void tc_load_fix(const bf16* __restrict__ in, int t, 
     const bool edge = tm.Y0 == 0 || tm.Y0 + TH == tm.Hs || tm.X0 == 0 || tm.X0 + TW == tm.Ws;
 #pragma unroll
     for (int k = 0; k < K; ++k) {
-        const int j = threadIdx.x + (int)blockDim.x * k;
+        const int j = threadIdx.x + 256 * k;
         fixp[k] = (edge && j < NFIX) ? tc_fix_piece<CIN>(in, tm, b, H, W, j, fixv[k]) : -1;
     }
 }
 
 // the pieces into every shifted copy that holds them
-template <int CIN, int K>
+template <int CIN, bool SW, int K>
 __device__ __forceinline__ void tc_store_fix(unsigned char* sA, const uint4 (&fixv)[K], const int (&fixp)[K]) {
-    constexpr int NC = CIN / 8;
-    constexpr int ABS = TcConv<CIN, 16>::ABS;
+    using L = HaloLayout<CIN, SW>;
 #pragma unroll
     for (int k = 0; k < K; ++k) {
         if (fixp[k] < 0) continue;
@@ -326,195 +355,235 @@ __device__ __forceinline__ void tc_store_fix(unsigned char* sA, const uint4 (&fi
 #pragma unroll
         for (int s = 0; s < 3; ++s) {
             const int x = hx - s;
-            if (x >= 0 && x < TW) *reinterpret_cast<uint4*>(sA + (s * NC + c) * ABS + (hr * TW + x) * 16) = fixv[k];
+            if (x >= 0 && x < TW) *reinterpret_cast<uint4*>(sA + L::off(s, c, hr, x)) = fixv[k];
         }
     }
 }
 
+// bounded mbarrier wait shared by the warp-specialized kernels: false (and the CTA's abort
+// flag and the error word set) once TC_WAIT_NS has passed or another thread has aborted
+__device__ __forceinline__ bool tc_wait(uint64_t* bar, uint32_t parity, volatile int* abort, int* err) {
+    if (tc::mbar_try_wait(bar, parity)) return true;
+    const uint64_t t0 = tc::globaltimer();
+    while (!tc::mbar_try_wait(bar, parity)) {
+        if (*abort) return false;
+        if (tc::globaltimer() - t0 > TC_WAIT_NS) {
+            *abort = 1;
+            atomicExch(err, 1);
+            return false;
+        }
+    }
+    return true;
+}
+
+// Warp roles: warps 0-7 (workers) patch the wrap-around pieces of each staged tile and drain
+// the accumulators (warp w reads TMEM lanes 32 (w % 4).. of M block w / 4); warp 8 (control,
+// one lane) issues the TMA loads and the MMAs.  Hand-offs, per tile i of the CTA (buffer
+// i % 3, accumulator set i % 2), all through mbarriers:
+//   full[b]    TMA bytes landed (expect-tx)         control -> workers
+//   fixed[b]   pieces patched (8 warp arrivals)     workers -> control
+//   done[s]    MMAs of the set completed (commit)   control -> workers, and buffer b reusable
+//   drained[s] accumulators read (8 warp arrivals)  workers -> control
 template <int CIN, int COUT, int MODE>
-__global__ void __launch_bounds__(256) k_conv3x3_tc(const __grid_constant__ CUtensorMap tmap,
+__global__ void __launch_bounds__(288) k_conv3x3_tc(const __grid_constant__ CUtensorMap tmap,
                                                     const bf16* __restrict__ in, const bf16* __restrict__ w,
                                                     const float* __restrict__ bias, void* out,
                                                     const bf16* __restrict__ mask, int H, int W, int dil,
                                                     int tiles_per_img, int B, int* err) {
     using G = TcConv<CIN, COUT>;
     constexpr int NC = G::NC;
+    constexpr bool SW = G::SW;
     extern __shared__ unsigned char smraw[];
-    unsigned char* sB = smraw + ((128u - (tc::smem_u32(smraw) & 127u)) & 127u);
+    unsigned char* sB = smraw + ((G::ALIGN - (tc::smem_u32(smraw) & (G::ALIGN - 1))) & (G::ALIGN - 1));
     unsigned char* sA0 = sB + G::BBYTES;
-    uint64_t* bars = reinterpret_cast<uint64_t*>(sA0 + G::NBUF * G::ABYTES);  // TMA of buffer 0..2; MMA set 0, 1
-    uint32_t* s_tmem = reinterpret_cast<uint32_t*>(bars + 5);
-    float* s_bias = reinterpret_cast<float*>(bars + 8);
+    uint64_t* full = reinterpret_cast<uint64_t*>(sA0 + G::NBUF * G::ABYTES);
+    uint64_t* fixed = full + 3;
+    uint64_t* done = full + 6;
+    uint64_t* drained = full + 8;
+    uint32_t* s_tmem = reinterpret_cast<uint32_t*>(full + 10);
+    volatile int* abort = reinterpret_cast<volatile int*>(full + 10) + 1;
+    float* s_bias = reinterpret_cast<float*>(full + 12);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int total = tiles_per_img * B;
     const int G0 = gridDim.x;
     auto issue = [&](int t, int buf) {
         const int b = t / tiles_per_img;
         const TileMap tm = tile_map(t - b * tiles_per_img, H, W, dil);
-        tc::mbar_arrive_expect_tx(&bars[buf], G::ABYTES);
-        tc_issue_halo<CIN>(&tmap, sA0 + buf * G::ABYTES, &bars[buf], tm, b);
-    };
-    uint4 fixv[G::NFIXK];
-    int fixp[G::NFIXK];
-    auto load_fix = [&](int t) { tc_load_fix<CIN>(in, t, tiles_per_img, H, W, dil, fixv, fixp); };
-    // epilogue of tile t from accumulator set `set`: warp w reads TMEM lanes 32 (w % 4).. of
-    // M block w / 4, i.e. tile row 4 (w / 4) + w % 4, one pixel per thread
-    auto epilogue = [&](int t, int set, uint32_t tmem) {
-        const int b = t / tiles_per_img;
-        const TileMap tm = tile_map(t - b * tiles_per_img, H, W, dil);
-        const int q = warp & 3, mt = warp >> 2;
-        const uint32_t taddr = tmem + ((uint32_t)(32 * q) << 16) + 64 * set + 32 * mt;
-        float v[COUT];
-        if constexpr (COUT == 32) {
-            uint32_t r[32];
-            tc::ld_32x32b_x32(taddr, r);
-            tc::wait_ld();
-#pragma unroll
-            for (int j = 0; j < 32; ++j) v[j] = __uint_as_float(r[j]);
-        } else {
-            uint32_t r[16];
-            tc::ld_32x32b_x16(taddr, r);
-            tc::wait_ld();
-#pragma unroll
-            for (int j = 0; j < 16; ++j) v[j] = __uint_as_float(r[j]);
-        }
-        const int y = tm.gy(tm.Y0 + 4 * mt + q), x = tm.gx(tm.X0 + lane);
-        const size_t pix = ((size_t)b * H + y) * W + x;
-        if (MODE == 1) {
-            float* o = reinterpret_cast<float*>(out);
-            const size_t plane = (size_t)H * W;
-            o[((size_t)b * 2 + 0) * plane + (size_t)y * W + x] = v[0] + s_bias[0];
-            o[((size_t)b * 2 + 1) * plane + (size_t)y * W + x] = v[1] + s_bias[1];
-        } else {
-            uint4* o = reinterpret_cast<uint4*>(reinterpret_cast<bf16*>(out) + pix * COUT);
-            const uint4* mk = MODE == 2 ? reinterpret_cast<const uint4*>(mask + pix * COUT) : nullptr;
-#pragma unroll
-            for (int j = 0; j < COUT / 8; ++j) {
-                float e[8];
-#pragma unroll
-                for (int k = 0; k < 8; ++k) e[k] = v[8 * j + k];
-                if (MODE == 0) {
-#pragma unroll
-                    for (int k = 0; k < 8; ++k) e[k] = fmaxf(e[k] + s_bias[8 * j + k], 0.f);
-                } else if (MODE == 2) {
-                    const uint4 m4 = __ldg(mk + j);
-                    const uint32_t mw[4] = {m4.x, m4.y, m4.z, m4.w};
-#pragma unroll
-                    for (int k = 0; k < 8; ++k) {
-                        const unsigned short h = (unsigned short)(mw[k >> 1] >> (16 * (k & 1)));
-                        if (!(__bfloat162float(__ushort_as_bfloat16(h)) > 0.f)) e[k] = 0.f;
-                    }
-                }
-                o[j] = make_uint4(pack2(e[0], e[1]), pack2(e[2], e[3]), pack2(e[4], e[5]), pack2(e[6], e[7]));
-            }
-        }
+        tc::mbar_arrive_expect_tx(&full[buf], G::ABYTES);
+        tc_issue_halo<CIN, SW>(&tmap, sA0 + buf * G::ABYTES, &full[buf], tm, b);
     };
     if (threadIdx.x == 0) {
-        for (int k = 0; k < 5; ++k) tc::mbar_init(&bars[k], 1);
-        if ((int)blockIdx.x < total) issue(blockIdx.x, 0);
-        if ((int)blockIdx.x + G0 < total) issue(blockIdx.x + G0, 1);
+        for (int k = 0; k < 3; ++k) {
+            tc::mbar_init(&full[k], 1);
+            tc::mbar_init(&fixed[k], 8);
+        }
+        for (int k = 0; k < 2; ++k) {
+            tc::mbar_init(&done[k], 1);
+            tc::mbar_init(&drained[k], 8);
+        }
+        *abort = 0;
     }
-    if (warp == 1) {
+    if (warp == 8) {
         tc::alloc(s_tmem, G::TMEM_COLS);
         tc::relinquish();
     }
-    if ((int)blockIdx.x < total) load_fix(blockIdx.x);
-    // weights w[co][tap][ci] -> B rows (tap, c, co); the bias
-    for (int i = threadIdx.x; i < COUT * 9 * NC; i += G::THREADS) {
+    // weights w[co][tap][ci] -> B: rows (tap, c, co) of 16 bytes, or with the swizzle rows
+    // (tap, co) of 64 bytes (chunk c at c ^ ((row >> 1) & 3)); the bias
+    for (int i = threadIdx.x; i < COUT * 9 * NC; i += blockDim.x) {
         const int co = i / (9 * NC), r = i - co * (9 * NC);
-        *reinterpret_cast<uint4*>(sB + (r * COUT + co) * 16) = __ldg(reinterpret_cast<const uint4*>(w) + i);
+        const uint4 v = __ldg(reinterpret_cast<const uint4*>(w) + i);
+        if constexpr (SW) {
+            const int tap = r / NC, c = r - tap * NC, row = tap * COUT + co;
+            *reinterpret_cast<uint4*>(sB + row * 64 + ((c ^ ((row >> 1) & 3)) << 4)) = v;
+        } else {
+            *reinterpret_cast<uint4*>(sB + (r * COUT + co) * 16) = v;
+        }
     }
     if (MODE != 2 && threadIdx.x < COUT) s_bias[threadIdx.x] = __ldg(bias + threadIdx.x);
+    tc::fence_async_smem();
     tc::fence_before();
     __syncthreads();
     tc::fence_after();
     const uint32_t tmem = *s_tmem;
-    const uint64_t a_desc0 = tc::desc_noswz(tc::smem_u32(sA0), G::ABS, 128);
-    const uint64_t b_desc0 = tc::desc_noswz(tc::smem_u32(sB), COUT * 16, 128);
-    constexpr uint32_t IDESC = tc::idesc_bf16(128, COUT);
-    // on a timeout: report, give everything in flight one more bounded wait (thread 0)
-    // (MMAs of tiles i - 1 and, if issued, i; TMAs of tiles i and i + 1; the TMA of tile i + 2
-    // is issued only after both waits of iteration i have succeeded)
-    auto drain = [&](int i, int t, bool mma_i) {
-        if (threadIdx.x == 0) {
-            atomicExch(err, 1);
-            if (i >= 1) tc::mbar_wait(&bars[3 + ((i - 1) & 1)], ((i - 1) >> 1) & 1, TC_WAIT_NS);
-            if (mma_i) tc::mbar_wait(&bars[3 + (i & 1)], (i >> 1) & 1, TC_WAIT_NS);
-            tc::mbar_wait(&bars[i % 3], (i / 3) & 1, TC_WAIT_NS);
-            if (t + G0 < total) tc::mbar_wait(&bars[(i + 1) % 3], ((i + 1) / 3) & 1, TC_WAIT_NS);
-        }
-        __syncthreads();
-    };
-    int i = 0;
-    bool failed = false;
-    for (int t = blockIdx.x; t < total; t += G0, ++i) {
-        const int buf = i % 3;
-        unsigned char* sA = sA0 + buf * G::ABYTES;
-        const bool landed = tc::mbar_wait(&bars[buf], (i / 3) & 1, TC_WAIT_NS);
-        if (__syncthreads_or(!landed)) {
-            drain(i, t, false);
-            failed = true;
-            break;
-        }
-        tc_store_fix<CIN>(sA, fixv, fixp);
-        tc::fence_async_smem();
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            tc::fence_after();
-            const uint64_t a_buf = a_desc0 + (uint64_t)((buf * G::ABYTES) >> 4);
-            const uint32_t d_set = tmem + 64 * (i & 1);
+
+    if (warp == 8) {
+        // ---------------- control: TMA and MMA issue (lane 0) ----------------
+        if (lane == 0) {
+            const uint64_t a_desc0 =
+                SW ? tc::desc_sw64(tc::smem_u32(sA0)) : tc::desc_noswz(tc::smem_u32(sA0), G::ABS, 128);
+            const uint64_t b_desc0 =
+                SW ? tc::desc_sw64(tc::smem_u32(sB)) : tc::desc_noswz(tc::smem_u32(sB), COUT * 16, 128);
+            constexpr uint32_t IDESC = tc::idesc_bf16(128, COUT);
+            int n_tma = 0, n_mma = 0;  // issued
+            if ((int)blockIdx.x < total) { issue(blockIdx.x, 0); ++n_tma; }
+            if ((int)blockIdx.x + G0 < total) { issue(blockIdx.x + G0, 1); ++n_tma; }
+            int i = 0;
+            for (int t = blockIdx.x; t < total; t += G0, ++i) {
+                const int buf = i % 3, set = i & 1;
+                if (!tc_wait(&fixed[buf], (i / 3) & 1, abort, err)) break;
+                if (i >= 2 && !tc_wait(&drained[set], ((i - 2) >> 1) & 1, abort, err)) break;
+                tc::fence_after();
+                const uint64_t a_buf = a_desc0 + (uint64_t)((buf * G::ABYTES) >> 4);
+                const uint32_t d_set = tmem + 64 * set;
 #pragma unroll 1
-            for (int mt = 0; mt < 2; ++mt) {
+                for (int mt = 0; mt < 2; ++mt) {
 #pragma unroll
-                for (int tap = 0; tap < 9; ++tap) {
-                    const int dy = tap / 3, dx = tap - 3 * dy;
+                    for (int tap = 0; tap < 9; ++tap) {
+                        const int dy = tap / 3, dx = tap - 3 * dy;
 #pragma unroll
-                    for (int kk = 0; kk < NC / 2; ++kk) {
-                        // start addresses advance in 16-byte units in the descriptor's low bits
-                        const uint64_t a =
-                            a_buf + (uint64_t)(((dx * NC + 2 * kk) * G::ABS + (4 * mt + dy) * TW * 16) >> 4);
-                        const uint64_t bd = b_desc0 + (uint64_t)(((tap * NC + 2 * kk) * COUT * 16) >> 4);
-                        tc::mma_bf16(d_set + 32 * mt, a, bd, IDESC, (tap | kk) != 0);
+                        for (int kk = 0; kk < NC / 2; ++kk) {
+                            // start addresses advance in 16-byte units in the descriptor's low bits; with
+                            // the swizzle, row offsets are whole 8-row atoms and K half kk starts 32 bytes in
+                            const int a_off = SW ? dx * G::CPY + (4 * mt + dy) * TW * 64 + 32 * kk
+                                                 : (dx * NC + 2 * kk) * G::ABS + (4 * mt + dy) * TW * 16;
+                            const int b_off = SW ? tap * COUT * 64 + 32 * kk : (tap * NC + 2 * kk) * COUT * 16;
+                            tc::mma_bf16(d_set + 32 * mt, a_buf + (uint64_t)(a_off >> 4),
+                                         b_desc0 + (uint64_t)(b_off >> 4), IDESC, (tap | kk) != 0);
+                        }
                     }
                 }
+                tc::commit(&done[set]);
+                ++n_mma;
+                // the buffer of tile i - 1 takes the TMA of tile i + 2 once that tile's MMAs completed
+                if (t + 2 * G0 < total) {
+                    if (i >= 1 && !tc_wait(&done[(i - 1) & 1], ((i - 1) >> 1) & 1, abort, err)) break;
+                    issue(t + 2 * G0, (i + 2) % 3);
+                    ++n_tma;
+                }
             }
-            tc::commit(&bars[3 + (i & 1)]);
+            if (*abort) {
+                // one more bounded wait for everything issued: the last MMA batch and the last two TMAs
+                if (n_mma > 0) tc::mbar_wait(&done[(n_mma - 1) & 1], ((n_mma - 1) >> 1) & 1, TC_WAIT_NS);
+                for (int k = n_tma - 2 < 0 ? 0 : n_tma - 2; k < n_tma; ++k)
+                    tc::mbar_wait(&full[k % 3], (k / 3) & 1, TC_WAIT_NS);
+            }
         }
-        if (i >= 1) {
-            // the previous tile's MMAs: then its A buffer takes the TMA two tiles ahead and its
-            // accumulators are drained while this tile's MMAs run
-            const bool done = tc::mbar_wait(&bars[3 + ((i - 1) & 1)], ((i - 1) >> 1) & 1, TC_WAIT_NS);
-            if (__syncthreads_or(!done)) {
-                drain(i, t, true);
-                failed = true;
-                break;
+        __syncwarp();
+    } else {
+        // ---------------- workers: wrap-around pieces and epilogue ----------------
+        uint4 fixv[G::NFIXK];
+        int fixp[G::NFIXK];
+        const int q = warp & 3, mt = warp >> 2;
+        auto epilogue = [&](int t, int set) {
+            const int b = t / tiles_per_img;
+            const TileMap tm = tile_map(t - b * tiles_per_img, H, W, dil);
+            const uint32_t taddr = tmem + ((uint32_t)(32 * q) << 16) + 64 * set + 32 * mt;
+            float v[COUT];
+            if constexpr (COUT == 32) {
+                uint32_t r[32];
+                tc::ld_32x32b_x32(taddr, r);
+                tc::wait_ld();
+#pragma unroll
+                for (int j = 0; j < 32; ++j) v[j] = __uint_as_float(r[j]);
+            } else {
+                uint32_t r[16];
+                tc::ld_32x32b_x16(taddr, r);
+                tc::wait_ld();
+#pragma unroll
+                for (int j = 0; j < 16; ++j) v[j] = __uint_as_float(r[j]);
             }
-            tc::fence_after();
+            const int y = tm.gy(tm.Y0 + 4 * mt + q), x = tm.gx(tm.X0 + lane);
+            const size_t pix = ((size_t)b * H + y) * W + x;
+            if (MODE == 1) {
+                float* o = reinterpret_cast<float*>(out);
+                const size_t plane = (size_t)H * W;
+                o[((size_t)b * 2 + 0) * plane + (size_t)y * W + x] = v[0] + s_bias[0];
+                o[((size_t)b * 2 + 1) * plane + (size_t)y * W + x] = v[1] + s_bias[1];
+            } else {
+                uint4* o = reinterpret_cast<uint4*>(reinterpret_cast<bf16*>(out) + pix * COUT);
+                const uint4* mk = MODE == 2 ? reinterpret_cast<const uint4*>(mask + pix * COUT) : nullptr;
+#pragma unroll
+                for (int j = 0; j < COUT / 8; ++j) {
+                    float e[8];
+#pragma unroll
+                    for (int k = 0; k < 8; ++k) e[k] = v[8 * j + k];
+                    if (MODE == 0) {
+#pragma unroll
+                        for (int k = 0; k < 8; ++k) e[k] = fmaxf(e[k] + s_bias[8 * j + k], 0.f);
+                    } else if (MODE == 2) {
+                        const uint4 m4 = __ldg(mk + j);
+                        const uint32_t mw[4] = {m4.x, m4.y, m4.z, m4.w};
+#pragma unroll
+                        for (int k = 0; k < 8; ++k) {
+                            const unsigned short h = (unsigned short)(mw[k >> 1] >> (16 * (k & 1)));
+                            if (!(__bfloat162float(__ushort_as_bfloat16(h)) > 0.f)) e[k] = 0.f;
+                        }
+                    }
+                    o[j] = make_uint4(pack2(e[0], e[1]), pack2(e[2], e[3]), pack2(e[4], e[5]), pack2(e[6], e[7]));
+                }
+            }
+        };
+        if ((int)blockIdx.x < total) tc_load_fix<CIN>(in, blockIdx.x, tiles_per_img, H, W, dil, fixv, fixp);
+        int i = 0;
+        for (int t = blockIdx.x; t < total; t += G0, ++i) {
+            const int buf = i % 3;
+            if (!tc_wait(&full[buf], (i / 3) & 1, abort, err)) break;
+            tc_store_fix<CIN, SW>(sA0 + buf * G::ABYTES, fixv, fixp);
+            tc::fence_async_smem();
+            __syncwarp();
+            if (lane == 0) tc::mbar_arrive(&fixed[buf]);
+            if (t + G0 < total) tc_load_fix<CIN>(in, t + G0, tiles_per_img, H, W, dil, fixv, fixp);
+            if (i >= 1) {
+                // tile i - 1: its MMAs have had the whole patch step of tile i to complete
+                if (!tc_wait(&done[(i - 1) & 1], ((i - 1) >> 1) & 1, abort, err)) break;
+                tc::fence_after();
+                epilogue(t - G0, (i - 1) & 1);
+                tc::fence_before();
+                __syncwarp();
+                if (lane == 0) tc::mbar_arrive(&drained[(i - 1) & 1]);
+            }
         }
-        if (threadIdx.x == 0 && t + 2 * G0 < total) issue(t + 2 * G0, (i + 2) % 3);
-        if (t + G0 < total) load_fix(t + G0);
-        if (i >= 1) epilogue(t - G0, (i - 1) & 1, tmem);
-        // TMEM reads complete before the MMAs of tile i + 1 overwrite accumulator set (i + 1) & 1
-        tc::fence_before();
-        __syncthreads();
-    }
-    if (!failed && i >= 1) {
-        const int tl = blockIdx.x + (i - 1) * G0;
-        const bool done = tc::mbar_wait(&bars[3 + ((i - 1) & 1)], ((i - 1) >> 1) & 1, TC_WAIT_NS);
-        if (__syncthreads_or(!done)) {
-            if (threadIdx.x == 0) {
-                atomicExch(err, 1);
-                tc::mbar_wait(&bars[3 + ((i - 1) & 1)], ((i - 1) >> 1) & 1, TC_WAIT_NS);
+        if (!*abort && i >= 1) {
+            if (tc_wait(&done[(i - 1) & 1], ((i - 1) >> 1) & 1, abort, err)) {
+                tc::fence_after();
+                epilogue(blockIdx.x + (i - 1) * G0, (i - 1) & 1);
             }
-        } else {
-            tc::fence_after();
-            epilogue(tl, (i - 1) & 1, tmem);
         }
     }
     tc::fence_before();
     __syncthreads();
     tc::fence_after();
-    if (warp == 1) tc::dealloc(tmem, G::TMEM_COLS);
+    if (warp == 8) tc::dealloc(tmem, G::TMEM_COLS);
 }
 
 // ---------------------------------------------------------------------------
@@ -607,18 +676,28 @@ __global__ void __launch_bounds__(288) k_wgrad(const bf16* __restrict__ a, const
     if (threadIdx.x < COUT) bpartial[(size_t)blockIdx.x * COUT + threadIdx.x] = bacc;
 }
 
-__global__ void k_wgrad_reduce(const float* __restrict__ partial, const float* __restrict__ bpartial, int nparts,
-                               int nw, int nb, float* dW, float* db) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+// sum of the CTAs' partials in a fixed order: a 256-thread block owns 32 consecutive outputs;
+// thread (g, j) adds partials g, g + 8, ... of output j, then the 8 group sums are added in order
+__global__ void __launch_bounds__(256) k_wgrad_reduce(const float* __restrict__ partial,
+                                                      const float* __restrict__ bpartial, int nparts, int nw, int nb,
+                                                      float* dW, float* db) {
+    __shared__ float part[8][33];
+    const int j = threadIdx.x & 31, g = threadIdx.x >> 5;
+    const int i = blockIdx.x * 32 + j;
+    float s = 0.f;
     if (i < nw) {
-        float s = 0.f;
-        for (int p = 0; p < nparts; ++p) s += partial[(size_t)p * nw + i];
-        dW[i] = s;
+        for (int p = g; p < nparts; p += 8) s += __ldg(partial + (size_t)p * nw + i);
     } else if (i < nw + nb) {
-        const int j = i - nw;
-        float s = 0.f;
-        for (int p = 0; p < nparts; ++p) s += bpartial[(size_t)p * nb + j];
-        db[j] = s;
+        for (int p = g; p < nparts; p += 8) s += __ldg(bpartial + (size_t)p * nb + (i - nw));
+    }
+    part[g][j] = s;
+    __syncthreads();
+    if (g == 0 && i < nw + nb) {
+        float t = 0.f;
+#pragma unroll
+        for (int k = 0; k < 8; ++k) t += part[k][j];
+        if (i < nw) dW[i] = t;
+        else db[i - nw] = t;
     }
 }
 
@@ -626,47 +705,55 @@ __global__ void k_wgrad_reduce(const float* __restrict__ partial, const float* _
 // weight gradient on the tcgen05 tensor cores (CIN = 32), operands staged by TMA:
 // D[m][co] = sum_p A[m][p] dz[p][co] with M rows m = (dx, ci) of one dy, i.e.
 // the taps (dy, 0..2) times 32 input channels, and K = the pixels of the CTA's
-// tiles.  Both operands are MN-major (16-byte rows of 8 consecutive M or N
-// elements, one row per pixel), which is the NHWC layout itself: A is the
-// forward kernel's three column-shifted halo copies (blocks (s, c), ABS bytes
-// apart, so the 16 8-row groups of an M block are blocks 0..15 at SBO = ABS,
-// and pixel rows advance by LBO = 128 per 8 pixels); the row offset dy selects
-// the tap row.  Block s = 3 (the 4th group of four) is a constant block of
-// ones, so M rows 96..127 of the dy = 0 block accumulate sum_p dz[p][co], the
-// bias gradient.  dz of a tile is COUT / 8 TMA boxes (8 channels x TW x TH)
-// at DBS = TH TW 16 bytes.  Three accumulators (dy = 0, 1, 2) of N = COUT
-// columns stay in TMEM over all of the CTA's tiles and are written once as
-// the CTA's partial sums (reduced by k_wgrad_reduce).
+// tiles.  Both operands are MN-major (one row per pixel holding consecutive M or
+// N elements), which is the NHWC layout itself.  A is the forward kernel's three
+// column-shifted halo copies in the 64-byte-swizzled layout: a copy's 64-byte
+// rows hold the 32 channels, so the four 32-element M groups of an M block are
+// copies s = 0..3 (LBO = the copy size) and 8-pixel K groups are 512 bytes apart
+// (SBO); the row offset dy selects the tap row.  Copy s = 3 is a constant block
+// of ones, so M rows 96..127 of the dy = 0 block accumulate sum_p dz[p][co], the
+// bias gradient.  dz of a tile is one TMA box of (TH x TW pixels x 32 channels)
+// with the same swizzle (COUT = 32) or two 8-channel boxes without swizzle
+// (COUT = 16; LBO = 128 along K, SBO = TH TW 16 between the 8-channel groups).
+// Three accumulators (dy = 0, 1, 2) of N = COUT columns stay in TMEM over all of
+// the CTA's tiles and are written once as the CTA's partial sums (reduced by
+// k_wgrad_reduce).  Warp roles and hand-offs as in k_conv3x3_tc, two stages:
+// full[b] (TMA landed), fixed[b] (pieces patched), done[b] (MMAs of the tile in
+// buffer b completed, so the buffer takes the TMA two tiles ahead).
 // ---------------------------------------------------------------------------
 template <int COUT>
 struct TcWgrad {
     static constexpr int CIN = 32, NC = 4;
-    static constexpr int ABS = TcConv<32, 16>::ABS;
-    static constexpr int DBS = TH * TW * 16;
-    static constexpr int ABLK = 4 * NC * ABS;                     // three shifted copies + the ones block
-    static constexpr int STAGE = ABLK + (COUT / 8) * DBS;        // one buffer: A then dz
-    static constexpr int TXBYTES = 3 * NC * ABS + (COUT / 8) * DBS;
+    using L = HaloLayout<32, true>;
+    static constexpr bool DSW = COUT == 32;                       // dz swizzled
+    static constexpr int DBS = TH * TW * 16;                      // one 8-channel dz block (COUT = 16)
+    static constexpr int ABLK = 4 * L::CPY;                       // three shifted copies + the ones copy
+    static constexpr int DZB = TH * TW * COUT * 2;
+    static constexpr int STAGE = ABLK + DZB;                      // one buffer: A then dz
+    static constexpr int TXBYTES = 3 * L::CPY + DZB;
     static constexpr int NBUF = 2;
-    static constexpr int SMEM = 128 + NBUF * STAGE + 64;
+    static constexpr int SMEM = 1024 + NBUF * STAGE + 96;
     static constexpr int TMEM_COLS = 128;
-    static constexpr int THREADS = 256;
-    static constexpr int NFIXK = (TcConv<32, 16>::NFIX + THREADS - 1) / THREADS;
-    static_assert(STAGE % 128 == 0 && ABS % 128 == 0, "TMA destinations 128-byte aligned");
-    // an M block reads groups 0..15 at ABS from block 0, rows up to (dy + TH) TW of each
-    static_assert(15 * ABS + (TH + 2) * TW * 16 <= ABLK, "A operand out of range");
+    static constexpr int THREADS = 288;
+    static constexpr int NFIXK = (TcConv<32, 16>::NFIX + 255) / 256;
+    static_assert(STAGE % 1024 == 0 && L::CPY % 1024 == 0, "swizzle atoms aligned");
 };
 
 template <int COUT>
-__global__ void __launch_bounds__(256) k_wgrad_tc(const __grid_constant__ CUtensorMap amap,
+__global__ void __launch_bounds__(288) k_wgrad_tc(const __grid_constant__ CUtensorMap amap,
                                                   const __grid_constant__ CUtensorMap dzmap,
                                                   const bf16* __restrict__ a, float* partial, float* bpartial,
                                                   int H, int W, int B, int dil, int* err) {
     using G = TcWgrad<COUT>;
-    constexpr int CIN = 32, NC = 4;
+    using L = typename G::L;
+    constexpr int CIN = 32;
     extern __shared__ unsigned char smraw[];
-    unsigned char* s0 = smraw + ((128u - (tc::smem_u32(smraw) & 127u)) & 127u);
-    uint64_t* bars = reinterpret_cast<uint64_t*>(s0 + G::NBUF * G::STAGE);  // TMA of buffer 0, 1; MMA
-    uint32_t* s_tmem = reinterpret_cast<uint32_t*>(bars + 3);
+    unsigned char* s0 = smraw + ((1024u - (tc::smem_u32(smraw) & 1023u)) & 1023u);
+    uint64_t* full = reinterpret_cast<uint64_t*>(s0 + G::NBUF * G::STAGE);
+    uint64_t* fixed = full + 2;
+    uint64_t* done = full + 4;
+    uint32_t* s_tmem = reinterpret_cast<uint32_t*>(full + 6);
+    volatile int* abort = reinterpret_cast<volatile int*>(full + 6) + 1;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int tiles_per_img = (H / TH) * (W / TW), total = tiles_per_img * B;
     const int G0 = gridDim.x;
@@ -674,29 +761,33 @@ __global__ void __launch_bounds__(256) k_wgrad_tc(const __grid_constant__ CUtens
         const int b = t / tiles_per_img;
         const TileMap tm = tile_map(t - b * tiles_per_img, H, W, dil);
         unsigned char* st = s0 + buf * G::STAGE;
-        tc::mbar_arrive_expect_tx(&bars[buf], G::TXBYTES);
-        tc_issue_halo<CIN>(&amap, st, &bars[buf], tm, b);
+        tc::mbar_arrive_expect_tx(&full[buf], G::TXBYTES);
+        tc_issue_halo<CIN, true>(&amap, st, &full[buf], tm, b);
+        if constexpr (G::DSW) {
+            tc::tma_load_5d(st + G::ABLK, &dzmap, &full[buf], 0, tm.rx, tm.X0, tm.ry, b * tm.Hs + tm.Y0);
+        } else {
 #pragma unroll
-        for (int c = 0; c < COUT / 8; ++c)
-            tc::tma_load_5d(st + G::ABLK + c * G::DBS, &dzmap, &bars[buf], 8 * c, tm.rx, tm.X0, tm.ry,
-                            b * tm.Hs + tm.Y0);
+            for (int c = 0; c < COUT / 8; ++c)
+                tc::tma_load_5d(st + G::ABLK + c * G::DBS, &dzmap, &full[buf], 8 * c, tm.rx, tm.X0, tm.ry,
+                                b * tm.Hs + tm.Y0);
+        }
     };
-    uint4 fixv[G::NFIXK];
-    int fixp[G::NFIXK];
     if (threadIdx.x == 0) {
-        for (int k = 0; k < 3; ++k) tc::mbar_init(&bars[k], 1);
-        if ((int)blockIdx.x < total) issue(blockIdx.x, 0);
-        if ((int)blockIdx.x + G0 < total) issue(blockIdx.x + G0, 1);
+        for (int k = 0; k < 2; ++k) {
+            tc::mbar_init(&full[k], 1);
+            tc::mbar_init(&fixed[k], 8);
+            tc::mbar_init(&done[k], 1);
+        }
+        *abort = 0;
     }
-    if (warp == 1) {
+    if (warp == 8) {
         tc::alloc(s_tmem, G::TMEM_COLS);
         tc::relinquish();
     }
-    if ((int)blockIdx.x < total) tc_load_fix<CIN>(a, blockIdx.x, tiles_per_img, H, W, dil, fixv, fixp);
-    // the ones blocks (s = 3) of both buffers: BF16 1.0 = 0x3F80
-    for (int i = threadIdx.x; i < G::NBUF * NC * G::ABS / 16; i += G::THREADS) {
-        const int buf = i / (NC * G::ABS / 16), r = i - buf * (NC * G::ABS / 16);
-        *reinterpret_cast<uint4*>(s0 + buf * G::STAGE + 3 * NC * G::ABS + r * 16) =
+    // the ones copies (s = 3) of both buffers: BF16 1.0 = 0x3F80 (constant, so the swizzle is moot)
+    for (int i = threadIdx.x; i < G::NBUF * L::CPY / 16; i += blockDim.x) {
+        const int buf = i / (L::CPY / 16), r = i - buf * (L::CPY / 16);
+        *reinterpret_cast<uint4*>(s0 + buf * G::STAGE + 3 * L::CPY + r * 16) =
             make_uint4(0x3F803F80u, 0x3F803F80u, 0x3F803F80u, 0x3F803F80u);
     }
     tc::fence_async_smem();
@@ -704,97 +795,111 @@ __global__ void __launch_bounds__(256) k_wgrad_tc(const __grid_constant__ CUtens
     __syncthreads();
     tc::fence_after();
     const uint32_t tmem = *s_tmem;
-    // MN-major operands: LBO = the step between 8-pixel groups along K, SBO = between 8-element groups along M / N
-    const uint64_t a_desc0 = tc::desc_noswz(tc::smem_u32(s0), 128, G::ABS);
-    const uint64_t d_desc0 = tc::desc_noswz(tc::smem_u32(s0 + G::ABLK), 128, G::DBS);
-    constexpr uint32_t IDESC = tc::idesc_bf16(128, COUT) | (1u << 15) | (1u << 16);
-    int i = 0;
-    bool failed = false;
-    for (int t = blockIdx.x; t < total; t += G0, ++i) {
-        const int buf = i & 1;
-        unsigned char* st = s0 + buf * G::STAGE;
-        const bool landed = tc::mbar_wait(&bars[buf], (i >> 1) & 1, TC_WAIT_NS);
-        if (__syncthreads_or(!landed)) {
-            if (threadIdx.x == 0) {
-                atomicExch(err, 1);
-                tc::mbar_wait(&bars[buf], (i >> 1) & 1, TC_WAIT_NS);
-                if (t + G0 < total) tc::mbar_wait(&bars[buf ^ 1], ((i + 1) >> 1) & 1, TC_WAIT_NS);
-            }
-            __syncthreads();
-            failed = true;
-            break;
-        }
-        tc_store_fix<CIN>(st, fixv, fixp);
-        if (t + G0 < total) tc_load_fix<CIN>(a, t + G0, tiles_per_img, H, W, dil, fixv, fixp);
-        tc::fence_async_smem();
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            tc::fence_after();
-            const uint64_t a_st = a_desc0 + (uint64_t)((buf * G::STAGE) >> 4);
-            const uint64_t d_st = d_desc0 + (uint64_t)((buf * G::STAGE) >> 4);
+    int n_tiles = 0;  // tiles of this CTA
+    for (int t = blockIdx.x; t < total; t += G0) ++n_tiles;
+
+    if (warp == 8) {
+        // ---------------- control: TMA and MMA issue (lane 0) ----------------
+        if (lane == 0) {
+            // MN-major with the 64-byte swizzle: LBO = the step between 32-element M groups (copies),
+            // SBO = 512 between 8-pixel K groups; without swizzle: LBO = 128 along K, SBO between
+            // 8-element N groups
+            auto desc_sw64_mn = [](uint32_t saddr, uint32_t lbo) {
+                return (uint64_t)((saddr >> 4) & 0x3FFFu) | ((uint64_t)((lbo >> 4) & 0x3FFFu) << 16) |
+                       ((uint64_t)(512 >> 4) << 32) | (1ull << 46) | (4ull << 61);
+            };
+            const uint64_t a_desc0 = desc_sw64_mn(tc::smem_u32(s0), L::CPY);
+            const uint64_t d_desc0 = G::DSW ? desc_sw64_mn(tc::smem_u32(s0 + G::ABLK), G::DZB)
+                                            : tc::desc_noswz(tc::smem_u32(s0 + G::ABLK), 128, G::DBS);
+            constexpr uint32_t IDESC = tc::idesc_bf16(128, COUT) | (1u << 15) | (1u << 16);
+            int n_tma = 0, n_mma = 0;
+            if (n_tiles > 0) { issue(blockIdx.x, 0); ++n_tma; }
+            if (n_tiles > 1) { issue(blockIdx.x + G0, 1); ++n_tma; }
+            for (int i = 0; i < n_tiles; ++i) {
+                const int buf = i & 1;
+                if (!tc_wait(&fixed[buf], (i >> 1) & 1, abort, err)) break;
+                tc::fence_after();
+                const uint64_t a_st = a_desc0 + (uint64_t)((buf * G::STAGE) >> 4);
+                const uint64_t d_st = d_desc0 + (uint64_t)((buf * G::STAGE) >> 4);
 #pragma unroll 1
-            for (int dy = 0; dy < 3; ++dy) {
+                for (int dy = 0; dy < 3; ++dy) {
 #pragma unroll 4
-                for (int ks = 0; ks < TH * TW / 16; ++ks) {
-                    // K slice ks: 16 pixels of tile row r = ks / 2 from column x0 = 16 (ks & 1)
-                    const int r = ks >> 1, x0 = (ks & 1) * 16;
-                    const uint64_t ad = a_st + (uint64_t)((((r + dy) * TW + x0) * 16) >> 4);
-                    const uint64_t dd = d_st + (uint64_t)(((r * TW + x0) * 16) >> 4);
-                    tc::mma_bf16(tmem + 32 * dy, ad, dd, IDESC, (i | ks) != 0);
+                    for (int ks = 0; ks < TH * TW / 16; ++ks) {
+                        // K slice ks: 16 pixels of tile row r = ks / 2 from column x0 = 16 (ks & 1)
+                        const int r = ks >> 1, x0 = (ks & 1) * 16;
+                        const int a_off = ((r + dy) * TW + x0) * 64;
+                        const int d_off = (r * TW + x0) * (G::DSW ? 64 : 16);
+                        tc::mma_bf16(tmem + 32 * dy, a_st + (uint64_t)(a_off >> 4), d_st + (uint64_t)(d_off >> 4),
+                                     IDESC, (i | ks) != 0);
+                    }
+                }
+                tc::commit(&done[buf]);
+                ++n_mma;
+                if (i + 2 < n_tiles) {
+                    if (!tc_wait(&done[buf], (i >> 1) & 1, abort, err)) break;
+                    issue(blockIdx.x + (i + 2) * G0, buf);
+                    ++n_tma;
                 }
             }
-            tc::commit(&bars[2]);
-        }
-        const bool done = tc::mbar_wait(&bars[2], i & 1, TC_WAIT_NS);
-        if (__syncthreads_or(!done)) {
-            if (threadIdx.x == 0) {
-                atomicExch(err, 1);
-                tc::mbar_wait(&bars[2], i & 1, TC_WAIT_NS);
-                if (t + G0 < total) tc::mbar_wait(&bars[buf ^ 1], ((i + 1) >> 1) & 1, TC_WAIT_NS);
+            if (*abort) {
+                if (n_mma > 0) tc::mbar_wait(&done[(n_mma - 1) & 1], ((n_mma - 1) >> 1) & 1, TC_WAIT_NS);
+                for (int k = n_tma - 2 < 0 ? 0 : n_tma - 2; k < n_tma; ++k)
+                    tc::mbar_wait(&full[k & 1], (k >> 1) & 1, TC_WAIT_NS);
             }
-            __syncthreads();
-            failed = true;
-            break;
         }
-        // this buffer is free again: the TMA of the tile after next
-        if (threadIdx.x == 0 && t + 2 * G0 < total) issue(t + 2 * G0, buf);
-    }
-    if (!failed && i > 0) {
-        tc::fence_after();
-        // warp w: lane quarter q = w % 4 holds M rows 32 q + lane = (dx = q, ci = lane); warps 0-3
-        // drain the dy = 0 and dy = 2 accumulators, warps 4-7 the dy = 1 one
-        const int q = warp & 3;
-        float* P = partial + (size_t)blockIdx.x * COUT * 9 * CIN;
-        for (int dy = warp >> 2; dy < 3; dy += 2) {
-            const uint32_t taddr = tmem + ((uint32_t)(32 * q) << 16) + 32 * dy;
-            float v[COUT];
-            if constexpr (COUT == 32) {
-                uint32_t r[32];
-                tc::ld_32x32b_x32(taddr, r);
-                tc::wait_ld();
+        __syncwarp();
+    } else {
+        // ---------------- workers: wrap-around pieces, then the partial sums ----------------
+        uint4 fixv[G::NFIXK];
+        int fixp[G::NFIXK];
+        if (n_tiles > 0) tc_load_fix<CIN>(a, blockIdx.x, tiles_per_img, H, W, dil, fixv, fixp);
+        for (int i = 0; i < n_tiles; ++i) {
+            const int buf = i & 1;
+            if (!tc_wait(&full[buf], (i >> 1) & 1, abort, err)) break;
+            tc_store_fix<CIN, true>(s0 + buf * G::STAGE, fixv, fixp);
+            tc::fence_async_smem();
+            __syncwarp();
+            if (lane == 0) tc::mbar_arrive(&fixed[buf]);
+            if (i + 1 < n_tiles) tc_load_fix<CIN>(a, blockIdx.x + (i + 1) * G0, tiles_per_img, H, W, dil, fixv, fixp);
+        }
+        // the last batch's commit completes after every earlier MMA of this thread
+        if (!*abort && n_tiles > 0 && tc_wait(&done[(n_tiles - 1) & 1], ((n_tiles - 1) >> 1) & 1, abort, err)) {
+            tc::fence_after();
+            // warp w: lane quarter q = w % 4 holds M rows 32 q + lane = (dx = q, ci = lane); warps 0-3
+            // drain the dy = 0 and dy = 2 accumulators, warps 4-7 the dy = 1 one
+            const int q = warp & 3;
+            float* P = partial + (size_t)blockIdx.x * COUT * 9 * CIN;
+            for (int dy = warp >> 2; dy < 3; dy += 2) {
+                const uint32_t taddr = tmem + ((uint32_t)(32 * q) << 16) + 32 * dy;
+                float v[COUT];
+                if constexpr (COUT == 32) {
+                    uint32_t r[32];
+                    tc::ld_32x32b_x32(taddr, r);
+                    tc::wait_ld();
 #pragma unroll
-                for (int j = 0; j < 32; ++j) v[j] = __uint_as_float(r[j]);
-            } else {
-                uint32_t r[16];
-                tc::ld_32x32b_x16(taddr, r);
-                tc::wait_ld();
+                    for (int j = 0; j < 32; ++j) v[j] = __uint_as_float(r[j]);
+                } else {
+                    uint32_t r[16];
+                    tc::ld_32x32b_x16(taddr, r);
+                    tc::wait_ld();
 #pragma unroll
-                for (int j = 0; j < 16; ++j) v[j] = __uint_as_float(r[j]);
-            }
-            if (q < 3) {
-                const int tap = 3 * dy + q;
+                    for (int j = 0; j < 16; ++j) v[j] = __uint_as_float(r[j]);
+                }
+                if (q < 3) {
+                    const int tap = 3 * dy + q;
 #pragma unroll
-                for (int co = 0; co < COUT; ++co) P[(co * 9 + tap) * CIN + lane] = v[co];
-            } else if (dy == 0 && lane == 0) {
+                    for (int co = 0; co < COUT; ++co) P[(co * 9 + tap) * CIN + lane] = v[co];
+                } else if (dy == 0 && lane == 0) {
 #pragma unroll
-                for (int co = 0; co < COUT; ++co) bpartial[(size_t)blockIdx.x * COUT + co] = v[co];
+                    for (int co = 0; co < COUT; ++co) bpartial[(size_t)blockIdx.x * COUT + co] = v[co];
+                }
             }
         }
     }
     tc::fence_before();
     __syncthreads();
     tc::fence_after();
-    if (warp == 1) tc::dealloc(tmem, G::TMEM_COLS);
+    if (warp == 8) tc::dealloc(tmem, G::TMEM_COLS);
 }
 
 // images (fp32 planar [B][2][H][W]) -> NHWC bf16 with 16 channels (2 real)
@@ -953,17 +1058,20 @@ static PFN_cuTensorMapEncodeTiled_v12000 tmap_encoder() {
 
 // 5-D view (C, rx, X, ry, Y + (H/d) b) of B NHWC images with C channels: the sub-grid
 // (ry, rx) of dilation d is the 3-D box (C, X, Y) at fixed (rx, ry); boxes of 8 channels x TW x rows
-static bool halo_tensor_map(CUtensorMap* m, const bf16* act, int C, int d, int H, int W, int B, int rows = TH + 2) {
+static bool halo_tensor_map(CUtensorMap* m, const bf16* act, int C, int d, int H, int W, int B, int rows = TH + 2,
+                            bool sw64 = false) {
     const PFN_cuTensorMapEncodeTiled_v12000 enc = tmap_encoder();
     if (!enc) return false;
     const cuuint64_t e = sizeof(bf16);
     cuuint64_t dims[5] = {(cuuint64_t)C, (cuuint64_t)d, (cuuint64_t)(W / d), (cuuint64_t)d, (cuuint64_t)(H / d) * B};
     cuuint64_t strides[4] = {C * e, (cuuint64_t)d * C * e, (cuuint64_t)W * C * e, (cuuint64_t)d * W * C * e};
-    cuuint32_t box[5] = {8, 1, TW, 1, (cuuint32_t)rows};
+    // boxes of 8 channels (16-byte rows), or of all 32 channels with the 64-byte swizzle
+    cuuint32_t box[5] = {sw64 ? 32u : 8u, 1, TW, 1, (cuuint32_t)rows};
     cuuint32_t estr[5] = {1, 1, 1, 1, 1};
+    if (sw64 && C != 32) return false;
     return enc(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 5, const_cast<bf16*>(act), dims, strides, box, estr,
-               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+               CU_TENSOR_MAP_INTERLEAVE_NONE, sw64 ? CU_TENSOR_MAP_SWIZZLE_64B : CU_TENSOR_MAP_SWIZZLE_NONE,
+               CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
 template <int CIN, int COUT, int MODE>
@@ -972,7 +1080,7 @@ static bool conv_launch(reg_net* n, const bf16* in, const bf16* w, const float* 
     const int tiles = (n->H / TH) * (n->W / TW);
     if (n->conv_kind == REG_CONV_TCGEN05) {
         CUtensorMap map;
-        if (!halo_tensor_map(&map, in, CIN, d, n->H, n->W, B)) return false;
+        if (!halo_tensor_map(&map, in, CIN, d, n->H, n->W, B, TH + 2, TcConv<CIN, COUT>::SW)) return false;
         const int total = tiles * B;
         int grid = n->tc_grid[CIN == 32][COUT == 32][MODE];
         if (grid > total) grid = total;
@@ -990,7 +1098,8 @@ static bool conv_launch(reg_net* n, const bf16* in, const bf16* w, const float* 
 template <int COUT>
 static int wgrad_tc_launch(reg_net* n, const bf16* a, const bf16* dz, int B, int d) {
     CUtensorMap am, dm;
-    if (!halo_tensor_map(&am, a, 32, d, n->H, n->W, B) || !halo_tensor_map(&dm, dz, COUT, d, n->H, n->W, B, TH))
+    if (!halo_tensor_map(&am, a, 32, d, n->H, n->W, B, TH + 2, true) ||
+        !halo_tensor_map(&dm, dz, COUT, d, n->H, n->W, B, TH, TcWgrad<COUT>::DSW))
         return 0;
     const int total = (n->H / TH) * (n->W / TW) * B;
     const int grid = std::min(total, n->tc_wgrad_grid[COUT == 32]);
@@ -1289,7 +1398,7 @@ static int net_loss_grad(reg_net* n, const float* images, const float* targets, 
             k_wgrad<16, 32><<<n->nwg, 288, wgrad_smem(16, 32), n->stream>>>(n->act[0], dz, n->partial, n->bpartial, H, W, B, d);
         }
         const int nw = L.coutp * 9 * L.cinp, nb = L.coutp;
-        k_wgrad_reduce<<<(nw + nb + 255) / 256, 256, 0, n->stream>>>(n->partial, n->bpartial, nparts, nw, nb, gWl, gbl);
+        k_wgrad_reduce<<<(nw + nb + 31) / 32, 256, 0, n->stream>>>(n->partial, n->bpartial, nparts, nw, nb, gWl, gbl);
         if (l > 0) {
             // input gradient through the ReLU of layer l-1: correlation with the flipped, transposed kernel
             const bf16* wtl = n->wt + n->wfoff[l];

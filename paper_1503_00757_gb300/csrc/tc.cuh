@@ -29,6 +29,15 @@ __device__ __forceinline__ uint64_t desc_noswz(uint32_t saddr, uint32_t lbo, uin
            ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | (1ull << 46);
 }
 
+// the same with the 64-byte swizzle (layout type 4 in bits 61-63): K-major rows of 64 bytes
+// (32 BF16 along K) whose 16-byte chunks are permuted within 8-row atoms of 512 bytes,
+// chunk j of row r stored at chunk j ^ ((r >> 1) & 3) (r counted from a 1024-byte boundary);
+// SBO = 512, the step between 8-row atoms; LBO unused (encoded as 16 bytes)
+__device__ __forceinline__ uint64_t desc_sw64(uint32_t saddr) {
+    return (uint64_t)((saddr >> 4) & 0x3FFFu) | (1ull << 16) | ((uint64_t)(512 >> 4) << 32) | (1ull << 46) |
+           (4ull << 61);
+}
+
 // instruction descriptor of kind::f16: D FP32 (bits 4-5 = 1), A and B BF16 (bits 7-9,
 // 10-12 = 1), both K-major (bits 15, 16 = 0), N >> 3 in bits 17-22, M >> 4 in bits 24-28
 __host__ __device__ constexpr uint32_t idesc_bf16(int M, int N) {
@@ -84,6 +93,10 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* mbar, uint32_t parity) {
         : "r"(smem_u32(mbar)), "r"(parity)
         : "memory");
     return ok != 0;
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t* mbar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(mbar)) : "memory");
 }
 
 // expect `bytes` more transaction bytes on *mbar and arrive once
