@@ -98,16 +98,23 @@ def test_cluster_transport_matches_oracle_and_two_kernel_path(case):
 
 def test_cluster_solve_matches_oracle_solve():
     """A full registration (Algorithm 1) on each transport path reaches the tolerance with the
-    FP64 oracle's Newton count and its velocity to 1e-3 (the end-to-end bar).  The solves run
-    to ||g|| <= 1e-3 ||g(0)||: at 1e-2 the stopping test itself admits velocities about 2e-3
-    apart (measured between the two FP32 paths), so a tighter solve is what determines v to
-    the bar."""
+    FP64 oracle's Newton count, and the FP64 oracle confirms the stopping test at the GPU's
+    velocity: ||g(v)|| <= 1e-3 ||g(0)|| with g evaluated by the oracle (slack 10 % for the FP32
+    gradient the GPU stopped on, whose error is ~1e-5 ||g(0)||).
+
+    The velocity itself is fixed only to the stopping rule: two iterates that both satisfy
+    ||g|| <= 1e-3 ||g(0)|| may differ by up to ||H^-1|| 2e-3 ||g(0)||, i.e. by kappa(H) 2e-3
+    relative, and the paths' FP32 roundings send PCG down slightly different iterates (measured
+    1.0e-3 for the two-kernel path and 1.6e-3 for the cluster path against the oracle's solve),
+    so v is compared at 3e-3 as a sanity bound; the gradient check is the one that binds."""
     import torch
     from paper_1503_00757_gb300.binding import Context, default_opts
     n, nt = 128, 16
     mT, mR, _ = synth.ellipses_pair(n, 3100, vmax=0.2)
-    v_ref, st_ref = Registration(mT, mR, nt, regnorm=1, beta_v=1e-3, beta_w=math.inf).solve(tol=1e-3)
+    P = Registration(mT, mR, nt, regnorm=1, beta_v=1e-3, beta_w=math.inf)
+    v_ref, st_ref = P.solve(tol=1e-3)
     assert st_ref["status"] == 0
+    g0 = np.linalg.norm(P.gradient(np.zeros_like(v_ref))[0])
     for cluster in (True, False):
         ctx = Context(n, n, nt, regnorm=1, beta=1e-3, gamma=math.inf)
         ctx.set_transport(cluster)
@@ -119,4 +126,7 @@ def test_cluster_solve_matches_oracle_solve():
         tag = "cluster" if cluster else "two-kernel"
         assert st["status"] == 0 and st["gnorm_rel"] <= 1e-3
         assert st["n_newton"] == st_ref["n_newton"]
-        check_rel(f"solve v ({tag} path)", to_np(v), v_ref, 1e-3)
+        vg = to_np(v).astype(np.float64)
+        g_rel = np.linalg.norm(P.gradient(vg)[0]) / g0
+        check(f"oracle ||g(v)|| / ||g(0)|| at the solved v ({tag} path)", g_rel, 1.1e-3)
+        check_rel(f"solve v ({tag} path), stopping-rule spread", vg, v_ref, 3e-3)
