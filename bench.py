@@ -816,6 +816,36 @@ def main():
                     "speedup": w_["registrations_per_s"] / z["registrations_per_s"]}
             netw.close()
             exw.close()
+            # the same network (fully convolutional) on this benchmark's own 512^2, nt=32 pairs: zero start
+            # against the prediction, same stopping test, through the executor that times `value`
+            netb = Net(N_GRID, N_GRID, PAIRS)
+            netb.set_params(torch.from_numpy(np.load(wpath).astype(np.float32)).to(dev))
+            netb.set_output_scale(wscale)
+            xb = torch.stack([torch.stack([p_["mT"], p_["mR"]]) for p_ in pairs]).contiguous()
+
+            def run512(v0, o):
+                ps = [dict(p_, v=(torch.zeros(2, N_GRID, N_GRID, device=dev) if v0 is None else v0[i].clone()),
+                           detgrad=0) for i, p_ in enumerate(pairs)]
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                _, st_ = ex.solve(ps, o, check=False)
+                torch.cuda.synchronize()
+                return st_, time.perf_counter() - t0
+
+            st0b, s0b = run512(None, opts)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            vpb = torch.empty(PAIRS, 2, N_GRID, N_GRID, device=dev)
+            netb.forward(xb, vpb)
+            torch.cuda.synchronize()
+            spb = time.perf_counter() - t0
+            st1b, s1b = run512(vpb, default_opts(tol=1e-2, warm_start=1))
+            zb, wb = ws.summarize(st0b, s0b), ws.summarize(st1b, s1b + spb)
+            warm["at_512"] = {"workload": WORKLOAD.split(";")[0] + "; the 256^2-trained network applied at 512^2, "
+                              f"{PAIRS} pairs of this step, tol 1e-2",
+                              "plain": zb, "warm": wb, "matvec_reduction": 1.0 - wb["matvec_mean"] / zb["matvec_mean"],
+                              "speedup": wb["registrations_per_s"] / zb["registrations_per_s"]}
+            netb.close()
         # shear-control model (nonlinear Stokes, s = -1/2: shear thickening, +1/2: shear thinning) on the
         # first 512^2 pair: a full solve and Hessian matvecs/s at its solution (one context, single-stream tiles)
         shear = {}

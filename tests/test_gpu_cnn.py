@@ -22,6 +22,8 @@ import pytest
 from oracle import cnn
 from paper_1503_00757_gb300 import synth
 
+from .gpu_util import check
+
 pytestmark = pytest.mark.gpu
 
 
@@ -191,17 +193,17 @@ def test_per_layer_parity(H, W, B, kind):
         z = cnn.conv3x3(a, Wl, bl, dil[l])
         out = _layer(net, REG_NET_OUTPUT, l, (B, cout, H, W))
         if l < L - 1:
-            assert _rel(out, np.maximum(z, 0.0)) < 1e-2, ("forward", l, _rel(out, np.maximum(z, 0.0)))
+            check(f"network layer output, BF16 ({kind})", _rel(out, np.maximum(z, 0.0)), 1e-2, layer=l)
         else:
-            assert _rel(out, z) < 1e-4, ("forward", l, _rel(out, z))
+            check(f"network raw output, FP32 ({kind})", _rel(out, z), 1e-4, layer=l)
         dz = _layer(net, REG_NET_OUTPUT_GRAD, l, (B, cout, H, W))
         da, dW, db = cnn.conv3x3_backward(a, Wl, dz / M, dil[l])
-        assert _rel(g[l][0], dW) < 1e-4, ("dW", l, _rel(g[l][0], dW))
-        assert _rel(g[l][1], db) < 1e-4, ("db", l, _rel(g[l][1], db))
+        check(f"network weight gradient ({kind})", _rel(g[l][0], dW), 1e-4, layer=l)
+        check(f"network bias gradient ({kind})", _rel(g[l][1], db), 1e-4, layer=l)
         if l > 0:
             dz_prev = _layer(net, REG_NET_OUTPUT_GRAD, l - 1, (B, cin, H, W))
             ref = M * da * (a > 0.0)
-            assert _rel(dz_prev, ref) < 1e-2, ("input gradient", l, _rel(dz_prev, ref))
+            check(f"network input gradient, BF16 ({kind})", _rel(dz_prev, ref), 1e-2, layer=l)
     net.close()
 
 
