@@ -403,6 +403,13 @@ int reg_net_set_output_scale(reg_net* net, float scale);
 int reg_net_loss_grad(reg_net* net, const float* images, const float* targets, int B, double* loss, float* grads);
 /* One Adam step with learning rate lr on that loss.  Synchronous (loss is read back). */
 int reg_net_train_step(reg_net* net, const float* images, const float* targets, int B, float lr, double* loss);
+/* Warm start for image pairs on the doubled grid (2H, 2W) from the network at H x W (the
+ * resolution it was trained at): the images (device, B x 2 x 2H x 2W) are restricted by full
+ * weighting (weights 1/4, 1/2, 1/4 per axis, periodic), the prediction P G net(x) on H x W is
+ * prolonged bilinearly (periodic), and the fine grid's own output map P G (sigma = 2 h of that
+ * grid) and the output scale s give v_out (device, B x 2 x 2H x 2W), divergence free on the fine
+ * grid.  2H, 2W <= 1024.  The first call allocates a projection context and buffers. */
+int reg_net_forward_fine(reg_net* net, const float* images, int B, float* v_out);
 /* Convolution kernel of every forward and input-gradient convolution:
  * REG_CONV_TCGEN05 (default): 5th-generation tensor cores, FP32 accumulator in
  *   tensor memory; a persistent CTA per tile slot, MMAs issued by one thread.

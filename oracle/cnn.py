@@ -116,6 +116,38 @@ def predict(params, x):
     return output_map(forward(params, x))
 
 
+def restrict2(u):
+    """(..., 2H, 2W) -> (..., H, W): full weighting around fine node (2i, 2j), weights 1/4, 1/2, 1/4
+    along each axis, periodic.  (Resampling of the warm-start pipeline; the paper has none.)"""
+    out = np.zeros(u.shape[:-2] + (u.shape[-2] // 2, u.shape[-1] // 2))
+    w = {-1: 0.25, 0: 0.5, 1: 0.25}
+    for dy in (-1, 0, 1):
+        for dx in (-1, 0, 1):
+            out += w[dy] * w[dx] * _shift(u, dy, dx)[..., ::2, ::2]
+    return out
+
+
+def prolong2(u):
+    """(..., H, W) -> (..., 2H, 2W): bilinear interpolation, periodic; fine node (y, x) sits at
+    coarse coordinates (y / 2, x / 2)."""
+    H, W = u.shape[-2:]
+    out = np.empty(u.shape[:-2] + (2 * H, 2 * W))
+    right = _shift(u, 0, 1)
+    down = _shift(u, 1, 0)
+    diag = _shift(u, 1, 1)
+    out[..., ::2, ::2] = u
+    out[..., ::2, 1::2] = 0.5 * (u + right)
+    out[..., 1::2, ::2] = 0.5 * (u + down)
+    out[..., 1::2, 1::2] = 0.25 * (u + right + down + diag)
+    return out
+
+
+def predict_fine(params, x_fine, scale=1.0):
+    """Warm start on the doubled grid from the network at the coarse grid: restrict the images,
+    predict there, prolong, and apply the fine grid's own output map, times the output scale."""
+    return scale * output_map(prolong2(predict(params, restrict2(x_fine))))
+
+
 def loss_and_grads(params, x, t):
     """MSE loss of the filtered, projected prediction against t and its parameter gradients."""
     out, acts = forward(params, x, cache=True)

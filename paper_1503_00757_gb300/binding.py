@@ -102,6 +102,7 @@ _SIGS = {
     "reg_net_set_output_scale": ([_P, ctypes.c_float], _I),
     "reg_net_loss_grad": ([_P, _P, _P, _I, ctypes.POINTER(_D), _P], _I),
     "reg_net_train_step": ([_P, _P, _P, _I, ctypes.c_float, ctypes.POINTER(_D)], _I),
+    "reg_net_forward_fine": ([_P, _P, _I, _P], _I),
     "reg_net_set_conv_kernel": ([_P, _I], _I),
     "reg_net_set_record": ([_P, _I], _I),
     "reg_net_layer_tensor": ([_P, _I, _I, _I, _P], _I),
@@ -288,6 +289,12 @@ class Net:
         B = images.shape[0]
         n = B * 2 * self.H * self.W
         _check(lib().reg_net_forward(self.h, _ptr(images, n, "images"), B, _ptr(v_out, n, "v_out")))
+
+    def forward_fine(self, images, v_out):
+        """Warm start for pairs on the doubled grid: images and v_out are B x 2 x 2H x 2W."""
+        B = images.shape[0]
+        n = B * 2 * 4 * self.H * self.W
+        _check(lib().reg_net_forward_fine(self.h, _ptr(images, n, "images"), B, _ptr(v_out, n, "v_out")))
 
     def set_output_scale(self, scale):
         """reg_net_forward returns scale times the projected prediction (warm-start damping)."""

@@ -1035,6 +1035,8 @@ struct reg_net {
     int* h_err;                // pinned copy, refreshed at the end of every forward / backward
     bool record;               // keep every layer's output gradient (reg_net_layer_tensor)
     bf16* dz_rec[NLAYER];
+    reg_ctx* proj_fine;        // output map on the (2H, 2W) grid of reg_net_forward_fine (created on first use)
+    float *coarse_img, *fine_v;  // restricted images (maxB x 2 x H x W), prolonged prediction (maxB x 2 x 2H x 2W)
 };
 
 static size_t conv_smem(int cin, int cout) {
@@ -1156,6 +1158,9 @@ static void opt_in(K k, size_t bytes) {
 extern "C" void reg_net_destroy(reg_net* n) {
     if (!n) return;
     if (n->proj) reg_destroy(n->proj);
+    if (n->proj_fine) reg_destroy(n->proj_fine);
+    cudaFree(n->coarse_img);
+    cudaFree(n->fine_v);
     void* ptrs[] = {n->d_layers, n->params, n->m1, n->m2, n->gW, n->gb, n->d_gwoff, n->d_gboff, n->d_wfoff,
                     n->wf, n->wt, n->bpad, n->dzA, n->dzB, n->out, n->pred, n->res, n->dout, n->partial,
                     n->bpartial, n->d_part, n->d_err};
@@ -1265,6 +1270,10 @@ extern "C" int reg_net_create(int H, int W, int max_batch, reg_net** out) {
 extern "C" int reg_net_set_stream(reg_net* n, void* stream) {
     if (!n) return reg_fail(REG_ERR_ARG, "net is NULL");
     n->stream = (cudaStream_t)stream;
+    if (n->proj_fine) {
+        const int st = reg_set_stream(n->proj_fine, stream);
+        if (st != REG_OK) return st;
+    }
     return reg_set_stream(n->proj, stream);
 }
 
@@ -1524,5 +1533,90 @@ extern "C" int reg_net_layer_tensor(reg_net* n, int kind, int layer, int B, floa
     }
     k_unpack_nhwc<<<304, 256, 0, n->stream>>>(src, out, cs, c, npix, plane);
     const cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? REG_OK : reg_fail(REG_ERR_CUDA, cudaGetErrorString(e));
+}
+
+namespace {
+// (B, 2, 2H, 2W) -> (B, 2, H, W): full weighting, weights 1/4, 1/2, 1/4 along each axis around
+// fine node (2i, 2j), periodic
+__global__ void k_restrict2(const float* __restrict__ f, float* __restrict__ c, int planes, int H, int W) {
+    const int Hf = 2 * H, Wf = 2 * W;
+    const long long total = (long long)planes * H * W;
+    for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < total;
+         idx += (long long)gridDim.x * blockDim.x) {
+        const long long pl = idx / ((long long)H * W);
+        const int r = (int)(idx - pl * H * W), i = r / W, j = r - i * W;
+        const float* fp = f + pl * (long long)Hf * Wf;
+        const float wgt[3] = {0.25f, 0.5f, 0.25f};
+        float acc = 0.f;
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            const int y = (2 * i + a - 1 + Hf) & (Hf - 1);
+            float row = 0.f;
+#pragma unroll
+            for (int b = 0; b < 3; ++b) row += wgt[b] * fp[(long long)y * Wf + ((2 * j + b - 1 + Wf) & (Wf - 1))];
+            acc += wgt[a] * row;
+        }
+        c[idx] = acc;
+    }
+}
+
+// (B, 2, H, W) -> (B, 2, 2H, 2W): bilinear, periodic; fine node (y, x) sits at coarse (y / 2, x / 2)
+__global__ void k_prolong2(const float* __restrict__ c, float* __restrict__ f, int planes, int H, int W) {
+    const int Hf = 2 * H, Wf = 2 * W;
+    const long long total = (long long)planes * Hf * Wf;
+    for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < total;
+         idx += (long long)gridDim.x * blockDim.x) {
+        const long long pl = idx / ((long long)Hf * Wf);
+        const int r = (int)(idx - pl * Hf * Wf), y = r / Wf, x = r - y * Wf;
+        const float* cp = c + pl * (long long)H * W;
+        const int i0 = y >> 1, j0 = x >> 1, i1 = (i0 + 1) & (H - 1), j1 = (j0 + 1) & (W - 1);
+        const float ty = 0.5f * (y & 1), tx = 0.5f * (x & 1);
+        f[idx] = (1.f - ty) * ((1.f - tx) * cp[i0 * W + j0] + tx * cp[i0 * W + j1]) +
+                 ty * ((1.f - tx) * cp[i1 * W + j0] + tx * cp[i1 * W + j1]);
+    }
+}
+}  // namespace
+
+extern "C" int reg_net_forward_fine(reg_net* n, const float* images, int B, float* v_out) {
+    if (!n || !images || !v_out) return reg_fail(REG_ERR_ARG, "NULL argument");
+    if (B < 1 || B > n->maxB) return reg_fail(REG_ERR_ARG, "batch out of range");
+    const int H = n->H, W = n->W, Hf = 2 * H, Wf = 2 * W;
+    if (Hf > 1024 || Wf > 1024) return reg_fail(REG_ERR_ARG, "the fine grid (2H, 2W) must fit [16, 1024]");
+    if (!n->proj_fine) {
+        reg_ctx* pf = nullptr;
+        int st = reg_create(reg_grid{Hf, Wf}, 1, REG_H1, 1.0, INFINITY, 0.0, &pf);
+        if (st != REG_OK) return st;
+        st = reg_set_stream(pf, n->stream);
+        if (st != REG_OK) {
+            reg_destroy(pf);
+            return st;
+        }
+        const size_t pix = (size_t)n->maxB * H * W;
+        if (cudaMalloc((void**)&n->coarse_img, sizeof(float) * 2 * pix) != cudaSuccess ||
+            cudaMalloc((void**)&n->fine_v, sizeof(float) * 8 * pix) != cudaSuccess) {
+            cudaGetLastError();
+            cudaFree(n->coarse_img);
+            n->coarse_img = nullptr;
+            reg_destroy(pf);
+            return reg_fail(REG_ERR_NOMEM, "fine-grid warm-start buffers");
+        }
+        n->proj_fine = pf;
+    }
+    k_restrict2<<<304, 256, 0, n->stream>>>(images, n->coarse_img, 2 * B, H, W);
+    int st = net_forward(n, n->coarse_img, B);  // n->pred = P G net(x) on the H x W grid
+    if (st != REG_OK) return st;
+    k_prolong2<<<304, 256, 0, n->stream>>>(n->pred, n->fine_v, 2 * B, H, W);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return reg_fail(REG_ERR_CUDA, cudaGetErrorString(e));
+    // the fine grid's own output map P G (sigma = 2 h of that grid), then the output scale
+    const size_t ff = (size_t)2 * Hf * Wf;
+    const double sigma = 2.0 * (2.0 * M_PI / (double)(Hf > Wf ? Hf : Wf));
+    for (int b = 0; b < B; ++b) {
+        st = apply_smooth_proj(n->proj_fine, (float)(0.5 * sigma * sigma), n->fine_v + b * ff, v_out + b * ff);
+        if (st != REG_OK) return st;
+    }
+    if (n->out_scale != 1.f) launch_axpby(n->proj_fine, (long long)B * ff, n->out_scale, v_out, 0.f, v_out, -1, -1, v_out);
+    e = cudaGetLastError();
     return e == cudaSuccess ? REG_OK : reg_fail(REG_ERR_CUDA, cudaGetErrorString(e));
 }

@@ -226,3 +226,37 @@ def test_conv_kernels_agree():
         outs.append(_layer(net, REG_NET_OUTPUT, 7, (B, 2, H, W)))
         net.close()
     assert _rel(outs[0], outs[1]) < 1e-2
+
+
+def test_forward_fine_matches_oracle():
+    """Warm start on the doubled grid (reg_net_forward_fine): a 64^2 network applied to 128^2
+    pairs.  Checked in three parts.  (1) The restricted images the network saw: the GPU's packed
+    BF16 input of layer 0 against the oracle's FP64 full weighting rounded to BF16 (one BF16
+    rounding apart at most: one unit in the last place, at most 2^-7 of the value).  (2) Everything after the network: the oracle applies
+    the coarse output map, the bilinear prolongation, the fine output map and the scale to the
+    GPU's own FP32 raw network output (FP32 spectral passes: 1e-5).  (3) End to end against
+    oracle.cnn.predict_fine with BF16-rounded weights (3e-2, as for the coarse forward pass)."""
+    import torch
+    from paper_1503_00757_gb300.binding import REG_NET_INPUT, REG_NET_OUTPUT, Net, flatten_params
+    H, B, s = 64, 2, 0.7
+    params = cnn.init_params(31)
+    rng = np.random.default_rng(32)
+    params = [(bf16_round(W_), rng.standard_normal(b.shape) * 0.05) for W_, b in params]
+    x = np.stack([np.stack(synth.ellipses_pair(2 * H, 5500 + i, vmax=0.098, kmax=8)[:2]) for i in range(B)])
+    net = Net(H, H, B)
+    net.set_params(torch.tensor(flatten_params(params), dtype=torch.float32, device="cuda"))
+    net.set_output_scale(s)
+    xg = torch.tensor(x, dtype=torch.float32, device="cuda").contiguous()
+    v = torch.empty(B, 2, 2 * H, 2 * H, device="cuda")
+    net.forward_fine(xg, v)
+    torch.cuda.synchronize()
+    vg = v.cpu().numpy().astype(np.float64)
+    a0 = _layer(net, REG_NET_INPUT, 0, (B, 2, H, H))
+    ref0 = bf16_round(cnn.restrict2(x.astype(np.float32).astype(np.float64)))
+    check("doubled-grid warm start: restricted images (BF16)", float(np.abs(a0 - ref0).max() / np.abs(ref0).max()),
+          1.01 * 2.0 ** -7)
+    raw = _layer(net, REG_NET_OUTPUT, 7, (B, 2, H, H))
+    ref_post = s * cnn.output_map(cnn.prolong2(cnn.output_map(raw)))
+    check("doubled-grid warm start: prolongation and fine output map", _rel(vg, ref_post), 1e-5)
+    check("doubled-grid warm start: end to end", _rel(vg, cnn.predict_fine(params, x, s)), 3e-2)
+    net.close()
