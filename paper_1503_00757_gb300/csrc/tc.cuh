@@ -3,7 +3,8 @@
 // tensor memory (TMEM), completion through an mbarrier, tcgen05.ld for the
 // epilogue, and TMA tensor loads (cp.async.bulk.tensor) that stage operands.
 // Only the forms the convolution kernels use are wrapped: cta_group::1,
-// kind::f16 with BF16 A and B, operands without swizzle.
+// kind::f16 with BF16 A and B, operands without swizzle or with the 64-byte
+// swizzle.
 //
 // Canonical layouts without swizzle: a core matrix is 8 rows of 16 bytes
 // stored as 128 contiguous bytes.  K-major: a row is one M (or N) index and
@@ -11,8 +12,14 @@
 // 16 set): a row is one K index and holds 8 consecutive M (or N) elements.
 // For both, the matrix descriptor gives the start address, LBO = byte step
 // between core matrices adjacent along K and SBO = byte step between core
-// matrices adjacent along M (or N) (checked on the device against an exact
-// small-integer product for both majors).
+// matrices adjacent along M (or N).
+// With the 64-byte swizzle rows are 64 bytes (32 BF16) in 8-row atoms of 512
+// bytes (desc_sw64).  K-major: SBO = 512 between atoms along M (or N), LBO
+// unused, a K = 16 slice starts 32 bytes into the rows.  MN-major: LBO = byte
+// step between 32-element M (or N) groups, SBO = 512 between 8-row K groups.
+// Each of these readings was checked once on the device against an exact
+// small-integer product, with buffers that held every address of either
+// reading.
 #pragma once
 #include <cstdint>
 
