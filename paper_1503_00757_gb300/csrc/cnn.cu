@@ -504,6 +504,21 @@ __global__ void __launch_bounds__(288) k_conv3x3_tc(const __grid_constant__ CUte
         uint4 fixv[G::NFIXK];
         int fixp[G::NFIXK];
         const int q = warp & 3, mt = warp >> 2;
+        // this thread's pixel of tile t and, for the input gradient, its ReLU mask (loaded one patch
+        // step before the epilogue that uses it)
+        auto pixel_of = [&](int t) {
+            const int b = t / tiles_per_img;
+            const TileMap tm = tile_map(t - b * tiles_per_img, H, W, dil);
+            return ((size_t)b * H + tm.gy(tm.Y0 + 4 * mt + q)) * W + tm.gx(tm.X0 + lane);
+        };
+        uint4 mpre[COUT / 8];
+        auto load_mask = [&](int t) {
+            if constexpr (MODE == 2) {
+                const uint4* mk = reinterpret_cast<const uint4*>(mask + pixel_of(t) * COUT);
+#pragma unroll
+                for (int j = 0; j < COUT / 8; ++j) mpre[j] = __ldg(mk + j);
+            }
+        };
         auto epilogue = [&](int t, int set) {
             const int b = t / tiles_per_img;
             const TileMap tm = tile_map(t - b * tiles_per_img, H, W, dil);
@@ -531,8 +546,7 @@ __global__ void __launch_bounds__(288) k_conv3x3_tc(const __grid_constant__ CUte
                 o[((size_t)b * 2 + 1) * plane + (size_t)y * W + x] = v[1] + s_bias[1];
             } else {
                 uint4* o = reinterpret_cast<uint4*>(reinterpret_cast<bf16*>(out) + pix * COUT);
-                const uint4* mk = MODE == 2 ? reinterpret_cast<const uint4*>(mask + pix * COUT) : nullptr;
-#pragma unroll
+    #pragma unroll
                 for (int j = 0; j < COUT / 8; ++j) {
                     float e[8];
 #pragma unroll
@@ -541,7 +555,7 @@ __global__ void __launch_bounds__(288) k_conv3x3_tc(const __grid_constant__ CUte
 #pragma unroll
                         for (int k = 0; k < 8; ++k) e[k] = fmaxf(e[k] + s_bias[8 * j + k], 0.f);
                     } else if (MODE == 2) {
-                        const uint4 m4 = __ldg(mk + j);
+                        const uint4 m4 = mpre[j];
                         const uint32_t mw[4] = {m4.x, m4.y, m4.z, m4.w};
 #pragma unroll
                         for (int k = 0; k < 8; ++k) {
@@ -564,6 +578,7 @@ __global__ void __launch_bounds__(288) k_conv3x3_tc(const __grid_constant__ CUte
             if (lane == 0) tc::mbar_arrive(&fixed[buf]);
             if (t + G0 < total) tc_load_fix<CIN>(in, t + G0, tiles_per_img, H, W, dil, fixv, fixp);
             if (i >= 1) {
+                load_mask(t - G0);
                 // tile i - 1: its MMAs have had the whole patch step of tile i to complete
                 if (!tc_wait(&done[(i - 1) & 1], ((i - 1) >> 1) & 1, abort, err)) break;
                 tc::fence_after();
@@ -574,6 +589,7 @@ __global__ void __launch_bounds__(288) k_conv3x3_tc(const __grid_constant__ CUte
             }
         }
         if (!*abort && i >= 1) {
+            load_mask(blockIdx.x + (i - 1) * G0);
             if (tc_wait(&done[(i - 1) & 1], ((i - 1) >> 1) & 1, abort, err)) {
                 tc::fence_after();
                 epilogue(blockIdx.x + (i - 1) * G0, (i - 1) & 1);
