@@ -85,3 +85,13 @@ def test_new_entry_points_reject_invalid_arguments_without_gpu(lib):
     assert lib.reg_set_tiles(None, 4, 2, 0) == 1
     assert lib.reg_net_set_output_scale(None, ctypes.c_float(1.0)) == 1
     assert lib.reg_set_pdl(None, 1) == 1
+
+
+def test_network_entry_points_reject_invalid_arguments_without_gpu(lib):
+    """The tensor-core network's entry points check their arguments before any CUDA call."""
+    f = ctypes.c_float()
+    assert lib.reg_net_set_conv_kernel(None, 1) == 1
+    assert lib.reg_net_set_record(None, 1) == 1
+    assert lib.reg_net_layer_tensor(None, 0, 0, 1, ctypes.byref(f)) == 1
+    assert lib.reg_net_forward_fine(None, ctypes.byref(f), 1, ctypes.byref(f)) == 1
+    assert b"NULL" in lib.reg_last_error()
