@@ -918,6 +918,98 @@ __global__ void __launch_bounds__(288) k_wgrad_tc(const __grid_constant__ CUtens
     if (warp == 8) tc::dealloc(tmem, G::TMEM_COLS);
 }
 
+// ---------------------------------------------------------------------------
+// weight and bias gradient of layer 0 (2 real input channels, stored padded to 16):
+// 18 products per pixel and output channel, far from a dense contraction, so CUDA
+// cores.  Thread (co, r) of a 32 x TH block keeps dW[co][tap][0..1] for all 9 taps
+// in registers and walks the TW pixels of tile row r: one dz load, nine broadcast
+// float2 halo loads and 18 FMAs per pixel.  Partials per CTA are summed over the
+// rows in a fixed order and written as [co][tap][2] and [co] (k_wgrad_reduce_l0).
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) k_wgrad_l0(const bf16* __restrict__ a, const bf16* __restrict__ dz,
+                                                  float* partial, float* bpartial, int H, int W, int B, int dil) {
+    constexpr int COUT = 32, CS = 16;  // output channels; stored input channels per pixel
+    __shared__ float2 s_a[(TH + 2) * (TW + 2)];
+    // dz of the tile, then (after the tile loop) the per-row partial sums
+    __shared__ float s_buf[TH * TW * (COUT + 1)];
+    float(*s_dz)[COUT + 1] = reinterpret_cast<float(*)[COUT + 1]>(s_buf);
+    float(*s_red)[COUT][19] = reinterpret_cast<float(*)[COUT][19]>(s_buf);
+    static_assert(TH * COUT * 19 <= TH * TW * (COUT + 1), "reduction fits the dz tile");
+    const int co = threadIdx.x & 31, r = threadIdx.x >> 5;
+    float acc[9][2], bacc = 0.f;
+#pragma unroll
+    for (int t = 0; t < 9; ++t) acc[t][0] = acc[t][1] = 0.f;
+    const int per_img = (H / TH) * (W / TW), tiles = per_img * B;
+    for (int ti = blockIdx.x; ti < tiles; ti += gridDim.x) {
+        const int b = ti / per_img;
+        const TileMap tm = tile_map(ti - b * per_img, H, W, dil);
+        __syncthreads();
+        for (int i = threadIdx.x; i < (TH + 2) * (TW + 2); i += blockDim.x) {
+            const int hy = i / (TW + 2), hx = i - hy * (TW + 2);
+            const int gy = tm.gy(tm.Y0 + hy - 1 + tm.Hs), gx = tm.gx(tm.X0 + hx - 1 + tm.Ws);
+            const __nv_bfloat162 v = *reinterpret_cast<const __nv_bfloat162*>(a + (((size_t)b * H + gy) * W + gx) * CS);
+            s_a[i] = make_float2(__bfloat162float(v.x), __bfloat162float(v.y));
+        }
+        for (int i = threadIdx.x; i < TH * TW * COUT / 8; i += blockDim.x) {
+            const int p = i / (COUT / 8), c8 = i - p * (COUT / 8);
+            const size_t pix = ((size_t)b * H + tm.gy(tm.Y0 + p / TW)) * W + tm.gx(tm.X0 + (p % TW));
+            const uint4 v = __ldg(reinterpret_cast<const uint4*>(dz + pix * COUT) + c8);
+            const uint32_t w4[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                s_dz[p][8 * c8 + 2 * k] = __uint_as_float(w4[k] << 16);
+                s_dz[p][8 * c8 + 2 * k + 1] = __uint_as_float(w4[k] & 0xFFFF0000u);
+            }
+        }
+        __syncthreads();
+#pragma unroll 4
+        for (int x = 0; x < TW; ++x) {
+            const float d = s_dz[r * TW + x][co];
+            bacc += d;
+#pragma unroll
+            for (int dy = 0; dy < 3; ++dy)
+#pragma unroll
+                for (int dx = 0; dx < 3; ++dx) {
+                    const float2 av = s_a[(r + dy) * (TW + 2) + x + dx];
+                    acc[3 * dy + dx][0] = fmaf(d, av.x, acc[3 * dy + dx][0]);
+                    acc[3 * dy + dx][1] = fmaf(d, av.y, acc[3 * dy + dx][1]);
+                }
+        }
+    }
+    __syncthreads();  // every thread is done with the last dz tile
+#pragma unroll
+    for (int t = 0; t < 9; ++t) {
+        s_red[r][co][2 * t] = acc[t][0];
+        s_red[r][co][2 * t + 1] = acc[t][1];
+    }
+    s_red[r][co][18] = bacc;
+    __syncthreads();
+    for (int i = threadIdx.x; i < COUT * 19; i += blockDim.x) {
+        const int c = i / 19, k = i - c * 19;
+        float v = 0.f;
+        for (int rr = 0; rr < TH; ++rr) v += s_red[rr][c][k];
+        if (k < 18) partial[(size_t)blockIdx.x * COUT * 18 + c * 18 + k] = v;
+        else bpartial[(size_t)blockIdx.x * COUT + c] = v;
+    }
+}
+
+// layer 0's partials [part][co][tap][2] -> gW [co][tap][16] (channels 2..15 stay zero), gb [co]
+__global__ void k_wgrad_reduce_l0(const float* __restrict__ partial, const float* __restrict__ bpartial, int nparts,
+                                  float* gW, float* gb) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < 32 * 18) {
+        float v = 0.f;
+        for (int p = 0; p < nparts; ++p) v += partial[(size_t)p * 32 * 18 + i];
+        const int co = i / 18, k = i - co * 18, tap = k >> 1, ci = k & 1;
+        gW[(co * 9 + tap) * 16 + ci] = v;
+    } else if (i < 32 * 18 + 32) {
+        const int c = i - 32 * 18;
+        float v = 0.f;
+        for (int p = 0; p < nparts; ++p) v += bpartial[(size_t)p * 32 + c];
+        gb[c] = v;
+    }
+}
+
 // images (fp32 planar [B][2][H][W]) -> NHWC bf16 with 16 channels (2 real)
 __global__ void k_pack_input(const float* __restrict__ img, bf16* x, int B, int H, int W) {
     const size_t n = (size_t)B * H * W;
@@ -1418,12 +1510,17 @@ static int net_loss_grad(reg_net* n, const float* images, const float* targets, 
             k_wgrad<32, 16><<<n->nwg, 288, wgrad_smem(32, 16), n->stream>>>(n->act[l], dz, n->partial, n->bpartial, H, W, B, d);
         } else if (l > 0) {
             k_wgrad<32, 32><<<n->nwg, 288, wgrad_smem(32, 32), n->stream>>>(n->act[l], dz, n->partial, n->bpartial, H, W, B, d);
+        } else if (n->conv_kind == REG_CONV_TCGEN05) {
+            // layer 0 (2 real input channels): CUDA-core kernel, its own partial layout
+            k_wgrad_l0<<<n->nwg, 256, 0, n->stream>>>(n->act[0], dz, n->partial, n->bpartial, H, W, B, d);
+            k_wgrad_reduce_l0<<<3, 256, 0, n->stream>>>(n->partial, n->bpartial, n->nwg, gWl, gbl);
+            nparts = 0;
         } else {
-            // layer 0 (2 real input channels padded to 16) keeps the mma.sync kernel on either path
             k_wgrad<16, 32><<<n->nwg, 288, wgrad_smem(16, 32), n->stream>>>(n->act[0], dz, n->partial, n->bpartial, H, W, B, d);
         }
         const int nw = L.coutp * 9 * L.cinp, nb = L.coutp;
-        k_wgrad_reduce<<<(nw + nb + 31) / 32, 256, 0, n->stream>>>(n->partial, n->bpartial, nparts, nw, nb, gWl, gbl);
+        if (nparts > 0)
+            k_wgrad_reduce<<<(nw + nb + 31) / 32, 256, 0, n->stream>>>(n->partial, n->bpartial, nparts, nw, nb, gWl, gbl);
         if (l > 0) {
             // input gradient through the ReLU of layer l-1: correlation with the flipped, transposed kernel
             const bf16* wtl = n->wt + n->wfoff[l];
