@@ -477,6 +477,8 @@ def main():
     ap.add_argument("--matvecs", type=int, default=200)
     ap.add_argument("--no-warm", dest="warm", action="store_false",
                     help="skip the warm-start comparison")
+    ap.add_argument("--no-vol", dest="vol", action="store_false",
+                    help="skip the three-dimensional gradient and matvec measurement (128^3, nt=16)")
     ap.add_argument("--no-big", dest="big", action="store_false",
                     help="skip the 1024^2 matvec measurement")
     ap.add_argument("--no-shear", dest="shear", action="store_false",
@@ -790,6 +792,47 @@ def main():
             ctxb.close()
             big["kernel_classes"] = {str(k): {"launches": bcls[k][0], "ms": bcls[k][1], "GB": bcls[k][2] / 1e9}
                                      for k in bcls}
+        # three-dimensional problem: gradient and Gauss-Newton matvecs at 128^3, nt=16 (H1, div v = 0)
+        vol = None
+        if args.vol:
+            from paper_1503_00757_gb300.binding import Context3D
+            n3, nt3 = 128, 16
+            xs = 2.0 * np.pi * np.arange(n3) / n3
+            X1, X2, X3 = np.meshgrid(xs, xs, xs, indexing="ij")
+            bump = lambda a, b, c: np.exp(-4.0 * (np.sin((X1 - a) / 2) ** 2 + np.sin((X2 - b) / 2) ** 2 +
+                                                  np.sin((X3 - c) / 2) ** 2))
+            f3 = lambda a: torch.from_numpy(np.ascontiguousarray(a, dtype=np.float32)).to(dev)
+            c3 = Context3D(n3, n3, n3, nt3, beta=1e-2, gamma=math.inf, stream=stream)
+            c3.set_images(f3(bump(3.0, 3.1, 2.9)), f3(bump(3.25, 2.9, 3.2)))
+            v3 = f3(0.2 * np.stack([np.sin(X2 + X3), np.cos(X1) * np.sin(X3), np.sin(X1 - X2)]))
+            vt3 = f3(0.1 * np.stack([np.cos(X3), np.sin(X1 + X3), np.cos(X2)]))
+            g3_, H3_ = torch.empty_like(v3), torch.empty_like(v3)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            c3.gradient(v3, g3_)
+            torch.cuda.synchronize()
+            e0.record(stream)
+            c3.gradient(v3, g3_)
+            e1.record(stream)
+            e1.synchronize()
+            ms_g3 = e0.elapsed_time(e1)
+            c3.hessian_matvec(vt3, H3_)
+            torch.cuda.synchronize()
+            nmv3 = 5
+            e0.record(stream)
+            for _ in range(nmv3):
+                c3.hessian_matvec(vt3, H3_)
+            e1.record(stream)
+            e1.synchronize()
+            ms_mv3 = e0.elapsed_time(e1) / nmv3
+            c3.close()
+            # streaming model: the gradient history (3 floats per point and time level) read twice,
+            # v and v~ read, H v~ and b~ written once
+            b3 = (24 * (nt3 + 1) + 48) * n3 ** 3
+            pk3, _ = peaks()
+            vol = {"workload": "128^3 periodic box, nt=16, H1, beta_v=1e-2, div v = 0 (reg3_*)",
+                   "ms_per_gradient": ms_g3, "ms_per_matvec": ms_mv3, "matvec_per_s": 1e3 / ms_mv3,
+                   "roofline_streaming": {"bytes_per_matvec": b3, "GB/s": b3 / ms_mv3 / 1e6,
+                                          "frac_hbm": b3 / ms_mv3 / 1e6 / pk3}}
         # learned warm start vs plain zero start (256^2, nt=16, held-out pairs) with the committed weights
         warm = None
         wpath = os.path.join(ROOT, "paper_1503_00757_gb300", "weights", "warmstart_n256.npy")
@@ -922,6 +965,7 @@ def main():
                                  "peak": peak,
                                  "frac": stream_bytes(1024, 1024, NT) / big["ms_per_matvec"] / 1e6 / peak},
                              "kernel_classes": big["kernel_classes"]} if big else None),
+            "matvec_3d": vol,
             "ceilings": {"fp32_tflops_measured": fp32_tf, "hbm_gbs": peak,
                          "matvec_512": matvec_models(N_GRID, N_GRID, NT, mv_ms, peak, fp32_tf),
                          "matvec_512_concurrent": matvec_models(N_GRID, N_GRID, NT, mv_conc["ms_per_matvec"], peak,

@@ -464,6 +464,32 @@ int reg_net_layer_tensor(reg_net* net, int kind, int layer, int B, float* out);
  * Asynchronous; returns REG_OK, REG_ERR_ARG or REG_ERR_CUDA. */
 int reg_spectral_grad_static(reg_grid grid, const float* f, float* grad_f, void* stream);
 
+/* ---- three-dimensional problems (the paper's Sec. 3 equations for d = 3) ---- */
+
+/* One 3-D registration problem on the periodic box [0, 2 pi)^3 with the H1 seminorm
+ * (A = -Lap), Heun's RK2 with nt steps and the trapezoidal rule in pseudo-time, as in 2-D.
+ * n1, n2, n3: powers of two in [8, 256]; beta = beta_v > 0; gamma = beta_w: 0 (no
+ * constraint), INFINITY (div v = 0), else the mass-source weight.  Real fields are
+ * n1 x n2 x n3 floats, index (i1 n2 + i2) n3 + i3; vector fields (v, g, v~, H v~) are three
+ * such fields back to back.  All pointers are device pointers owned by the caller.
+ * Memory: about (3 nt + 30) n1 n2 n3 floats (the gradient history of the state is kept for
+ * the matvecs).  Not thread-safe per context; calls run on the context's stream. */
+typedef struct reg3_ctx reg3_ctx;
+int reg3_create(int n1, int n2, int n3, int nt, double beta, double gamma, reg3_ctx** out);
+void reg3_destroy(reg3_ctx* ctx);
+int reg3_set_stream(reg3_ctx* ctx, void* stream);
+/* Copies the template m_T and reference m_R in. */
+int reg3_set_images(reg3_ctx* ctx, const float* mT, const float* mR);
+/* Reduced gradient g = beta_v A v + K b (Eq. (e:control-eq-elim), b the body force of the
+ * state and adjoint solves) and, if J is not NULL, the objective (host double; synchronous).
+ * Fixes the linearization point of reg3_hessian_matvec.  REG_ERR_STATE before
+ * reg3_set_images; REG_ERR_NAN if J is not finite. */
+int reg3_gradient(reg3_ctx* ctx, const float* v, float* g, double* J);
+/* Gauss-Newton matvec H v~ = beta_v A v~ + K b~ (Eqs. (e:inc-state-eq-elim),
+ * (e:inc-adj-eq-elim), (e:inc-control-eq-elim)) at the v of the last reg3_gradient
+ * (REG_ERR_STATE before one).  Asynchronous. */
+int reg3_hessian_matvec(reg3_ctx* ctx, const float* vt, float* Hvt);
+
 /* ---- instrumentation ---- */
 
 /* Per-kernel-class CUDA-event timing (off by default).  While enabled, every

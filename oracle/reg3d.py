@@ -1,7 +1,7 @@
 """Three-dimensional registration operators (oracle; test infrastructure only).
 
 The paper states its method for d = 2 and names the three-dimensional case as the next step
-(Sec. 6); the equations of Sec. 3 are written for a general dimension d, so this module takes
+(Conclusions); the equations of Sec. 3 are written for a general dimension d, so this module takes
 them over unchanged for d = 3 on the periodic box [0, 2 pi)^3 with the H1 seminorm:
 
   * state, Eq. (e:state-eq-elim): d_t m + grad m . v = 0, m(0) = m_T;

@@ -102,6 +102,12 @@ _SIGS = {
     "reg_net_set_output_scale": ([_P, ctypes.c_float], _I),
     "reg_net_loss_grad": ([_P, _P, _P, _I, ctypes.POINTER(_D), _P], _I),
     "reg_net_train_step": ([_P, _P, _P, _I, ctypes.c_float, ctypes.POINTER(_D)], _I),
+    "reg3_create": ([_I, _I, _I, _I, _D, _D, ctypes.POINTER(_P)], _I),
+    "reg3_destroy": ([_P], None),
+    "reg3_set_stream": ([_P, _P], _I),
+    "reg3_set_images": ([_P, _P, _P], _I),
+    "reg3_gradient": ([_P, _P, _P, ctypes.POINTER(_D)], _I),
+    "reg3_hessian_matvec": ([_P, _P, _P], _I),
     "reg_net_forward_fine": ([_P, _P, _I, _P], _I),
     "reg_net_set_conv_kernel": ([_P, _I], _I),
     "reg_net_set_record": ([_P, _I], _I),
@@ -327,6 +333,39 @@ class Net:
     def layer_tensor(self, kind, layer, out):
         """Layer tensor of the last pass into out (device, B x C x H x W floats)."""
         _check(lib().reg_net_layer_tensor(self.h, int(kind), int(layer), out.shape[0], _ptr(out, out.numel(), "out")))
+
+
+class Context3D:
+    """One 3-D registration problem (reg3_*): H1 seminorm on an n1 x n2 x n3 periodic box."""
+
+    def __init__(self, n1, n2, n3, nt, beta=1e-2, gamma=math.inf, stream=None):
+        h = ctypes.c_void_p()
+        _check(lib().reg3_create(n1, n2, n3, nt, float(beta), float(gamma), ctypes.byref(h)))
+        self.h, self.N = h, n1 * n2 * n3
+        if stream is not None:
+            _check(lib().reg3_set_stream(h, ctypes.c_void_p(stream.cuda_stream)))
+
+    def close(self):
+        if self.h:
+            lib().reg3_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_images(self, mT, mR):
+        _check(lib().reg3_set_images(self.h, _ptr(mT, self.N, "mT"), _ptr(mR, self.N, "mR")))
+
+    def gradient(self, v, g_out):
+        J = ctypes.c_double()
+        _check(lib().reg3_gradient(self.h, _ptr(v, 3 * self.N, "v"), _ptr(g_out, 3 * self.N, "g"), ctypes.byref(J)))
+        return J.value
+
+    def hessian_matvec(self, vt, Hvt_out):
+        _check(lib().reg3_hessian_matvec(self.h, _ptr(vt, 3 * self.N, "vt"), _ptr(Hvt_out, 3 * self.N, "Hvt")))
 
 
 def flatten_params(params):

@@ -14,7 +14,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_lib")
 LIB_PATH = os.path.join(OUT_DIR, "libreg.so")
-SOURCES = ["kernels.cu", "transport_cluster.cu", "api.cu", "batch.cu", "cnn.cu", "noalloc.cu", "tune.cu", "peak.cu"]
+SOURCES = ["kernels.cu", "transport_cluster.cu", "api.cu", "batch.cu", "cnn.cu", "noalloc.cu", "tune.cu", "peak.cu", "reg3d.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
          "-I", os.path.join(ROOT, "include")]
