@@ -12,7 +12,9 @@
 // order.  A 3-D transform is three passes of batched 1-D radix-2 Stockham FFTs
 // (k3_fft_pass), one per axis: a CTA stages a tile of 32 lines in shared memory (loads
 // coalesced along the contiguous direction), runs the log2(L) butterfly stages between
-// two shared buffers and writes the tile back in natural order.
+// two shared buffers (row stride padded by one element against bank conflicts; twiddles
+// from a per-CTA table built once from exact fractions) and writes the tile back in
+// natural order.
 #include <cuda_runtime.h>
 
 #include <cmath>
@@ -36,36 +38,42 @@ struct LineMap {
 template <bool INV>
 __global__ void __launch_bounds__(R3_THREADS) k3_fft_pass(float2* __restrict__ data, LineMap m) {
     extern __shared__ float2 sbuf[];
+    const int TWL = m.TWL, L = m.L, SP = m.TWL + 1;  // padded stride: line elements fall in distinct banks
     float2* b0 = sbuf;
-    float2* b1 = sbuf + m.L * m.TWL;
-    const int TWL = m.TWL, L = m.L;
+    float2* b1 = sbuf + L * SP;
+    float2* tw = sbuf + 2 * L * SP;  // tw[k] = exp(-2 pi i k / L), k < L / 2
     const int tile = blockIdx.x;
     auto base = [&](int w) {
         const long long l = (long long)tile * TWL + w;
         return (l / m.Q) * (long long)m.P + (l % m.Q) * (long long)m.R;
     };
-    // stage the tile: b0[p TWL + w] = element p of line w (the contiguous direction fastest)
+    for (int k = threadIdx.x; k < L / 2; k += blockDim.x) {
+        float sn, cs;
+        sincospif(2.f * (float)k / (float)L, &sn, &cs);
+        tw[k] = make_float2(cs, -sn);
+    }
+    // stage the tile: b0[p SP + w] = element p of line w (the contiguous direction fastest)
     for (int e = threadIdx.x; e < L * TWL; e += blockDim.x) {
         int p, w;
         if (m.S == 1) { p = e % L; w = e / L; } else { w = e % TWL; p = e / TWL; }
-        b0[p * TWL + w] = data[base(w) + (long long)p * m.S];
+        b0[p * SP + w] = data[base(w) + (long long)p * m.S];
     }
     __syncthreads();
     float2* src = b0;
     float2* dst = b1;
     for (int Ns = 1; Ns < L; Ns <<= 1) {
+        const int step = L / (2 * Ns);  // exp(-i pi k / Ns) = tw[k step]
         for (int e = threadIdx.x; e < (L / 2) * TWL; e += blockDim.x) {
             const int w = e % TWL, j = e / TWL;
             const int k = j & (Ns - 1);
-            const float2 a = src[j * TWL + w];
-            const float2 c = src[(j + L / 2) * TWL + w];
-            float sn, cs;
-            sincospif((float)k / (float)Ns, &sn, &cs);  // angle pi k / Ns
-            const float ws = INV ? sn : -sn;
-            const float2 t = make_float2(c.x * cs - c.y * ws, c.x * ws + c.y * cs);
+            const float2 a = src[j * SP + w];
+            const float2 c = src[(j + L / 2) * SP + w];
+            const float2 t0 = tw[k * step];
+            const float ws = INV ? -t0.y : t0.y;
+            const float2 t = make_float2(c.x * t0.x - c.y * ws, c.x * ws + c.y * t0.x);
             const int d = (j / Ns) * 2 * Ns + k;
-            dst[d * TWL + w] = make_float2(a.x + t.x, a.y + t.y);
-            dst[(d + Ns) * TWL + w] = make_float2(a.x - t.x, a.y - t.y);
+            dst[d * SP + w] = make_float2(a.x + t.x, a.y + t.y);
+            dst[(d + Ns) * SP + w] = make_float2(a.x - t.x, a.y - t.y);
         }
         __syncthreads();
         float2* tmp = src;
@@ -75,7 +83,7 @@ __global__ void __launch_bounds__(R3_THREADS) k3_fft_pass(float2* __restrict__ d
     for (int e = threadIdx.x; e < L * TWL; e += blockDim.x) {
         int p, w;
         if (m.S == 1) { p = e % L; w = e / L; } else { w = e % TWL; p = e / TWL; }
-        data[base(w) + (long long)p * m.S] = src[p * TWL + w];
+        data[base(w) + (long long)p * m.S] = src[p * SP + w];
     }
 }
 
@@ -301,7 +309,7 @@ LineMap line_map(const Dims3& D, int axis) {
     return m;
 }
 
-size_t pass_smem(const LineMap& m) { return (size_t)2 * m.L * m.TWL * sizeof(float2); }
+size_t pass_smem(const LineMap& m) { return ((size_t)2 * m.L * (m.TWL + 1) + m.L / 2) * sizeof(float2); }
 
 // in-place 3-D transform of `count` consecutive spectra
 void fft3(reg3_ctx* c, float2* X, int count, bool inverse) {

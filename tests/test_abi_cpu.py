@@ -95,3 +95,17 @@ def test_network_entry_points_reject_invalid_arguments_without_gpu(lib):
     assert lib.reg_net_layer_tensor(None, 0, 0, 1, ctypes.byref(f)) == 1
     assert lib.reg_net_forward_fine(None, ctypes.byref(f), 1, ctypes.byref(f)) == 1
     assert b"NULL" in lib.reg_last_error()
+
+
+def test_3d_entry_points_reject_invalid_arguments_without_gpu(lib):
+    """reg3_* validate sizes and pointers before any CUDA call."""
+    h = ctypes.c_void_p()
+    inf = float("inf")
+    assert lib.reg3_create(12, 16, 16, 4, 1e-2, inf, ctypes.byref(h)) == 1   # not a power of two
+    assert lib.reg3_create(16, 16, 512, 4, 1e-2, inf, ctypes.byref(h)) == 1  # axis above 256
+    assert lib.reg3_create(16, 16, 16, 0, 1e-2, inf, ctypes.byref(h)) == 1   # nt
+    assert lib.reg3_create(16, 16, 16, 4, 0.0, inf, ctypes.byref(h)) == 1    # beta
+    assert lib.reg3_create(16, 16, 16, 4, 1e-2, -1.0, ctypes.byref(h)) == 1  # gamma
+    assert lib.reg3_gradient(None, None, None, None) == 1
+    assert lib.reg3_hessian_matvec(None, None, None) == 1
+    assert lib.reg3_set_images(None, None, None) == 1
