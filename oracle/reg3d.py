@@ -24,6 +24,8 @@ the Nyquist entry set to zero for grad and div, the full even symbol |k|^2 for A
 the trapezoidal inner product h1 h2 h3 sum.  The own radix-2 FFT of ``oracle.fft`` runs along
 each of the three axes.
 """
+import math
+
 import numpy as np
 
 from .fft import fft
@@ -193,3 +195,75 @@ class Registration3D:
         bt = body_force(lt, self.gm)
         self.bt = bt
         return self.beta_v * apply_A(vt) + apply_K(bt, self.beta_v, self.beta_w)
+
+
+def apply_precond(r, beta_v):
+    """(beta_v A)^-1 r with the k = 0 symbol of A replaced by 1 (App. E, as in 2-D)."""
+    _, _, _, KK = symbols(r.shape[-3:])
+    sym = beta_v * np.where(KK > 0.0, KK, 1.0)
+    return np.stack([np.real(ifftn3(fftn3(r[c]) / sym)) for c in range(3)])
+
+
+def _pcg(P, g, eta, maxit):
+    """Algorithm 2 with the spectral preconditioner: (v~, iterations)."""
+    vt = np.zeros_like(g)
+    r = -g
+    z = apply_precond(r, P.beta_v)
+    s = z.copy()
+    rz = inner(r, z)
+    gnorm = norm(g)
+    it = 0
+    for _ in range(maxit):
+        Hs = P.matvec(s)
+        it += 1
+        sHs = inner(s, Hs)
+        if sHs <= 0.0:
+            if it == 1:
+                vt = s.copy()
+            break
+        kappa = rz / sHs
+        vt = vt + kappa * s
+        r = r - kappa * Hs
+        if norm(r) < eta * gnorm:
+            break
+        z = apply_precond(r, P.beta_v)
+        rz_new = inner(z, r)
+        s = z + (rz_new / rz) * s
+        rz = rz_new
+    return vt, it
+
+
+def solve(P, tol=1e-2, maxit_newton=50, maxit_pcg=100, c1=1e-4, rho=0.5, max_ls=20):
+    """Algorithm 1 from v = 0 (inexact Gauss-Newton-Krylov with Armijo backtracking, forcing
+    eta_k = min(0.5, sqrt(||g_k|| / ||g_0||)), stop at ||g|| <= tol ||g_0||), the same steps as
+    the two-dimensional oracle's solve.  Returns (v, stats)."""
+    v = np.zeros((3,) + P.mT.shape)
+    g, J = P.gradient(v)
+    g0 = gnorm = norm(g)
+    stats = dict(n_newton=0, n_mv=0, n_ls=0, status=0, J0=J)
+    while g0 > 0.0 and gnorm / g0 > tol:
+        if stats["n_newton"] >= maxit_newton:
+            stats["status"] = 10
+            break
+        vt, it = _pcg(P, g, min(0.5, math.sqrt(gnorm / g0)), maxit_pcg)
+        stats["n_mv"] += it
+        gv = inner(g, vt)
+        if gv >= 0.0:
+            vt = -apply_precond(g, P.beta_v)
+            gv = inner(g, vt)
+        alpha, accepted = 1.0, False
+        for _ in range(max_ls):
+            stats["n_ls"] += 1
+            if P.objective(v + alpha * vt)[0] <= J + c1 * alpha * gv:
+                accepted = True
+                break
+            alpha *= rho
+        if not accepted:
+            stats["status"] = 5
+            break
+        v = v + alpha * vt
+        stats["n_newton"] += 1
+        g, J = P.gradient(v)
+        gnorm = norm(g)
+    stats.update(J=J, gnorm_rel=gnorm / g0 if g0 > 0 else 0.0)
+    return v, stats

@@ -124,3 +124,37 @@ def test_gradient_matches_finite_differences_second_order(beta_w):
         errs.append(abs(R.inner(g, d) - fd) / abs(fd))
     assert errs[-1] < 2e-3
     assert 3.0 < errs[0] / errs[1] < 5.0 and 3.0 < errs[1] / errs[2] < 5.0
+
+
+def test_precond_inverts_beta_A_off_the_zero_mode():
+    rng = np.random.default_rng(5)
+    r = rng.standard_normal((3, 8, 16, 8))
+    r -= r.mean(axis=(1, 2, 3), keepdims=True)
+    assert np.abs(1e-2 * R.apply_A(R.apply_precond(r, 1e-2)) - r).max() < 1e-10 * np.abs(r).max()
+    c = np.ones((3, 8, 16, 8))
+    assert np.abs(R.apply_precond(c, 1e-2) - 100.0 * c).max() < 1e-9
+
+
+def test_solve_reduces_to_the_2d_solve():
+    """Fields constant along x3: the 3-D Algorithm 1 takes the 2-D oracle's Newton and PCG
+    steps (same counts) and returns its velocity in components 1, 2 (zero in component 3)."""
+    n, n3, nt = 16, 4, 4
+    X1, X2 = S2.grid_coords(n, n)
+    mT2 = np.exp(-((X1 - 3.0) ** 2 + (X2 - 3.2) ** 2))
+    mR2 = np.exp(-((X1 - 3.4) ** 2 + (X2 - 2.9) ** 2) / 1.2)
+    lift = lambda f: np.repeat(f[..., None], n3, axis=-1)
+    P2 = Registration(mT2, mR2, nt, regnorm=S2.H1, beta_v=1e-2, beta_w=math.inf)
+    v2, st2 = P2.solve(tol=1e-3)
+    P3 = R.Registration3D(lift(mT2), lift(mR2), nt, 1e-2, math.inf)
+    v3, st3 = R.solve(P3, tol=1e-3)
+    assert st3["status"] == 0 and st2["status"] == 0
+    assert (st3["n_newton"], st3["n_mv"]) == (st2["n_newton"], st2["n_mv"])
+    assert np.abs(v3[:2] - np.stack([lift(v2[0]), lift(v2[1])])).max() < 1e-9 * np.abs(v2).max()
+    assert np.abs(v3[2]).max() < 1e-12
+
+
+def test_solve_3d_converges_divergence_free():
+    P, _, _ = _problem3d(4)
+    v, st = R.solve(P, tol=1e-2)
+    assert st["status"] == 0 and st["gnorm_rel"] <= 1e-2 and st["J"] < st["J0"]
+    assert np.abs(R.div(v)).max() < 1e-10 * max(np.abs(v).max(), 1e-30)
