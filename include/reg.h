@@ -489,6 +489,16 @@ int reg3_gradient(reg3_ctx* ctx, const float* v, float* g, double* J);
  * (e:inc-adj-eq-elim), (e:inc-control-eq-elim)) at the v of the last reg3_gradient
  * (REG_ERR_STATE before one).  Asynchronous. */
 int reg3_hessian_matvec(reg3_ctx* ctx, const float* vt, float* Hvt);
+/* Algorithm 1 from v = 0 (v: device, overwritten with the result): inexact Gauss-Newton-Krylov
+ * with Algorithm 2's PCG and the spectral preconditioner (beta_v A)^-1 (k = 0 symbol 1),
+ * forcing eta_k = min(0.5, sqrt(||g_k|| / ||g_0||)), Armijo backtracking (c1 = 1e-4, halving,
+ * 20 trials), stop at ||g|| <= tol ||g(0)||; at most maxit_newton Newton and maxit_pcg PCG
+ * iterations.  stats (host, nullable, 7 doubles): Newton iterations, matvecs, line-search
+ * trials, ||g|| / ||g(0)||, J, status, J(0) (filled on every return).  A trial whose J is
+ * not finite (a step beyond the explicit scheme's stability) is rejected like one that fails
+ * the decrease test.  Synchronous.  REG_ERR_LINESEARCH / REG_ERR_MAXIT when the search fails /
+ * the cap is reached (v holds the last iterate). */
+int reg3_solve(reg3_ctx* ctx, float* v, double tol, int maxit_newton, int maxit_pcg, double* stats);
 
 /* ---- instrumentation ---- */
 

@@ -108,6 +108,7 @@ _SIGS = {
     "reg3_set_images": ([_P, _P, _P], _I),
     "reg3_gradient": ([_P, _P, _P, ctypes.POINTER(_D)], _I),
     "reg3_hessian_matvec": ([_P, _P, _P], _I),
+    "reg3_solve": ([_P, _P, _D, _I, _I, _P], _I),
     "reg_net_forward_fine": ([_P, _P, _I, _P], _I),
     "reg_net_set_conv_kernel": ([_P, _I], _I),
     "reg_net_set_record": ([_P, _I], _I),
@@ -366,6 +367,20 @@ class Context3D:
 
     def hessian_matvec(self, vt, Hvt_out):
         _check(lib().reg3_hessian_matvec(self.h, _ptr(vt, 3 * self.N, "vt"), _ptr(Hvt_out, 3 * self.N, "Hvt")))
+
+    def solve(self, v_out, tol=1e-2, maxit_newton=50, maxit_pcg=100, check=True):
+        """Algorithm 1 from v = 0 into v_out; returns the stats as a dict."""
+        st = (ctypes.c_double * 7)()
+        rc = lib().reg3_solve(self.h, _ptr(v_out, 3 * self.N, "v"), float(tol), int(maxit_newton), int(maxit_pcg),
+                              ctypes.cast(st, ctypes.c_void_p))
+        if check:
+            _check(rc)
+        keys = ("n_newton", "n_mv", "n_ls", "gnorm_rel", "J", "status", "J0")
+        d = {k: st[i] for i, k in enumerate(keys)}
+        for k in ("n_newton", "n_mv", "n_ls", "status"):
+            d[k] = int(d[k])
+        d["rc"] = rc
+        return d
 
 
 def flatten_params(params):

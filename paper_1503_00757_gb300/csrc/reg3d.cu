@@ -277,6 +277,44 @@ __global__ void k3_reduce(const double* __restrict__ part, int nblk, double* out
     }
 }
 
+// per-block FP64 partial sums of sum_i a_i b_i (fixed-order reduction by k3_reduce)
+__global__ void __launch_bounds__(R3_THREADS) k3_dot_part(const float* __restrict__ a, const float* __restrict__ b,
+                                                          long long n, double* part) {
+    __shared__ double sh[R3_THREADS];
+    double t = 0.0;
+    GRID_STRIDE(i, n) t += (double)a[i] * (double)b[i];
+    sh[threadIdx.x] = t;
+    __syncthreads();
+    for (int o = R3_THREADS / 2; o > 0; o >>= 1) {
+        if (threadIdx.x < o) sh[threadIdx.x] += sh[threadIdx.x + o];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        part[blockIdx.x * 3] = sh[0];
+        part[blockIdx.x * 3 + 1] = 0.0;
+        part[blockIdx.x * 3 + 2] = 0.0;
+    }
+}
+
+// y = a x + b y
+__global__ void k3_axpby(const float* x, float* y, long long n, float a, float b) {  // x may be y
+    GRID_STRIDE(i, n) y[i] = a * x[i] + b * y[i];
+}
+
+// (beta A)^-1 on three spectra, the k = 0 symbol of A replaced by 1 (App. E)
+__global__ void k3_precond_spec(float2* X, Dims3 D, float beta) {
+    GRID_STRIDE(i, D.N) {
+        float k1, k2, k3, kk;
+        wave3(D, i, k1, k2, k3, kk);
+        const float s = 1.f / (beta * (kk > 0.f ? kk : 1.f));
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+            const float2 x = X[d * D.N + i];
+            X[d * D.N + i] = make_float2(x.x * s, x.y * s);
+        }
+    }
+}
+
 }  // namespace
 
 struct reg3_ctx {
@@ -515,4 +553,147 @@ extern "C" int reg3_hessian_matvec(reg3_ctx* c, const float* vt, float* Hvt) {
     // the assembly transforms x into g3 in place: give it vt from the caller's buffer
     assemble(c, vt, c->bt, Hvt);
     return r3_err("reg3_hessian_matvec");
+}
+
+namespace {
+
+// <a, b> on the grid (trapezoidal weight (2 pi)^3 / N) over 3 N values; synchronous
+double inner3(reg3_ctx* c, const float* a, const float* b) {
+    k3_dot_part<<<R3_BLOCKS, R3_THREADS, 0, c->stream>>>(a, b, 3 * c->D.N, c->d_part);
+    k3_reduce<<<1, 32, 0, c->stream>>>(c->d_part, R3_BLOCKS, c->d_sum);
+    cudaMemcpyAsync(c->h_sum, c->d_sum, sizeof(double), cudaMemcpyDeviceToHost, c->stream);
+    cudaStreamSynchronize(c->stream);
+    return std::pow(2.0 * M_PI, 3) / (double)c->D.N * c->h_sum[0];
+}
+
+void precond3(reg3_ctx* c, const float* r, float* out) {
+    const long long N = c->D.N;
+    k3_real2c<<<R3_BLOCKS, R3_THREADS, 0, c->stream>>>(r, c->G, 3 * N);
+    fft3(c, c->G, 3, false);
+    k3_precond_spec<<<R3_BLOCKS, R3_THREADS, 0, c->stream>>>(c->G, c->D, (float)c->beta);
+    fft3(c, c->G, 3, true);
+    k3_c2real<<<R3_BLOCKS, R3_THREADS, 0, c->stream>>>(c->G, out, 3 * N, 1.f / (float)N);
+}
+
+// J at x (one state solve; the gradient history is overwritten, which Algorithm 1 allows:
+// the next gradient evaluation rebuilds it at the accepted point)
+double objective3(reg3_ctx* c, const float* x) {
+    const long long N = c->D.N;
+    cudaMemcpyAsync(c->v, x, sizeof(float) * 3 * N, cudaMemcpyDeviceToDevice, c->stream);
+    forward_solve(c, c->mT, nullptr);
+    float2* X = reinterpret_cast<float2*>(c->g3);
+    k3_real2c<<<R3_BLOCKS, R3_THREADS, 0, c->stream>>>(x, X, 3 * N);
+    fft3(c, X, 3, false);
+    k3_energy_part<<<R3_BLOCKS, R3_THREADS, 0, c->stream>>>(c->mR, c->y, X, c->D, c->d_part);
+    k3_reduce<<<1, 32, 0, c->stream>>>(c->d_part, R3_BLOCKS, c->d_sum);
+    cudaMemcpyAsync(c->h_sum, c->d_sum, sizeof(double) * 3, cudaMemcpyDeviceToHost, c->stream);
+    cudaStreamSynchronize(c->stream);
+    const double hv = std::pow(2.0 * M_PI, 3) / (double)N;
+    double J = 0.5 * hv * c->h_sum[0] + 0.5 * c->beta * hv / (double)N * c->h_sum[1];
+    if (c->kmode == 2) J += 0.5 * c->gamma * hv / (double)N * c->h_sum[2];
+    c->have_lin = false;
+    return J;
+}
+
+}  // namespace
+
+extern "C" int reg3_solve(reg3_ctx* c, float* v, double tol, int maxit_newton, int maxit_pcg, double* stats) {
+    if (!c || !v) return reg_fail(REG_ERR_ARG, "NULL argument");
+    if (!c->have_images) return reg_fail(REG_ERR_STATE, "reg3_set_images first");
+    if (!(tol > 0.0) || maxit_newton < 0 || maxit_pcg < 1) return reg_fail(REG_ERR_ARG, "tol > 0, maxit_pcg >= 1");
+    const long long N3 = 3 * c->D.N;
+    float *g, *vt, *r, *z, *sd, *Hs, *vtrial;
+    float** bufs[] = {&g, &vt, &r, &z, &sd, &Hs, &vtrial};
+    for (float** b : bufs) *b = nullptr;
+    for (float** b : bufs)
+        if (cudaMalloc((void**)b, sizeof(float) * N3) != cudaSuccess) {
+            cudaGetLastError();
+            for (float** q : bufs) cudaFree(*q);
+            return reg_fail(REG_ERR_NOMEM, "reg3_solve work vectors");
+        }
+    int k = 0, nmv = 0, nls = 0, status = REG_OK;
+    double J = 0.0, J0 = 0.0, g0 = 0.0, gn = 0.0;
+    auto done = [&](int st) {
+        if (stats) {
+            stats[0] = k;
+            stats[1] = nmv;
+            stats[2] = nls;
+            stats[3] = g0 > 0.0 ? gn / g0 : 0.0;
+            stats[4] = J;
+            stats[5] = st;
+            stats[6] = J0;
+        }
+        for (float** q : bufs) cudaFree(*q);
+        return st;
+    };
+    const double c1 = 1e-4, rho = 0.5;
+    const int max_ls = 20;
+    // Algorithm 1 from v = 0: the stopping test is relative to ||g(0)||
+    cudaMemsetAsync(v, 0, sizeof(float) * N3, c->stream);
+    int st = reg3_gradient(c, v, g, &J);
+    if (st != REG_OK) return done(st);
+    J0 = J;
+    g0 = gn = std::sqrt(inner3(c, g, g));
+    while (g0 > 0.0 && gn / g0 > tol) {
+        if (k >= maxit_newton) { status = REG_ERR_MAXIT; break; }
+        // Algorithm 2: preconditioned CG on H v~ = -g to ||r|| < eta ||g||
+        const double eta = std::fmin(0.5, std::sqrt(gn / g0));
+        cudaMemsetAsync(vt, 0, sizeof(float) * N3, c->stream);
+        cudaMemsetAsync(r, 0, sizeof(float) * N3, c->stream);
+        k3_axpby<<<R3_BLOCKS, R3_THREADS, 0, c->stream>>>(g, r, N3, -1.f, 0.f);  // r = -g
+        precond3(c, r, z);
+        cudaMemcpyAsync(sd, z, sizeof(float) * N3, cudaMemcpyDeviceToDevice, c->stream);
+        double rz = inner3(c, r, z);
+        for (int it = 1; it <= maxit_pcg; ++it) {
+            st = reg3_hessian_matvec(c, sd, Hs);
+            if (st != REG_OK) return done(st);
+            ++nmv;
+            const double sHs = inner3(c, sd, Hs);
+            if (!(sHs > 0.0)) {
+                if (it == 1) cudaMemcpyAsync(vt, sd, sizeof(float) * N3, cudaMemcpyDeviceToDevice, c->stream);
+                break;
+            }
+            const float kappa = (float)(rz / sHs);
+            k3_axpby<<<R3_BLOCKS, R3_THREADS, 0, c->stream>>>(sd, vt, N3, kappa, 1.f);
+            k3_axpby<<<R3_BLOCKS, R3_THREADS, 0, c->stream>>>(Hs, r, N3, -kappa, 1.f);
+            if (std::sqrt(inner3(c, r, r)) < eta * gn) break;
+            precond3(c, r, z);
+            const double rz_new = inner3(c, z, r);
+            k3_axpby<<<R3_BLOCKS, R3_THREADS, 0, c->stream>>>(z, sd, N3, 1.f, (float)(rz_new / rz));
+            rz = rz_new;
+        }
+        double gv = inner3(c, g, vt);
+        if (gv >= 0.0) {  // not a descent direction: the preconditioned steepest descent step
+            precond3(c, g, vt);
+            k3_axpby<<<R3_BLOCKS, R3_THREADS, 0, c->stream>>>(vt, vt, N3, 0.f, -1.f);
+            gv = inner3(c, g, vt);
+        }
+        // Armijo backtracking on J
+        double alpha = 1.0;
+        bool accepted = false;
+        for (int l = 0; l < max_ls; ++l) {
+            cudaMemcpyAsync(vtrial, v, sizeof(float) * N3, cudaMemcpyDeviceToDevice, c->stream);
+            k3_axpby<<<R3_BLOCKS, R3_THREADS, 0, c->stream>>>(vt, vtrial, N3, (float)alpha, 1.f);
+            ++nls;
+            // a trial beyond the explicit scheme's stability gives a non-finite J: rejected like any
+            // other trial that fails the sufficient-decrease test
+            const double Jt = objective3(c, vtrial);
+            if (std::isfinite(Jt) && Jt <= J + c1 * alpha * gv) {
+                accepted = true;
+                break;
+            }
+            alpha *= rho;
+        }
+        if (!accepted) { status = REG_ERR_LINESEARCH; break; }
+        cudaMemcpyAsync(v, vtrial, sizeof(float) * N3, cudaMemcpyDeviceToDevice, c->stream);
+        ++k;
+        st = reg3_gradient(c, v, g, &J);
+        if (st != REG_OK) return done(st);
+        gn = std::sqrt(inner3(c, g, g));
+    }
+    const int e = r3_err("reg3_solve");
+    if (e != REG_OK) return done(e);
+    if (status == REG_ERR_LINESEARCH) return done(reg_fail(status, "line search failed"));
+    if (status == REG_ERR_MAXIT) return done(reg_fail(status, "Newton iteration cap reached before the tolerance"));
+    return done(REG_OK);
 }

@@ -109,3 +109,4 @@ def test_3d_entry_points_reject_invalid_arguments_without_gpu(lib):
     assert lib.reg3_gradient(None, None, None, None) == 1
     assert lib.reg3_hessian_matvec(None, None, None) == 1
     assert lib.reg3_set_images(None, None, None) == 1
+    assert lib.reg3_solve(None, None, 1e-2, 10, 10, None) == 1

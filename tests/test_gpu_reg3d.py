@@ -104,3 +104,32 @@ def test_matvec_needs_a_gradient_first():
     with pytest.raises(Exception):
         ctx.gradient(x, x.clone())  # no images yet
     ctx.close()
+
+
+@pytest.mark.parametrize("beta_w", [math.inf, 0.0])
+def test_solve_matches_oracle_solve(beta_w):
+    """Algorithm 1 on the GPU against the oracle's Algorithm 1 (16^3, nt = 4, tol 1e-2): the
+    same Newton count, the stopping test confirmed by the oracle's gradient at the GPU's v
+    (<= 1.1e-2 ||g(0)||: 10 % slack for the FP32 gradient the GPU stopped on), and v within
+    the spread two solves that both pass the test may have (compared at 2e-2: inexact PCG
+    solves determine v only to kappa(H) times the tolerance)."""
+    import torch
+    from paper_1503_00757_gb300.binding import Context3D
+    shape, nt, beta = (16, 16, 16), 4, 1e-2
+    mT, mR, _, _ = _inputs(shape, 7100, nt)
+    P = R.Registration3D(mT, mR, nt, beta, beta_w)
+    v_ref, st_ref = R.solve(P, tol=1e-2)
+    assert st_ref["status"] == 0
+    ctx = Context3D(*shape, nt, beta=beta, gamma=beta_w)
+    ctx.set_images(to_gpu(mT), to_gpu(mR))
+    v = torch.empty(3, *shape, device="cuda")
+    st = ctx.solve(v, tol=1e-2)
+    ctx.close()
+    assert st["rc"] == 0 and st["status"] == 0 and st["gnorm_rel"] <= 1e-2
+    assert st["n_newton"] == st_ref["n_newton"]
+    vg = to_np(v)
+    g0 = R.norm(P.gradient(np.zeros_like(v_ref))[0])
+    check(f"3-D solve: oracle ||g(v)|| / ||g(0)|| at the GPU's v (beta_w={beta_w})", R.norm(P.gradient(vg)[0]) / g0,
+          1.1e-2)
+    check(f"3-D solve: v against the oracle's solve (beta_w={beta_w})",
+          np.linalg.norm(vg - v_ref) / np.linalg.norm(v_ref), 2e-2)
