@@ -488,11 +488,13 @@ extern "C" int reg3_create(int n1, int n2, int n3, int nt, double beta, double g
         reg3_destroy(c);
         return reg_fail(REG_ERR_NOMEM, "3-D context allocation failed");
     }
-    size_t smax = 0;
-    for (int axis = 0; axis < 3; ++axis) {
-        const size_t s = pass_smem(line_map(c->D, axis));
-        if (s > smax) smax = s;
-    }
+    // the opt-in is a per-kernel, per-device attribute shared by every context: always the
+    // largest tile any legal grid needs (256-point lines, 32 per CTA), so that a smaller context
+    // created later never lowers it under a larger one
+    LineMap mmax;
+    mmax.L = 256;
+    mmax.TWL = R3_TILE;
+    const size_t smax = pass_smem(mmax);
     cudaFuncSetAttribute(k3_fft_pass<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smax);
     cudaFuncSetAttribute(k3_fft_pass<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smax);
     const int st = r3_err("3-D context set-up");
