@@ -133,3 +133,23 @@ def test_solve_matches_oracle_solve(beta_w):
           1.1e-2)
     check(f"3-D solve: v against the oracle's solve (beta_w={beta_w})",
           np.linalg.norm(vg - v_ref) / np.linalg.norm(v_ref), 2e-2)
+
+
+def test_contexts_of_different_sizes_coexist():
+    """A large-tile context stays usable after a smaller one is created (the FFT pass's
+    shared-memory opt-in is shared by all contexts of the process)."""
+    import torch
+    from paper_1503_00757_gb300.binding import Context3D
+    shape, nt = (8, 8, 256), 2
+    mT, mR, v, _ = _inputs(shape, 7200, nt)
+    big = Context3D(*shape, nt, beta=1e-2)
+    small = Context3D(16, 16, 16, 2, beta=1e-2)
+    big.set_images(to_gpu(mT), to_gpu(mR))
+    g = torch.empty(3, *shape, device="cuda")
+    J = big.gradient(to_gpu(v), g)
+    torch.cuda.synchronize()
+    small.close()
+    big.close()
+    g_ref, J_ref = R.Registration3D(mT, mR, nt, 1e-2).gradient(v)
+    assert abs(J - J_ref) < 2e-5 * abs(J_ref)
+    assert np.linalg.norm(to_np(g) - g_ref) < 2e-4 * np.linalg.norm(g_ref)
